@@ -1,0 +1,180 @@
+"""Pins for the PBAS oracle (Sec. 3.2; Hofmann et al. base method).
+
+Hand traces with the test-only forced draws (every field written out), the
+gradient-weight effect worked by hand, closed forms for constant input and a
+step, invariants (bounds of R and T, S equal to the sum of D, the own-value
+history rule, depth gating), and the rates of the Philox-driven draws.
+"""
+import numpy as np
+import pytest
+
+f32 = np.float32
+
+
+def _seq(values_r, H=1, W=1, gb=50, depth=0):
+    n = len(values_r)
+    rgb = np.empty((n, H, W, 3), np.uint8)
+    for t, v in enumerate(values_r):
+        rgb[t, ..., 0] = v
+    rgb[..., 1] = gb
+    rgb[..., 2] = gb
+    d = np.full((n, H, W), depth, np.uint16)
+    return rgb, d
+
+
+def test_hand_trace_single_pixel(orc):
+    # N = 2, #min = 2, forced draws (own slot t mod 2), depth invalid, 1x1 frame
+    # (gradient 0 everywhere, mean clamped to 1, weight 10).  Red: 100 100 130 110 110.
+    rgb, d = _seq([100, 100, 130, 110, 110])
+    p = orc.PBAS(1, 1, N=2, forced_rng=1)
+    masks = [int(p.step(rgb[t], d[t])[0, 0]) for t in range(5)]
+    assert masks == [0, 0, 255, 0, 0]
+    # frame 3: d_min 10 -> D[1] = 160, S = 160, mean D = 160 / 32 = 5;
+    # frame 4: slot 0 takes 110 with d_min 0.
+    assert p.sv[0, 0].tolist() == [110, 110]
+    assert p.sg[0, 0].tolist() == [0, 0]
+    assert p.sD[0, 0].tolist() == [0, 160]
+    assert int(p.S[0, 0]) == 160
+    # R: 18 (floored) through frame 2, then grows twice (R < 5 * 5).
+    up = f32(1) + f32(0.05)
+    assert p.R[0, 0] == f32(f32(18) * up) * up
+    # T: 2 (clamped) -> 2 + 1/0.0625 = 18 at frame 2, then -0.05/5 twice.
+    step = f32(0.05) / f32(5)
+    assert p.T[0, 0] == f32(f32(18) - step) - step
+    # green/blue constant: R stays at its floor, T at its floor
+    assert p.R[0, 1] == 18 and p.T[0, 1] == 2 and p.S[0, 1] == 0
+
+
+def test_hand_trace_neighbour_update_3x3(orc):
+    # Forced draws at frame 1: own slot 1, neighbour direction 1 (north-east),
+    # neighbour slot 0.  Red goes 50 -> 60 everywhere (background, gradient 0).
+    # Sources whose NE neighbour is inside: (x,y) in {0,1}x{1,2}; their targets
+    # (1,0),(2,0),(1,1),(2,1) take their own value 60 into slot 0.
+    rgb, d = _seq([50, 60], H=3, W=3)
+    p = orc.PBAS(3, 3, N=2, forced_rng=1)
+    for t in range(2):
+        assert not p.step(rgb[t], d[t]).any()
+    sv = p.sv[:, 0, :].reshape(3, 3, 2)
+    assert (sv[..., 1] == 60).all()
+    want0 = np.full((3, 3), 50)
+    for (x, y) in [(1, 0), (2, 0), (1, 1), (2, 1)]:
+        want0[y, x] = 60
+    np.testing.assert_array_equal(sv[..., 0], want0)
+
+
+def test_gradient_weight_uses_previous_mean(orc):
+    # Frame 0 columns 0,0,100,100: gradient row 0,50,50,0, mean 25, weight 10/25.
+    # Frame 1 columns 0,0,120,120: gradient 0,60,60,0.  Distances to the frame-0
+    # samples: 0, 0.4*10 = 4, 4 + 20 = 24, 20, against R = 18:
+    # only the last two columns are foreground (weight 10 would flag column 1).
+    rgb = np.zeros((2, 4, 4, 3), np.uint8)
+    rgb[0, :, 2:, :] = 100
+    rgb[1, :, 2:, :] = 120
+    d = np.zeros((2, 4, 4), np.uint16)
+    p = orc.PBAS(4, 4, N=3)
+    p.step(rgb[0], d[0])
+    assert p.gsum.tolist() == [400, 400, 400, 0]
+    m = p.step(rgb[1], d[1])
+    np.testing.assert_array_equal(m, np.tile([0, 0, 255, 255], (4, 1)).astype(np.uint8))
+
+
+def test_constant_input_closed_form(orc):
+    # Every distance is 0: background, d_min = 0, so S = 0, mean D = eps = 1/16,
+    # R stays at its floor (R > 5/16 shrinks it, the floor restores it) and T
+    # drops to T_lower after one frame; samples never change.
+    rgb, d = _seq([77] * 12, H=5, W=6, depth=3000)
+    p = orc.PBAS(6, 5)
+    for t in range(12):
+        assert not p.step(rgb[t], d[t]).any()
+    assert (p.R[:, :3] == 18).all() and (p.R[:, 3] == 4).all()
+    assert (p.T == 2).all() and (p.S == 0).all() and (p.sD == 0).all()
+    assert (p.sv[:, 0] == 77).all() and (p.sv[:, 3] == 77).all()  # 3000 mm -> 77
+
+
+def test_step_change_raises_T(orc):
+    # After a jump of 60 the pixel is foreground; no own update, so S stays 0
+    # and mean D = 1/16: T rises by T_inc / (1/16) = 16 per frame up to 200.
+    rgb, d = _seq([50] * 5 + [110] * 16, H=2, W=2)
+    p = orc.PBAS(2, 2)
+    Ts = []
+    for t in range(21):
+        m = p.step(rgb[t], d[t])
+        assert m.all() == (t >= 5)
+        Ts.append(float(p.T[0, 0]))
+    assert Ts[4] == 2.0
+    assert Ts[5:16] == [2.0 + 16 * k for k in range(1, 12)]
+    assert Ts[17:] == [200.0] * 4
+
+
+def _history_run(orc, W=9, H=7, n=25, seed=3):
+    from paper_2002_00250_gb300 import synth
+    cfg = synth.SceneConfig(W, H, n, seed=seed, n_objects=1, hole_fraction=0.2)
+    sc = synth.RGBDScene(cfg)
+    rgb, depth, _ = (synth.to_numpy(a) for a in sc.sequence())
+    return rgb, depth
+
+
+def test_invariants_and_own_value_history(orc):
+    W, H, n = 9, 7, 25
+    rgb, depth = _history_run(orc, W, H, n)
+    p = orc.PBAS(W, H, N=6, seed=11)
+    P = W * H
+    hist = [[set() for _ in range(4)] for _ in range(P)]
+    for t in range(n):
+        ch = np.stack([rgb[t, ..., 0], rgb[t, ..., 1], rgb[t, ..., 2], orc.depth_to_u8(depth[t])])
+        gr = np.stack([orc.sobel_grad_u8(c) for c in ch])
+        valid = depth[t].ravel() != 0
+        for i in range(P):
+            for c in range(4):
+                if c < 3 or valid[i] or t == 0:
+                    hist[i][c].add((int(ch[c].ravel()[i]), int(gr[c].ravel()[i])))
+        before_d = (p.sv[:, 3].copy(), p.sg[:, 3].copy(), p.R[:, 3].copy(), p.T[:, 3].copy())
+        p.step(rgb[t], depth[t])
+        assert (p.R[:, :3] >= 18).all() and (p.R[:, 3] >= 4).all()
+        assert (p.T >= 2).all() and (p.T <= 200).all()
+        np.testing.assert_array_equal(p.S, p.sD.astype(np.uint64).sum(axis=2))
+        for i in range(P):
+            for c in range(4):
+                for k in range(6):
+                    assert (int(p.sv[i, c, k]), int(p.sg[i, c, k])) in hist[i][c]
+        if t > 0:  # depth channel untouched where the reading is invalid
+            inv = ~valid
+            for a, b in zip(before_d, (p.sv[:, 3], p.sg[:, 3], p.R[:, 3], p.T[:, 3])):
+                np.testing.assert_array_equal(a[inv], b[inv])
+
+
+def test_draw_rates(orc):
+    # Background everywhere, T = 2 -> update probability 1/2.  Red 50 -> 52 with
+    # gradient 0: an own update writes D = 2*16 = 32 into a uniform slot; a
+    # neighbour write sets the value 52 but leaves D = 0.
+    W = H = 64
+    rgb, d = _seq([50, 52], H=H, W=W)
+    p = orc.PBAS(W, H, seed=123)
+    p.step(rgb[0], d[0])
+    p.step(rgb[1], d[1])
+    own = p.sD[:, 0, :] == 32
+    n_own = own.sum(axis=1)
+    assert set(np.unique(n_own).tolist()) <= {0, 1}
+    frac = n_own.mean()
+    assert abs(frac - 0.5) < 4 * np.sqrt(0.25 / (W * H))
+    counts = own.sum(axis=0)
+    expect = own.sum() / 20
+    chi2 = ((counts - expect) ** 2 / expect).sum()
+    assert chi2 < 45.3  # chi-square, 19 dof, p = 0.001
+    assert (counts > 0).all()
+    # neighbour writes: interior pixels receive on average 8 * 1/2 * 1/8 = 0.5
+    nb = ((p.sv[:, 0, :] == 52) & (p.sD[:, 0, :] == 0)).sum(axis=1).reshape(H, W)
+    inner = nb[1:-1, 1:-1].mean()
+    assert 0.4 < inner < 0.55
+
+
+def test_seed_and_stream_change_draws(orc):
+    rgb, d = _seq([50, 52], H=16, W=16)
+    outs = []
+    for seed, sid in [(1, 0), (1, 0), (2, 0), (1, 1)]:
+        p = orc.PBAS(16, 16, seed=seed, stream_id=sid)
+        p.step(rgb[0], d[0])
+        p.step(rgb[1], d[1])
+        outs.append(p.sD.copy())
+    assert (outs[0] == outs[1]).all()
+    assert (outs[0] != outs[2]).any() and (outs[0] != outs[3]).any()
