@@ -1,0 +1,224 @@
+/*
+ * fos.h -- C ABI of the GB300 (sm_103a) RGB-D foreground segmentation library.
+ *
+ * Foreground object segmentation in RGB-D video with two per-pixel background
+ * models (Janus, Kryjak, Gorgon, "Foreground object segmentation in RGB-D data
+ * implemented on GPU"):
+ *   GMM   Sec. 3.1 (Eq. 1): two separate Gaussian mixtures per pixel, one over
+ *         colour and one over depth; the depth model is used only where the
+ *         depth reading is valid (> 0); the two results are combined.
+ *   PBAS  Sec. 3.2: N background samples per pixel, each holding R, G, B and
+ *         depth, every channel processed separately with its own adaptive
+ *         decision threshold R(x), learning parameter T(x) and minimal-distance
+ *         record D(x); random update of the pixel's own and its neighbours'
+ *         samples; depth used only where valid.
+ *   Depth is rescaled from 16 to 8 bits as Sec. 4.2 describes.  The host owns
+ *   acquisition and copies frames to the GPU; the GPU classifies every pixel
+ *   in parallel and returns a binary mask (Sec. 4.2, "Application architecture").
+ *
+ * Conventions for every entry point:
+ *   - Frames are row-major.  rgb: H*W*3 bytes, interleaved R,G,B.  depth: H*W
+ *     uint16 millimetres, 0 = invalid.  masks: H*W bytes, 0 = background,
+ *     255 = foreground.
+ *   - "host" pointers are ordinary (pageable or pinned) CPU memory; "device"
+ *     pointers are CUDA global memory of the current device.  The caller owns
+ *     every frame buffer; the library does not keep a pointer after returning.
+ *   - A context owns its device state and is not thread-safe: one thread (and
+ *     one stream at a time) per context.
+ *   - Errors never abort.  Each call returns a fos_status; the text of the last
+ *     error is available from fos_last_error().  CUDA errors map to
+ *     FOS_ERR_CUDA.  A sticky CUDA error leaves the context unusable.
+ *   - The first frame a context processes (frame 0) initialises the models;
+ *     its masks are all background.
+ */
+#ifndef FOS_H
+#define FOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FOS_ABI_VERSION 1
+
+/* Method selection bits (fos_params.methods). */
+#define FOS_METHOD_GMM 1u  /* Sec. 3.1 */
+#define FOS_METHOD_PBAS 2u /* Sec. 3.2 */
+
+typedef enum fos_status {
+    FOS_OK = 0,
+    FOS_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or parameter */
+    FOS_ERR_CUDA = 2,        /* a CUDA call failed; see fos_last_error */
+    FOS_ERR_OOM = 3,         /* device or pinned host allocation failed */
+    FOS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    FOS_ERR_BUDGET = 5,      /* admission refused: memory budget exceeded */
+    FOS_ERR_STATE = 6,       /* call not valid in the context's current state */
+    FOS_ERR_UNSUPPORTED = 7  /* parameter combination not compiled in */
+} fos_status;
+
+/*
+ * Parameters.  fos_default_params() fills the values the library is tuned and
+ * tested with; the paper fixes N = 20 (Sec. 3.2) and alpha = 0.001 (Sec. 3.1);
+ * the other constants follow the cited base methods (Stauffer-Grimson GMM,
+ * Hofmann PBAS) or are readings of the paper documented with the library.
+ */
+typedef struct fos_params {
+    uint32_t methods;          /* FOS_METHOD_GMM | FOS_METHOD_PBAS */
+    /* ---- GMM (Sec. 3.1) ---- */
+    int32_t K_rgb;             /* components of the colour model: 1,2,3,5,7 */
+    int32_t K_d;               /* components of the depth model: 1,2,3 */
+    float alpha;               /* learning rate (paper: 0.001) */
+    float lambda;              /* match threshold on the Mahalanobis distance */
+    float w_depth;             /* weight of the depth model in the combined score */
+    float T_bg;                /* background weight fraction */
+    float v_init_rgb, v_init_d;/* variance of a new component */
+    float v_min_rgb, v_min_d;  /* variance floor */
+    /* ---- PBAS (Sec. 3.2) ---- */
+    int32_t N;                 /* samples per pixel, 1..32 (paper: 20) */
+    int32_t n_min;             /* matches needed for background */
+    float R_lower_rgb, R_lower_d, R_scale, R_incdec;
+    float T_lower, T_upper, T_inc, T_dec;
+    float alpha_g;             /* gradient weight numerator */
+    float eps_d;               /* floor of the mean minimal distance */
+    uint32_t seed;             /* Philox4x32-10 key word 0 */
+    uint32_t stream_id;        /* Philox4x32-10 key word 1 (camera stream) */
+    int32_t forced_rng;        /* 0: Philox; 1: deterministic test draws */
+    /* ---- input conversion (Sec. 4.2) ---- */
+    uint32_t depth_full_scale_mm; /* depth mapped onto 1..255, 0 = invalid */
+} fos_params;
+
+typedef struct fos_ctx fos_ctx;
+
+/* Fills *p with the defaults (both methods enabled). NULL-safe. */
+void fos_default_params(fos_params* p);
+
+/* ABI version of the loaded library (FOS_ABI_VERSION it was built with). */
+int32_t fos_abi_version(void);
+
+/*
+ * Creates a context for width x height frames (1..16384 each) and allocates
+ * its device state on the current CUDA device.  Returns NULL on error; the
+ * reason is then available from fos_last_error(NULL) on the calling thread.
+ */
+fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params);
+
+/* Frees the context and its device memory.  NULL-safe. */
+void fos_destroy(fos_ctx* ctx);
+
+/* Text of the context's last error ("" if none); ctx == NULL gives the calling
+ * thread's last fos_create error.  The pointer stays valid until the next call
+ * on the same context / thread. */
+const char* fos_last_error(const fos_ctx* ctx);
+
+/* Restarts the sequence: the next processed frame is frame 0 again. */
+fos_status fos_reset(fos_ctx* ctx);
+
+/* Number of frames processed since creation or the last reset. */
+int64_t fos_frame_index(const fos_ctx* ctx);
+
+/*
+ * One frame from HOST memory, synchronous: copies rgb and depth to the
+ * device, runs the enabled methods, copies the mask back and waits.
+ * mask_out receives the GMM mask when GMM is enabled, else the PBAS mask.
+ */
+fos_status fos_process_frame(fos_ctx* ctx, const uint8_t* rgb, const uint16_t* depth,
+                             uint8_t* mask_out);
+
+/* As fos_process_frame, returning both masks (either may be NULL if its
+ * method is disabled). */
+fos_status fos_process_frame2(fos_ctx* ctx, const uint8_t* rgb, const uint16_t* depth,
+                              uint8_t* mask_gmm, uint8_t* mask_pbas);
+
+/*
+ * One frame from DEVICE memory, asynchronous on `stream` (a cudaStream_t;
+ * NULL = legacy default stream).  mask_gmm / mask_pbas must be non-NULL for
+ * each enabled method.  Any alignment is accepted; 16-byte aligned buffers
+ * whose width is a multiple of 4 take the vectorised kernels.
+ */
+fos_status fos_process_frame_device(fos_ctx* ctx, const uint8_t* d_rgb, const uint16_t* d_depth,
+                                    uint8_t* d_mask_gmm, uint8_t* d_mask_pbas, void* stream);
+
+/*
+ * n_frames consecutive frames from DEVICE memory, asynchronous on `stream`.
+ * Frame f starts at d_rgb + f*H*W*3, d_depth + f*H*W, and writes its masks at
+ * d_mask_gmm + f*H*W, d_mask_pbas + f*H*W.
+ */
+fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8_t* d_rgb,
+                                     const uint16_t* d_depth, uint8_t* d_mask_gmm,
+                                     uint8_t* d_mask_pbas, void* stream);
+
+/*
+ * n_frames consecutive frames from HOST memory (same strides as above),
+ * pipelined: the copy of frame f+1 overlaps the kernels of frame f.  Pinned
+ * host buffers give the overlap; pageable ones still work, serialised.
+ * Synchronous: returns when every mask is in host memory.
+ */
+fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t* rgb,
+                                   const uint16_t* depth, uint8_t* mask_gmm, uint8_t* mask_pbas);
+
+/* ---------------------------------------------------------------------------
+ * Model state export / import (checkpoint, resume, step-by-step testing).
+ * Blob layout: fos_state_header, then the GMM section (if enabled), then the
+ * PBAS section (if enabled); every plane holds P = W*H values, unpadded.
+ *   GMM  (float32): for the colour model with K = K_rgb components, planes
+ *        w[k], mu_r[k], mu_g[k], mu_b[k], v[k] (in that order, each k = 0..K-1),
+ *        then for the depth model with K = K_d: w[k], mu[k], v[k].
+ *        Components are stored in ranked order (k = 0 ranks highest).
+ *   PBAS: samples  uint16 planes [c][k] (c = R,G,B,D; k = 0..N-1), value in the
+ *                  low byte, gradient magnitude in the high byte;
+ *         D        uint16 planes [c][k]: minimal distance x16 (rounded);
+ *         R, T     float32 planes [c];
+ *         S        uint32 planes [c]: sum over k of D[c][k];
+ *         gsum     uint64[4]: gradient-magnitude sums of the last frame.
+ * ------------------------------------------------------------------------- */
+typedef struct fos_state_header {
+    uint32_t magic;      /* 0x53534F46 ("FOSS") */
+    uint32_t abi_version;
+    int32_t width, height;
+    uint32_t methods;
+    int32_t K_rgb, K_d, N;
+    int64_t frame_index;
+    uint64_t gmm_bytes, pbas_bytes;
+} fos_state_header;
+
+/* Size in bytes of the blob fos_get_state writes. */
+fos_status fos_state_size(const fos_ctx* ctx, size_t* bytes);
+/* Writes the blob into host memory (synchronises the context's work). */
+fos_status fos_get_state(fos_ctx* ctx, void* host_buf, size_t bytes);
+/* Replaces the device state with a blob from fos_get_state of a context with
+ * the same size, methods, K_rgb, K_d and N. */
+fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes);
+
+/* ---------------------------------------------------------------------------
+ * Measurement hooks.
+ * ------------------------------------------------------------------------- */
+#define FOS_KERNEL_GMM 0        /* GMM classify + update (Sec. 3.1) */
+#define FOS_KERNEL_PBAS_CLASSIFY 1 /* PBAS gradient, classify, own update */
+#define FOS_KERNEL_PBAS_NEIGHBOUR 2 /* PBAS neighbour update */
+#define FOS_KERNEL_INIT 3       /* frame-0 initialisation */
+#define FOS_KERNEL_COUNT 4
+
+typedef struct fos_kernel_timing {
+    int64_t launches;
+    double total_ms;  /* sum of CUDA-event durations on the launch stream */
+} fos_kernel_timing;
+
+/* Bit k of mask enables CUDA-event timing around every launch of kernel k. */
+fos_status fos_set_timing(fos_ctx* ctx, uint32_t kernel_mask);
+/* Waits for the timed launches and writes FOS_KERNEL_COUNT entries; then
+ * clears the accumulators. */
+fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT]);
+
+/*
+ * PBAS update counters since the last call (then cleared):
+ * out[0] own-sample updates, out[1] neighbour-sample writes applied,
+ * out[2] neighbour requests issued, out[3] frames.
+ */
+fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOS_H */

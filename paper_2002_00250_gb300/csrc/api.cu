@@ -1,0 +1,574 @@
+// api.cu -- the C ABI (include/fos.h): contexts, device state, frame loop,
+// state export/import, timing and counters.
+//
+// The paper's heterogeneous frame loop (Sec. 4.2): the host allocates the
+// background model, copies each frame to the GPU, the GPU classifies and
+// updates every pixel in parallel, and the mask is copied back.  Here the
+// context owns the device-resident model (SoA planes, padded to 128 elements
+// so every plane starts 256-byte aligned); frames come either from device
+// memory (asynchronous, caller's stream) or from host memory (synchronous,
+// with the next frame's copy overlapping the current frame's kernels).
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fos.h"
+#include "fos_internal.h"
+
+using namespace fos;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t start, stop;
+};
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct fos_ctx {
+    int W = 0, H = 0;
+    int64_t P = 0, plane = 0;
+    fos_params prm{};
+    int64_t t = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;       // host-pointer API: kernels + mask copies
+    cudaStream_t copy_stream = nullptr;  // host-pointer API: input copies
+    float* gmm = nullptr;
+    uint16_t* samp = nullptr;
+    uint16_t* Dq = nullptr;
+    float* R = nullptr;
+    float* T = nullptr;
+    uint32_t* S = nullptr;
+    uint32_t* req = nullptr;
+    unsigned long long* aux = nullptr;  // gsum[2][4], counters[4]
+    uint8_t* h_rgb[2] = {nullptr, nullptr};  // device staging for host frames
+    uint16_t* h_depth[2] = {nullptr, nullptr};
+    uint8_t* h_mg[2] = {nullptr, nullptr};
+    uint8_t* h_mp[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+    uint32_t timing_mask = 0;
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    uint64_t frames_since_counters = 0;
+    std::string err;
+};
+
+namespace {
+
+fos_status fail(fos_ctx* c, fos_status st, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+fos_status cuda_fail(fos_ctx* c, const char* what, cudaError_t e)
+{
+    char buf[512];
+    std::snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return fail(c, e == cudaErrorMemoryAllocation ? FOS_ERR_OOM : FOS_ERR_CUDA, buf);
+}
+
+#define FOS_TRY(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, #call, e_); \
+    } while (0)
+
+bool gmm_on(const fos_ctx* c) { return c->prm.methods & FOS_METHOD_GMM; }
+bool pbas_on(const fos_ctx* c) { return c->prm.methods & FOS_METHOD_PBAS; }
+
+bool k_supported(int Kr, int Kd)
+{
+    const bool r = Kr == 1 || Kr == 2 || Kr == 3 || Kr == 5 || Kr == 7;
+    const bool d = Kd >= 1 && Kd <= 3;
+    return r && d;
+}
+
+fos_status validate_params(const fos_params* p, std::string& why)
+{
+    if (!p) { why = "params is NULL"; return FOS_ERR_INVALID_ARG; }
+    if (p->methods == 0 || (p->methods & ~(FOS_METHOD_GMM | FOS_METHOD_PBAS))) {
+        why = "methods must be a non-empty subset of GMM|PBAS"; return FOS_ERR_INVALID_ARG;
+    }
+    if (p->methods & FOS_METHOD_GMM) {
+        if (!k_supported(p->K_rgb, p->K_d)) {
+            why = "unsupported (K_rgb, K_d); K_rgb in {1,2,3,5,7}, K_d in {1,2,3}";
+            return FOS_ERR_UNSUPPORTED;
+        }
+        if (!(p->alpha > 0.f && p->alpha <= 1.f) || !(p->lambda > 0.f) || !(p->T_bg > 0.f) ||
+            !(p->w_depth >= 0.f && p->w_depth <= 1.f) || !(p->v_init_rgb > 0.f) ||
+            !(p->v_init_d > 0.f) || !(p->v_min_rgb > 0.f) || !(p->v_min_d > 0.f)) {
+            why = "GMM parameter out of range"; return FOS_ERR_INVALID_ARG;
+        }
+    }
+    if (p->methods & FOS_METHOD_PBAS) {
+        if (p->N < 1 || p->N > 32 || p->n_min < 1 || p->n_min > p->N) {
+            why = "PBAS needs 1 <= n_min <= N <= 32"; return FOS_ERR_INVALID_ARG;
+        }
+        if (!(p->T_lower > 0.f) || !(p->T_upper >= p->T_lower) || !(p->eps_d > 0.f) ||
+            !(p->R_lower_rgb > 0.f) || !(p->R_lower_d > 0.f) || !(p->R_incdec >= 0.f && p->R_incdec < 1.f)) {
+            why = "PBAS parameter out of range"; return FOS_ERR_INVALID_ARG;
+        }
+    }
+    if (p->depth_full_scale_mm == 0 || p->depth_full_scale_mm > 65535u * 4u) {
+        why = "depth_full_scale_mm out of range"; return FOS_ERR_INVALID_ARG;
+    }
+    return FOS_OK;
+}
+
+cudaEvent_t pool_event(fos_ctx* c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// Records events around one launch when its kind is being timed.
+struct TimedScope {
+    fos_ctx* c;
+    cudaStream_t s;
+    TimedLaunch tl{};
+    bool on;
+    TimedScope(fos_ctx* c_, int kind, cudaStream_t s_) : c(c_), s(s_), on(false)
+    {
+        if (c->timing_mask & (1u << kind)) {
+            tl.kind = kind;
+            tl.start = pool_event(c);
+            tl.stop = pool_event(c);
+            if (tl.start && tl.stop) {
+                cudaEventRecord(tl.start, s);
+                on = true;
+            }
+        }
+    }
+    ~TimedScope()
+    {
+        if (on) {
+            cudaEventRecord(tl.stop, s);
+            c->timed.push_back(tl);
+        }
+    }
+};
+
+fos_status launch_result(fos_ctx* c, LaunchResult r, const char* what)
+{
+    if (r == kLaunchOk) return FOS_OK;
+    if (r == kLaunchUnsupported) return fail(c, FOS_ERR_UNSUPPORTED, std::string(what) + ": unsupported configuration");
+    return cuda_fail(c, what, cudaGetLastError());
+}
+
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mask)
+{
+    PbasArgs a{};
+    const fos_params& p = c->prm;
+    a.W = c->W; a.H = c->H; a.P = c->P; a.plane = c->plane;
+    a.rgb = rgb; a.depth = depth; a.mask = mask;
+    a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S; a.req = c->req;
+    a.gsum_prev = c->aux + ((c->t + 1) & 1) * 4;  // buffer of frame t-1
+    a.gsum_cur = c->aux + (c->t & 1) * 4;
+    a.counters = c->aux + 8;
+    a.R_lower_rgb = p.R_lower_rgb; a.R_lower_d = p.R_lower_d; a.R_scale = p.R_scale;
+    a.R_incdec = p.R_incdec; a.T_lower = p.T_lower; a.T_upper = p.T_upper;
+    a.T_inc = p.T_inc; a.T_dec = p.T_dec; a.alpha_g = p.alpha_g; a.eps_d = p.eps_d;
+    a.N = p.N; a.n_min = p.n_min; a.seed = p.seed; a.stream_id = p.stream_id;
+    a.forced = p.forced_rng; a.depth_fs = p.depth_full_scale_mm;
+    a.t = uint32_t(c->t);
+    a.vec_ok = (c->W % 4 == 0) && aligned(mask, 4);
+    return a;
+}
+
+fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mg,
+                          uint8_t* mp, cudaStream_t s)
+{
+    if (!rgb || !depth) return fail(c, FOS_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    if (gmm_on(c) && !mg) return fail(c, FOS_ERR_INVALID_ARG, "GMM enabled: mask_gmm must be non-NULL");
+    if (pbas_on(c) && !mp) return fail(c, FOS_ERR_INVALID_ARG, "PBAS enabled: mask_pbas must be non-NULL");
+    const bool first = c->t == 0;
+    if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 8 * sizeof(unsigned long long), s));
+    if (gmm_on(c)) {
+        GmmArgs a{};
+        const fos_params& p = c->prm;
+        a.P = c->P; a.plane = c->plane; a.state = c->gmm;
+        a.rgb = rgb; a.depth = depth; a.mask = mg;
+        a.alpha = p.alpha; a.lam2 = p.lambda * p.lambda; a.w_depth = p.w_depth; a.T_bg = p.T_bg;
+        a.v_init_rgb = p.v_init_rgb; a.v_init_d = p.v_init_d;
+        a.v_min_rgb = p.v_min_rgb; a.v_min_d = p.v_min_d;
+        a.depth_fs = p.depth_full_scale_mm;
+        a.init = first ? 1 : 0;
+        a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4);
+        TimedScope ts(c, first ? FOS_KERNEL_INIT : FOS_KERNEL_GMM, s);
+        fos_status st = launch_result(c, launch_gmm(a, p.K_rgb, p.K_d, s), "gmm");
+        if (st != FOS_OK) return st;
+    }
+    if (pbas_on(c)) {
+        const PbasArgs a = pbas_args(c, rgb, depth, mp);
+        if (first) {
+            TimedScope ts(c, FOS_KERNEL_INIT, s);
+            fos_status st = launch_result(c, launch_pbas_init(a, s), "pbas_init");
+            if (st != FOS_OK) return st;
+        } else {
+            {
+                TimedScope ts(c, FOS_KERNEL_PBAS_CLASSIFY, s);
+                fos_status st = launch_result(c, launch_pbas_classify(a, s), "pbas_classify");
+                if (st != FOS_OK) return st;
+            }
+            {
+                TimedScope ts(c, FOS_KERNEL_PBAS_NEIGHBOUR, s);
+                fos_status st = launch_result(c, launch_pbas_neighbour(a, s), "pbas_neighbour");
+                if (st != FOS_OK) return st;
+            }
+        }
+    }
+    c->t += 1;
+    c->frames_since_counters += 1;
+    return FOS_OK;
+}
+
+fos_status ensure_staging(fos_ctx* c)
+{
+    if (c->h_rgb[0]) return FOS_OK;
+    for (int b = 0; b < 2; ++b) {
+        FOS_TRY(c, cudaMalloc(&c->h_rgb[b], size_t(c->P) * 3 + 16));
+        FOS_TRY(c, cudaMalloc(&c->h_depth[b], size_t(c->P) * 2 + 16));
+        FOS_TRY(c, cudaMalloc(&c->h_mg[b], size_t(c->P) + 16));
+        FOS_TRY(c, cudaMalloc(&c->h_mp[b], size_t(c->P) + 16));
+        FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
+        FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
+    }
+    return FOS_OK;
+}
+
+size_t gmm_bytes(const fos_ctx* c)
+{
+    return gmm_on(c) ? size_t(gmm_planes(c->prm.K_rgb, c->prm.K_d)) * c->P * 4 : 0;
+}
+
+size_t pbas_bytes(const fos_ctx* c)
+{
+    if (!pbas_on(c)) return 0;
+    const size_t P = size_t(c->P), N = size_t(c->prm.N);
+    return 4 * N * P * 2 * 2 + 3 * 4 * P * 4 + 4 * 8;
+}
+
+void free_all(fos_ctx* c)
+{
+    cudaFree(c->gmm); cudaFree(c->samp); cudaFree(c->Dq); cudaFree(c->R); cudaFree(c->T);
+    cudaFree(c->S); cudaFree(c->req); cudaFree(c->aux);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
+        if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
+        if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void fos_default_params(fos_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->methods = FOS_METHOD_GMM | FOS_METHOD_PBAS;
+    p->K_rgb = 3; p->K_d = 3;
+    p->alpha = 0.001f; p->lambda = 2.5f; p->w_depth = 0.5f; p->T_bg = 0.7f;
+    p->v_init_rgb = 36.f; p->v_init_d = 4.f; p->v_min_rgb = 4.f; p->v_min_d = 0.25f;
+    p->N = 20; p->n_min = 2;
+    p->R_lower_rgb = 18.f; p->R_lower_d = 4.f; p->R_scale = 5.f; p->R_incdec = 0.05f;
+    p->T_lower = 2.f; p->T_upper = 200.f; p->T_inc = 1.f; p->T_dec = 0.05f;
+    p->alpha_g = 10.f; p->eps_d = 1.f / 16.f;
+    p->seed = 0; p->stream_id = 0; p->forced_rng = 0;
+    p->depth_full_scale_mm = 10000;
+}
+
+int32_t fos_abi_version(void) { return FOS_ABI_VERSION; }
+
+fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
+{
+    g_create_error.clear();
+    if (width < 1 || height < 1 || width > 16384 || height > 16384) {
+        fail(nullptr, FOS_ERR_INVALID_ARG, "width and height must be in 1..16384");
+        return nullptr;
+    }
+    std::string why;
+    if (validate_params(params, why) != FOS_OK) {
+        fail(nullptr, FOS_ERR_INVALID_ARG, why);
+        return nullptr;
+    }
+    fos_ctx* c = new fos_ctx();
+    c->W = width; c->H = height;
+    c->P = int64_t(width) * height;
+    c->plane = round_up(c->P, 128);
+    c->prm = *params;
+    auto bail = [&](const char* what, cudaError_t e) -> fos_ctx* {
+        cuda_fail(nullptr, what, e);
+        free_all(c);
+        delete c;
+        return nullptr;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail("cudaGetDevice", e);
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
+    if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
+    const size_t pl = size_t(c->plane);
+    if (gmm_on(c)) {
+        const size_t n = size_t(gmm_planes(params->K_rgb, params->K_d)) * pl * sizeof(float);
+        if ((e = cudaMalloc(&c->gmm, n)) != cudaSuccess) return bail("cudaMalloc(gmm)", e);
+    }
+    if (pbas_on(c)) {
+        const size_t N = size_t(params->N);
+        if ((e = cudaMalloc(&c->samp, 4 * N * pl * 2)) != cudaSuccess) return bail("cudaMalloc(samples)", e);
+        if ((e = cudaMalloc(&c->Dq, 4 * N * pl * 2)) != cudaSuccess) return bail("cudaMalloc(D)", e);
+        if ((e = cudaMalloc(&c->R, 4 * pl * 4)) != cudaSuccess) return bail("cudaMalloc(R)", e);
+        if ((e = cudaMalloc(&c->T, 4 * pl * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
+        if ((e = cudaMalloc(&c->S, 4 * pl * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
+        if ((e = cudaMalloc(&c->req, pl * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
+    }
+    if ((e = cudaMalloc(&c->aux, 12 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
+    if ((e = cudaMemset(c->aux, 0, 12 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
+    return c;
+}
+
+void fos_destroy(fos_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamSynchronize(ctx->copy_stream);
+    free_all(ctx);
+    delete ctx;
+}
+
+const char* fos_last_error(const fos_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+fos_status fos_reset(fos_ctx* ctx)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    ctx->t = 0;
+    return FOS_OK;
+}
+
+int64_t fos_frame_index(const fos_ctx* ctx) { return ctx ? ctx->t : -1; }
+
+fos_status fos_process_frame_device(fos_ctx* ctx, const uint8_t* d_rgb, const uint16_t* d_depth,
+                                    uint8_t* d_mask_gmm, uint8_t* d_mask_pbas, void* stream)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    return process_device(ctx, d_rgb, d_depth, d_mask_gmm, d_mask_pbas, static_cast<cudaStream_t>(stream));
+}
+
+fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8_t* d_rgb,
+                                     const uint16_t* d_depth, uint8_t* d_mask_gmm,
+                                     uint8_t* d_mask_pbas, void* stream)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
+    const int64_t P = ctx->P;
+    for (int32_t f = 0; f < n_frames; ++f) {
+        fos_status st = process_device(ctx, d_rgb + f * P * 3, d_depth + f * P,
+                                       d_mask_gmm ? d_mask_gmm + f * P : nullptr,
+                                       d_mask_pbas ? d_mask_pbas + f * P : nullptr,
+                                       static_cast<cudaStream_t>(stream));
+        if (st != FOS_OK) return st;
+    }
+    return FOS_OK;
+}
+
+fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t* rgb,
+                                   const uint16_t* depth, uint8_t* mask_gmm, uint8_t* mask_pbas)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
+    if (n_frames > 0 && (!rgb || !depth)) return fail(ctx, FOS_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
+    if (gmm_on(ctx) && !mask_gmm && n_frames > 0) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_gmm must be non-NULL");
+    if (pbas_on(ctx) && !mask_pbas && n_frames > 0) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_pbas must be non-NULL");
+    fos_status st = ensure_staging(ctx);
+    if (st != FOS_OK) return st;
+    const size_t P = size_t(ctx->P);
+    for (int32_t f = 0; f < n_frames; ++f) {
+        const int b = f & 1;
+        FOS_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[b], 0));
+        FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_rgb[b], rgb + f * P * 3, P * 3, cudaMemcpyHostToDevice, ctx->copy_stream));
+        FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_depth[b], depth + f * P, P * 2, cudaMemcpyHostToDevice, ctx->copy_stream));
+        FOS_TRY(ctx, cudaEventRecord(ctx->ev_in[b], ctx->copy_stream));
+        FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[b], 0));
+        st = process_device(ctx, ctx->h_rgb[b], ctx->h_depth[b], ctx->h_mg[b], ctx->h_mp[b], ctx->stream);
+        if (st != FOS_OK) return st;
+        if (gmm_on(ctx))
+            FOS_TRY(ctx, cudaMemcpyAsync(mask_gmm + f * P, ctx->h_mg[b], P, cudaMemcpyDeviceToHost, ctx->stream));
+        if (pbas_on(ctx))
+            FOS_TRY(ctx, cudaMemcpyAsync(mask_pbas + f * P, ctx->h_mp[b], P, cudaMemcpyDeviceToHost, ctx->stream));
+        FOS_TRY(ctx, cudaEventRecord(ctx->ev_done[b], ctx->stream));
+    }
+    FOS_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return FOS_OK;
+}
+
+fos_status fos_process_frame2(fos_ctx* ctx, const uint8_t* rgb, const uint16_t* depth,
+                              uint8_t* mask_gmm, uint8_t* mask_pbas)
+{
+    return fos_process_frames_host(ctx, 1, rgb, depth, mask_gmm, mask_pbas);
+}
+
+fos_status fos_process_frame(fos_ctx* ctx, const uint8_t* rgb, const uint16_t* depth, uint8_t* mask_out)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    if (!mask_out) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_out must be non-NULL");
+    fos_status st = ensure_staging(ctx);
+    if (st != FOS_OK) return st;
+    // the mask of the method not returned goes to the context's staging buffer
+    if (gmm_on(ctx)) {
+        if (!pbas_on(ctx)) return fos_process_frames_host(ctx, 1, rgb, depth, mask_out, nullptr);
+        std::vector<uint8_t> unused(size_t(ctx->P));
+        return fos_process_frames_host(ctx, 1, rgb, depth, mask_out, unused.data());
+    }
+    return fos_process_frames_host(ctx, 1, rgb, depth, nullptr, mask_out);
+}
+
+fos_status fos_state_size(const fos_ctx* ctx, size_t* bytes)
+{
+    if (!ctx || !bytes) return FOS_ERR_INVALID_ARG;
+    *bytes = sizeof(fos_state_header) + gmm_bytes(ctx) + pbas_bytes(ctx);
+    return FOS_OK;
+}
+
+fos_status fos_get_state(fos_ctx* ctx, void* host_buf, size_t bytes)
+{
+    if (!ctx || !host_buf) return FOS_ERR_INVALID_ARG;
+    size_t need;
+    fos_state_size(ctx, &need);
+    if (bytes < need) return fail(ctx, FOS_ERR_INVALID_ARG, "state buffer too small");
+    FOS_TRY(ctx, cudaDeviceSynchronize());
+    uint8_t* out = static_cast<uint8_t*>(host_buf);
+    fos_state_header h{};
+    h.magic = 0x53534F46u; h.abi_version = FOS_ABI_VERSION;
+    h.width = ctx->W; h.height = ctx->H; h.methods = ctx->prm.methods;
+    h.K_rgb = ctx->prm.K_rgb; h.K_d = ctx->prm.K_d; h.N = ctx->prm.N;
+    h.frame_index = ctx->t; h.gmm_bytes = gmm_bytes(ctx); h.pbas_bytes = pbas_bytes(ctx);
+    std::memcpy(out, &h, sizeof h);
+    out += sizeof h;
+    const size_t P = size_t(ctx->P), pl = size_t(ctx->plane);
+    if (gmm_on(ctx)) {
+        const size_t np = size_t(gmm_planes(ctx->prm.K_rgb, ctx->prm.K_d));
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->gmm, pl * 4, P * 4, np, cudaMemcpyDeviceToHost));
+        out += np * P * 4;
+    }
+    if (pbas_on(ctx)) {
+        const size_t N4 = 4 * size_t(ctx->prm.N);
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * 2, ctx->samp, pl * 2, P * 2, N4, cudaMemcpyDeviceToHost));
+        out += N4 * P * 2;
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * 2, ctx->Dq, pl * 2, P * 2, N4, cudaMemcpyDeviceToHost));
+        out += N4 * P * 2;
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->R, pl * 4, P * 4, 4, cudaMemcpyDeviceToHost));
+        out += 4 * P * 4;
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->T, pl * 4, P * 4, 4, cudaMemcpyDeviceToHost));
+        out += 4 * P * 4;
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->S, pl * 4, P * 4, 4, cudaMemcpyDeviceToHost));
+        out += 4 * P * 4;
+        if (ctx->t > 0) {
+            FOS_TRY(ctx, cudaMemcpy(out, ctx->aux + ((ctx->t - 1) & 1) * 4, 32, cudaMemcpyDeviceToHost));
+        } else {
+            std::memset(out, 0, 32);
+        }
+    }
+    return FOS_OK;
+}
+
+fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes)
+{
+    if (!ctx || !host_buf) return FOS_ERR_INVALID_ARG;
+    size_t need;
+    fos_state_size(ctx, &need);
+    if (bytes < need) return fail(ctx, FOS_ERR_INVALID_ARG, "state buffer too small");
+    const uint8_t* in = static_cast<const uint8_t*>(host_buf);
+    fos_state_header h;
+    std::memcpy(&h, in, sizeof h);
+    if (h.magic != 0x53534F46u || h.width != ctx->W || h.height != ctx->H ||
+        h.methods != ctx->prm.methods || h.K_rgb != ctx->prm.K_rgb || h.K_d != ctx->prm.K_d ||
+        h.N != ctx->prm.N || h.frame_index < 0)
+        return fail(ctx, FOS_ERR_INVALID_ARG, "state blob does not match this context");
+    in += sizeof h;
+    FOS_TRY(ctx, cudaDeviceSynchronize());
+    const size_t P = size_t(ctx->P), pl = size_t(ctx->plane);
+    if (gmm_on(ctx)) {
+        const size_t np = size_t(gmm_planes(ctx->prm.K_rgb, ctx->prm.K_d));
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->gmm, pl * 4, in, P * 4, P * 4, np, cudaMemcpyHostToDevice));
+        in += np * P * 4;
+    }
+    if (pbas_on(ctx)) {
+        const size_t N4 = 4 * size_t(ctx->prm.N);
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->samp, pl * 2, in, P * 2, P * 2, N4, cudaMemcpyHostToDevice));
+        in += N4 * P * 2;
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->Dq, pl * 2, in, P * 2, P * 2, N4, cudaMemcpyHostToDevice));
+        in += N4 * P * 2;
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->R, pl * 4, in, P * 4, P * 4, 4, cudaMemcpyHostToDevice));
+        in += 4 * P * 4;
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->T, pl * 4, in, P * 4, P * 4, 4, cudaMemcpyHostToDevice));
+        in += 4 * P * 4;
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->S, pl * 4, in, P * 4, P * 4, 4, cudaMemcpyHostToDevice));
+        in += 4 * P * 4;
+        // gsum of the last frame goes where the next frame reads it; the other
+        // buffer is the next frame's accumulator and starts at zero
+        const int64_t t = h.frame_index;
+        unsigned long long g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (t > 0) std::memcpy(g + ((t - 1) & 1) * 4, in, 32);
+        FOS_TRY(ctx, cudaMemcpy(ctx->aux, g, sizeof g, cudaMemcpyHostToDevice));
+    }
+    ctx->t = h.frame_index;
+    return FOS_OK;
+}
+
+fos_status fos_set_timing(fos_ctx* ctx, uint32_t kernel_mask)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    ctx->timing_mask = kernel_mask;
+    return FOS_OK;
+}
+
+fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
+{
+    if (!ctx || !out) return FOS_ERR_INVALID_ARG;
+    for (int k = 0; k < FOS_KERNEL_COUNT; ++k) { out[k].launches = 0; out[k].total_ms = 0.0; }
+    for (const TimedLaunch& tl : ctx->timed) {
+        FOS_TRY(ctx, cudaEventSynchronize(tl.stop));
+        float ms = 0.f;
+        FOS_TRY(ctx, cudaEventElapsedTime(&ms, tl.start, tl.stop));
+        out[tl.kind].launches += 1;
+        out[tl.kind].total_ms += ms;
+    }
+    ctx->timed.clear();
+    ctx->ev_used = 0;
+    return FOS_OK;
+}
+
+fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4])
+{
+    if (!ctx || !out) return FOS_ERR_INVALID_ARG;
+    FOS_TRY(ctx, cudaDeviceSynchronize());
+    unsigned long long c[4];
+    FOS_TRY(ctx, cudaMemcpy(c, ctx->aux + 8, sizeof c, cudaMemcpyDeviceToHost));
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = ctx->frames_since_counters;
+    FOS_TRY(ctx, cudaMemset(ctx->aux + 8, 0, 4 * sizeof(unsigned long long)));
+    ctx->frames_since_counters = 0;
+    return FOS_OK;
+}
+
+}  // extern "C"

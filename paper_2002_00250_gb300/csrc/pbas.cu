@@ -1,0 +1,454 @@
+// pbas.cu -- PBAS classify-and-update over R, G, B and depth (paper Sec. 3.2).
+//
+// Each sample holds R, G, B and D; each channel is processed separately with
+// its own decision threshold R(x), learning parameter T(x) and minimal-
+// distance record D(x) (base method: Hofmann et al., cited by the paper); the
+// depth channel only where the depth reading is valid; the pixel is
+// foreground if any processed channel is.  Two launches per frame realise the
+// two-phase semantics (every pixel is classified against the model of the
+// previous frame, then the neighbour updates land):
+//   classify : stage the frame tile plus a 1-pixel halo in shared memory,
+//              Sobel gradient per channel, distance to the N samples, own
+//              update, R/T/D update, neighbour-update request, mask, and the
+//              per-channel gradient sums for the next frame's weight;
+//   neighbour: every pixel gathers the requests of its 8 neighbours that point
+//              at it and writes its own (value, gradient) into the slots asked
+//              for.
+// Arithmetic is IEEE single precision with every operation rounded once
+// (explicit _rn intrinsics, no contraction), so results are bit-exact against
+// a plain C implementation of the same steps.
+#include "fos_internal.h"
+#include "philox.cuh"
+
+namespace fos {
+namespace {
+
+// Neighbour directions N, NE, E, SE, S, SW, W, NW (x to the right, y down).
+__host__ __device__ constexpr int dir_dx(int j) { return j == 0 || j == 4 ? 0 : (j < 4 ? 1 : -1); }
+__host__ __device__ constexpr int dir_dy(int j) { return j == 2 || j == 6 ? 0 : (j < 2 || j == 7 ? -1 : 1); }
+
+__device__ __forceinline__ uint32_t depth_to_u8(uint32_t d, uint32_t fs)
+{
+    if (d == 0) return 0;
+    uint32_t q = (d * 255u + (fs >> 1)) / fs;
+    return q < 1u ? 1u : (q > 255u ? 255u : q);
+}
+
+template <int PX, int TY>
+struct Geo {
+    static constexpr int TW = 32 * PX;       // tile width (pixels)
+    static constexpr int SW = TW + 2;        // staged width with halo
+    static constexpr int SH = TY + 2;        // staged height with halo
+    static constexpr int SWP = (SW + 3) & ~3;
+    static constexpr int CH = SH * SWP;      // bytes per staged channel
+};
+
+// Stage the tile plus a 1-pixel halo, edge-clamped, as 4 channel planes
+// (R, G, B, depth rescaled to 8 bits; 0 = invalid depth).
+template <int PX, int TY>
+__device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, uint8_t* sm)
+{
+    using G = Geo<PX, TY>;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int idx = tid; idx < G::SH * G::SW; idx += 32 * TY) {
+        const int r = idx / G::SW, col = idx - r * G::SW;
+        const int gx = min(max(x0 - 1 + col, 0), a.W - 1);
+        const int gy = min(max(y0 - 1 + r, 0), a.H - 1);
+        const int64_t p = int64_t(gy) * a.W + gx;
+        const int o = r * G::SWP + col;
+        sm[o] = a.rgb[3 * p];
+        sm[G::CH + o] = a.rgb[3 * p + 1];
+        sm[2 * G::CH + o] = a.rgb[3 * p + 2];
+        sm[3 * G::CH + o] = uint8_t(depth_to_u8(a.depth[p], a.depth_fs));
+    }
+}
+
+// Gradient magnitude: 3x3 Sobel, |gx| + |gy|, >> 3, clamped to 255.
+__device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int c)
+{
+    const int a00 = s[(r - 1) * swp + c - 1], a01 = s[(r - 1) * swp + c], a02 = s[(r - 1) * swp + c + 1];
+    const int a10 = s[r * swp + c - 1], a12 = s[r * swp + c + 1];
+    const int a20 = s[(r + 1) * swp + c - 1], a21 = s[(r + 1) * swp + c], a22 = s[(r + 1) * swp + c + 1];
+    const int gx = (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
+    const int gy = (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
+    const int m = (abs(gx) + abs(gy)) >> 3;
+    return uint32_t(m > 255 ? 255 : m);
+}
+
+template <int PX>
+__device__ __forceinline__ void ld16(const uint16_t* p, uint32_t (&o)[PX])
+{
+    if constexpr (PX == 4) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        o[0] = v.x & 0xFFFFu; o[1] = v.x >> 16; o[2] = v.y & 0xFFFFu; o[3] = v.y >> 16;
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int PX>
+__device__ __forceinline__ void ldf(const float* p, float (&o)[PX])
+{
+    if constexpr (PX == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int PX>
+__device__ __forceinline__ void stf(float* p, const float (&o)[PX])
+{
+    if constexpr (PX == 4) *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    else *p = o[0];
+}
+
+template <int PX>
+__device__ __forceinline__ void ldu(const uint32_t* p, uint32_t (&o)[PX])
+{
+    if constexpr (PX == 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        o[0] = *p;
+    }
+}
+
+template <int PX>
+__device__ __forceinline__ void stu(uint32_t* p, const uint32_t (&o)[PX])
+{
+    if constexpr (PX == 4) *reinterpret_cast<uint4*>(p) = make_uint4(o[0], o[1], o[2], o[3]);
+    else *p = o[0];
+}
+
+// Block-wide sum of NV per-thread counters, one atomicAdd per counter per block.
+template <int TY, int NV>
+__device__ __forceinline__ void block_add(uint32_t (&v)[NV], unsigned long long* const (&dst)[NV])
+{
+    __shared__ uint32_t red[NV][TY];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        uint32_t s = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if (threadIdx.x == 0) red[q][threadIdx.y] = s;
+    }
+    __syncthreads();
+    if (threadIdx.y == 0 && threadIdx.x < NV) {
+        unsigned long long s = 0;
+#pragma unroll
+        for (int w = 0; w < TY; ++w) s += red[threadIdx.x][w];
+        if (s) atomicAdd(dst[threadIdx.x], s);
+    }
+}
+
+struct Draws {
+    bool coin1, coin2;
+    uint32_t k1, j, k2;
+};
+
+// Random draws for pixel p, frame t, channel c: Philox4x32-10 with counter
+// (p, t, c, 0) and key (seed, stream_id).  Words 0 and 2 give the two coins
+// (24-bit uniform < 1/T), word 1 the own slot, word 3 the direction (3 bits)
+// and the neighbour slot (29 bits).
+__device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c, float prob, int N)
+{
+    Draws d;
+    if (a.forced) {
+        d.coin1 = d.coin2 = true;
+        d.k1 = a.t % uint32_t(N);
+        d.j = a.t % 8u;
+        d.k2 = (a.t + 1u) % uint32_t(N);
+        return d;
+    }
+    const uint4 u = philox4x32_10(make_uint4(p, a.t, c, 0u), make_uint2(a.seed, a.stream_id));
+    const float two_m24 = 5.9604644775390625e-8f;
+    d.coin1 = __fmul_rn(__uint2float_rn(u.x >> 8), two_m24) < prob;
+    d.k1 = __umulhi(u.y, uint32_t(N));
+    d.coin2 = __fmul_rn(__uint2float_rn(u.z >> 8), two_m24) < prob;
+    d.j = u.w >> 29;
+    d.k2 = uint32_t((uint64_t(u.w & 0x1FFFFFFFu) * uint64_t(N)) >> 29);
+    return d;
+}
+
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
+{
+    using G = Geo<PX, TY>;
+    __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    const int N = NT > 0 ? NT : a.N;
+    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
+    stage_input<PX, TY>(a, x0, y0, sm);
+    __syncthreads();
+
+    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
+    const int x = x0 + lx0, y = y0 + ly;
+    bool inb[PX];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) inb[i] = (y < a.H) && (x + i < a.W);
+    const int64_t p0 = int64_t(y) * a.W + x;
+    const bool vec = (PX == 4) && inb[0];  // W % 4 == 0 on this path: all PX in frame
+
+    const float omr = __fsub_rn(1.0f, a.R_incdec), opr = __fadd_rn(1.0f, a.R_incdec);
+    const float n16 = __int2float_rn(16 * N);
+
+    uint32_t reqw[PX];
+    bool anyfg[PX];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) { reqw[i] = 0; anyfg[i] = false; }
+    uint32_t cnt6[6] = {0, 0, 0, 0, 0, 0};  // gsum R,G,B,D; own updates; requests
+
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+        // gradient weight: alpha_g / mean gradient magnitude of the previous frame
+        float mean = __fdiv_rn(__ull2float_rn(a.gsum_prev[c]), __ll2float_rn(a.P));
+        mean = fmaxf(mean, 1.0f);
+        const float wgc = __fdiv_rn(a.alpha_g, mean);
+        uint32_t gsc = 0;
+        uint32_t v[PX], g[PX];
+        bool act[PX];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            const int col = lx0 + i + 1;
+            v[i] = sm[c * G::CH + (ly + 1) * G::SWP + col];
+            g[i] = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
+            act[i] = inb[i] && (c < 3 || sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0);
+            if (inb[i]) gsc += g[i];
+            any |= act[i];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cnt6[q] += (q == c) ? gsc : 0u;
+        if (!any) continue;
+
+        float Rv[PX], Tv[PX];
+        uint32_t Sv[PX];
+        const int64_t pc = int64_t(c) * a.plane + p0;
+        if (vec) {
+            ldf<PX>(a.R + pc, Rv);
+            ldf<PX>(a.T + pc, Tv);
+            ldu<PX>(a.S + pc, Sv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PX; ++i) {
+                Rv[i] = inb[i] ? a.R[pc + i] : 0.f;
+                Tv[i] = inb[i] ? a.T[pc + i] : 1.f;
+                Sv[i] = inb[i] ? a.S[pc + i] : 0u;
+            }
+        }
+
+        int cnt[PX];
+        float dmin[PX];
+#pragma unroll
+        for (int i = 0; i < PX; ++i) { cnt[i] = 0; dmin[i] = INFINITY; }
+        const uint16_t* sp = a.samp + int64_t(c) * N * a.plane + p0;
+#pragma unroll(NT > 0 ? NT : 4)
+        for (int k = 0; k < N; ++k) {
+            uint32_t s[PX];
+            if (vec) {
+                ld16<PX>(sp + int64_t(k) * a.plane, s);
+            } else {
+#pragma unroll
+                for (int i = 0; i < PX; ++i) s[i] = inb[i] ? sp[int64_t(k) * a.plane + i] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < PX; ++i) {
+                const int dv = abs(int(v[i]) - int(s[i] & 0xFFu));
+                const int dg = abs(int(g[i]) - int(s[i] >> 8));
+                const float dist = __fadd_rn(__fmul_rn(wgc, __int2float_rn(dg)), __int2float_rn(dv));
+                cnt[i] += dist < Rv[i] ? 1 : 0;
+                dmin[i] = fminf(dmin[i], dist);
+            }
+        }
+
+        const float Rlo = c < 3 ? a.R_lower_rgb : a.R_lower_d;
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if (!act[i]) continue;
+            const bool fg = cnt[i] < a.n_min;
+            anyfg[i] |= fg;
+            Draws d{false, false, 0u, 0u, 0u};
+            if (!fg) {
+                const float prob = __fdiv_rn(1.0f, Tv[i]);
+                d = draws(a, uint32_t(p0 + i), uint32_t(c), prob, N);
+                if (d.coin1) {
+                    const int64_t o = (int64_t(c) * N + d.k1) * a.plane + p0 + i;
+                    a.samp[o] = uint16_t(v[i] | (g[i] << 8));
+                    const float q16 = __fmul_rn(dmin[i], 16.0f);
+                    const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
+                    Sv[i] = Sv[i] + q - uint32_t(a.Dq[o]);
+                    a.Dq[o] = uint16_t(q);
+                    cnt6[4] += 1;
+                }
+            }
+            const float dbar = fmaxf(__fdiv_rn(__uint2float_rn(Sv[i]), n16), a.eps_d);
+            const float Rs = __fmul_rn(dbar, a.R_scale);
+            float Rn = Rv[i] > Rs ? __fmul_rn(Rv[i], omr) : __fmul_rn(Rv[i], opr);
+            Rv[i] = Rn < Rlo ? Rlo : Rn;
+            float Tn = fg ? __fadd_rn(Tv[i], __fdiv_rn(a.T_inc, dbar))
+                          : __fsub_rn(Tv[i], __fdiv_rn(a.T_dec, dbar));
+            Tn = Tn < a.T_lower ? a.T_lower : Tn;
+            Tv[i] = Tn > a.T_upper ? a.T_upper : Tn;
+            if (!fg && d.coin2) {
+                reqw[i] |= (1u + d.j * uint32_t(N) + d.k2) << (8 * c);
+                cnt6[5] += 1;
+            }
+        }
+        if (vec) {
+            stf<PX>(a.R + pc, Rv);
+            stf<PX>(a.T + pc, Tv);
+            stu<PX>(a.S + pc, Sv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PX; ++i)
+                if (inb[i]) { a.R[pc + i] = Rv[i]; a.T[pc + i] = Tv[i]; a.S[pc + i] = Sv[i]; }
+        }
+    }
+
+    if (vec) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int i = 0; i < PX; ++i) m |= (anyfg[i] ? 255u : 0u) << (8 * i);
+        if (a.vec_ok) {
+            *reinterpret_cast<uint32_t*>(a.mask + p0) = m;
+        } else {
+#pragma unroll
+            for (int i = 0; i < PX; ++i) a.mask[p0 + i] = anyfg[i] ? 255 : 0;
+        }
+        stu<PX>(a.req + p0, reqw);
+    } else {
+#pragma unroll
+        for (int i = 0; i < PX; ++i)
+            if (inb[i]) { a.mask[p0 + i] = anyfg[i] ? 255 : 0; a.req[p0 + i] = reqw[i]; }
+    }
+
+    unsigned long long* const dst[6] = {a.gsum_cur, a.gsum_cur + 1, a.gsum_cur + 2, a.gsum_cur + 3,
+                                        a.counters, a.counters + 2};
+    block_add<TY, 6>(cnt6, dst);
+}
+
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY) pbas_neighbour_kernel(const PbasArgs a)
+{
+    using G = Geo<PX, TY>;
+    __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    __shared__ uint32_t sreq[G::SH * G::SW];
+    const int N = NT > 0 ? NT : a.N;
+    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
+    stage_input<PX, TY>(a, x0, y0, sm);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int idx = tid; idx < G::SH * G::SW; idx += 32 * TY) {
+        const int r = idx / G::SW, col = idx - r * G::SW;
+        const int gx = x0 - 1 + col, gy = y0 - 1 + r;
+        const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
+        sreq[idx] = in ? a.req[int64_t(gy) * a.W + gx] : 0u;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid < 4) {
+        // this frame's classify pass has consumed the previous frame's sums;
+        // the buffer becomes the next frame's accumulator
+        a.gsum_prev[tid] = 0ull;
+    }
+    __syncthreads();
+
+    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
+    const int x = x0 + lx0, y = y0 + ly;
+    uint32_t applied[1] = {0};
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+        if (y >= a.H || x + i >= a.W) continue;
+        const int col = lx0 + i + 1;
+        const int64_t p = int64_t(y) * a.W + x + i;
+        const bool dvalid = sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0;
+        uint32_t cached[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t r = sreq[(ly + 1 - dir_dy(j)) * G::SW + (col - dir_dx(j))];
+            if (r == 0) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint32_t b = (r >> (8 * c)) & 0xFFu;
+                if (b == 0) continue;
+                const uint32_t code = b - 1u;
+                const uint32_t jj = code / uint32_t(N);
+                if (jj != uint32_t(j) || (c == 3 && !dvalid)) continue;
+                const uint32_t k2 = code - jj * uint32_t(N);
+                if (cached[c] == 0xFFFFFFFFu) {
+                    const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
+                    cached[c] = v | (sobel(sm + c * G::CH, G::SWP, ly + 1, col) << 8);
+                }
+                a.samp[(int64_t(c) * N + k2) * a.plane + p] = uint16_t(cached[c]);
+                applied[0] += 1;
+            }
+        }
+    }
+    unsigned long long* const dst[1] = {a.counters + 1};
+    block_add<TY, 1>(applied, dst);
+}
+
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
+{
+    using G = Geo<PX, TY>;
+    __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    const int N = NT > 0 ? NT : a.N;
+    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
+    stage_input<PX, TY>(a, x0, y0, sm);
+    __syncthreads();
+    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
+    const int x = x0 + lx0, y = y0 + ly;
+    uint32_t gs[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+        if (y >= a.H || x + i >= a.W) continue;
+        const int col = lx0 + i + 1;
+        const int64_t p = int64_t(y) * a.W + x + i;
+#pragma unroll 1
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
+            const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
+            gs[c] += g;
+            const uint16_t sv = uint16_t(v | (g << 8));
+            for (int k = 0; k < N; ++k) {
+                a.samp[(int64_t(c) * N + k) * a.plane + p] = sv;
+                a.Dq[(int64_t(c) * N + k) * a.plane + p] = 0;
+            }
+            a.R[int64_t(c) * a.plane + p] = c < 3 ? a.R_lower_rgb : a.R_lower_d;
+            a.T[int64_t(c) * a.plane + p] = a.T_lower;
+            a.S[int64_t(c) * a.plane + p] = 0u;
+        }
+        a.mask[p] = 0;
+        a.req[p] = 0u;
+    }
+    unsigned long long* const dst[4] = {a.gsum_cur, a.gsum_cur + 1, a.gsum_cur + 2, a.gsum_cur + 3};
+    block_add<TY, 4>(gs, dst);
+}
+
+template <int PX, int TY>
+dim3 grid_for(const PbasArgs& a)
+{
+    return dim3(unsigned((a.W + 32 * PX - 1) / (32 * PX)), unsigned((a.H + TY - 1) / TY));
+}
+
+}  // namespace
+
+#define FOS_PBAS_DISPATCH(KERNEL)                                                       \
+    if (a.P == 0) return kLaunchOk;                                                     \
+    if (a.vec_ok) {                                                                     \
+        constexpr int PX = 4, TY = 4;                                                   \
+        if (a.N == 20) KERNEL<20, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a); \
+        else KERNEL<0, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a);          \
+    } else {                                                                            \
+        constexpr int PX = 1, TY = 8;                                                   \
+        if (a.N == 20) KERNEL<20, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a); \
+        else KERNEL<0, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a);          \
+    }                                                                                   \
+    return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+
+LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s) { FOS_PBAS_DISPATCH(pbas_init_kernel) }
+LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s) { FOS_PBAS_DISPATCH(pbas_classify_kernel) }
+LaunchResult launch_pbas_neighbour(const PbasArgs& a, cudaStream_t s) { FOS_PBAS_DISPATCH(pbas_neighbour_kernel) }
+
+#undef FOS_PBAS_DISPATCH
+
+}  // namespace fos

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the C ABI in include/fos.h (argument marshalling only).
+
+Every step of the segmentation runs in the CUDA library ``libfos.so``; this
+module converts numpy arrays / torch tensors to pointers and back.  There is
+no CPU fallback: if the library cannot be loaded, importing the binding
+raises.  Device tensors are torch CUDA tensors; streams are torch streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfos.so")
+
+METHOD_GMM = 1
+METHOD_PBAS = 2
+KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_NEIGHBOUR, KERNEL_INIT = 0, 1, 2, 3
+KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_neighbour", "init")
+STATUS = {0: "FOS_OK", 1: "FOS_ERR_INVALID_ARG", 2: "FOS_ERR_CUDA", 3: "FOS_ERR_OOM",
+          4: "FOS_ERR_TIMEOUT", 5: "FOS_ERR_BUDGET", 6: "FOS_ERR_STATE", 7: "FOS_ERR_UNSUPPORTED"}
+
+
+class FosError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of fos_params (include/fos.h)."""
+    _fields_ = [("methods", ctypes.c_uint32),
+                ("K_rgb", ctypes.c_int32), ("K_d", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("lambda_", ctypes.c_float),
+                ("w_depth", ctypes.c_float), ("T_bg", ctypes.c_float),
+                ("v_init_rgb", ctypes.c_float), ("v_init_d", ctypes.c_float),
+                ("v_min_rgb", ctypes.c_float), ("v_min_d", ctypes.c_float),
+                ("N", ctypes.c_int32), ("n_min", ctypes.c_int32),
+                ("R_lower_rgb", ctypes.c_float), ("R_lower_d", ctypes.c_float),
+                ("R_scale", ctypes.c_float), ("R_incdec", ctypes.c_float),
+                ("T_lower", ctypes.c_float), ("T_upper", ctypes.c_float),
+                ("T_inc", ctypes.c_float), ("T_dec", ctypes.c_float),
+                ("alpha_g", ctypes.c_float), ("eps_d", ctypes.c_float),
+                ("seed", ctypes.c_uint32), ("stream_id", ctypes.c_uint32),
+                ("forced_rng", ctypes.c_int32), ("depth_full_scale_mm", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class StateHeader(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("abi_version", ctypes.c_uint32),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("methods", ctypes.c_uint32), ("K_rgb", ctypes.c_int32),
+                ("K_d", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("frame_index", ctypes.c_int64), ("gmm_bytes", ctypes.c_uint64),
+                ("pbas_bytes", ctypes.c_uint64)]
+
+
+class KernelTiming(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+# Every exported function and its ctypes signature (checked against the header
+# by the tests).
+_vp, _i32, _i64, _u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+_st = ctypes.c_int
+SIGNATURES = {
+    "fos_default_params": (None, [ctypes.POINTER(Params)]),
+    "fos_abi_version": (_i32, []),
+    "fos_create": (_vp, [_i32, _i32, ctypes.POINTER(Params)]),
+    "fos_destroy": (None, [_vp]),
+    "fos_last_error": (ctypes.c_char_p, [_vp]),
+    "fos_reset": (_st, [_vp]),
+    "fos_frame_index": (_i64, [_vp]),
+    "fos_process_frame": (_st, [_vp, _vp, _vp, _vp]),
+    "fos_process_frame2": (_st, [_vp, _vp, _vp, _vp, _vp]),
+    "fos_process_frame_device": (_st, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "fos_process_frames_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "fos_process_frames_host": (_st, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "fos_state_size": (_st, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "fos_get_state": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "fos_set_state": (_st, [_vp, _vp, ctypes.c_size_t]),
+    "fos_set_timing": (_st, [_vp, _u32]),
+    "fos_get_timing": (_st, [_vp, ctypes.POINTER(KernelTiming)]),
+    "fos_get_counters": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfos.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    load().fos_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        key = "lambda_" if k == "lambda" else k
+        if not hasattr(p, key):
+            raise KeyError(k)
+        setattr(p, key, v)
+    return p
+
+
+def _ptr(x) -> int | None:
+    """Raw address of a numpy array or torch tensor (None passes NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+@dataclass
+class StateView:
+    """Decoded state blob (numpy views into the host copy)."""
+    header: StateHeader
+    gmm: dict | None
+    pbas: dict | None
+
+
+class Segmenter:
+    """One camera stream: owns a fos_ctx (device-resident GMM and/or PBAS model)."""
+
+    def __init__(self, width: int, height: int, params: Params | None = None, **overrides):
+        self.lib = load()
+        self.params = params if params is not None else default_params(**overrides)
+        if params is not None and overrides:
+            for k, v in overrides.items():
+                setattr(self.params, "lambda_" if k == "lambda" else k, v)
+        self.W, self.H, self.P = width, height, width * height
+        h = self.lib.fos_create(width, height, ctypes.byref(self.params))
+        if not h:
+            raise FosError(1, self.lib.fos_last_error(None).decode())
+        self.h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fos_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, st: int):
+        if st != 0:
+            raise FosError(st, self.lib.fos_last_error(self.h).decode())
+
+    @property
+    def gmm(self) -> bool:
+        return bool(self.params.methods & METHOD_GMM)
+
+    @property
+    def pbas(self) -> bool:
+        return bool(self.params.methods & METHOD_PBAS)
+
+    def reset(self):
+        self._check(self.lib.fos_reset(self.h))
+
+    @property
+    def frame_index(self) -> int:
+        return int(self.lib.fos_frame_index(self.h))
+
+    # -- host frames ---------------------------------------------------------
+    def process_host(self, rgb: np.ndarray, depth: np.ndarray):
+        """Frames from host memory ((n,H,W,3) u8 and (n,H,W) u16, or one frame).
+        Returns (mask_gmm, mask_pbas) numpy arrays (None for a disabled method)."""
+        single = rgb.ndim == 3
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        n = 1 if single else rgb.shape[0]
+        shape = (self.H, self.W) if single else (n, self.H, self.W)
+        assert rgb.size == n * self.P * 3 and depth.size == n * self.P
+        mg = np.empty(shape, np.uint8) if self.gmm else None
+        mp = np.empty(shape, np.uint8) if self.pbas else None
+        self._check(self.lib.fos_process_frames_host(self.h, n, _ptr(rgb), _ptr(depth),
+                                                     _ptr(mg), _ptr(mp)))
+        return mg, mp
+
+    def process_frame(self, rgb, depth, mask_out) -> None:
+        """fos_process_frame: one host frame, the primary method's mask."""
+        self._check(self.lib.fos_process_frame(self.h, _ptr(rgb), _ptr(depth), _ptr(mask_out)))
+
+    # -- device frames -------------------------------------------------------
+    def process_device(self, rgb, depth, mask_gmm=None, mask_pbas=None, stream=None):
+        """Frames already on the device (torch CUDA tensors), asynchronous.
+        rgb (n,H,W,3) or (H,W,3) u8; depth u16 of matching shape; masks u8."""
+        n = 1 if rgb.dim() == 3 else rgb.shape[0]
+        assert rgb.numel() == n * self.P * 3 and depth.numel() == n * self.P
+        self._check(self.lib.fos_process_frames_device(
+            self.h, n, _ptr(rgb), _ptr(depth), _ptr(mask_gmm), _ptr(mask_pbas),
+            _stream_handle(stream)))
+
+    # -- state -----------------------------------------------------------------
+    def state_size(self) -> int:
+        n = ctypes.c_size_t()
+        self._check(self.lib.fos_state_size(self.h, ctypes.byref(n)))
+        return n.value
+
+    def get_state(self) -> np.ndarray:
+        buf = np.empty(self.state_size(), np.uint8)
+        self._check(self.lib.fos_get_state(self.h, _ptr(buf), buf.size))
+        return buf
+
+    def set_state(self, blob: np.ndarray) -> None:
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        self._check(self.lib.fos_set_state(self.h, _ptr(blob), blob.size))
+
+    def decode_state(self, blob: np.ndarray | None = None) -> StateView:
+        return decode_state(self.get_state() if blob is None else blob)
+
+    # -- measurement -------------------------------------------------------------
+    def set_timing(self, kernel_mask: int) -> None:
+        self._check(self.lib.fos_set_timing(self.h, kernel_mask))
+
+    def get_timing(self) -> dict:
+        arr = (KernelTiming * 4)()
+        self._check(self.lib.fos_get_timing(self.h, arr))
+        return {KERNEL_NAMES[k]: (arr[k].launches, arr[k].total_ms) for k in range(4)}
+
+    def get_counters(self) -> dict:
+        arr = (ctypes.c_uint64 * 4)()
+        self._check(self.lib.fos_get_counters(self.h, arr))
+        return dict(own_updates=arr[0], neighbour_writes=arr[1], requests=arr[2], frames=arr[3])
+
+
+def decode_state(blob: np.ndarray) -> StateView:
+    """Split a fos_get_state blob into named planes (layout: include/fos.h)."""
+    hdr = StateHeader.from_buffer_copy(blob[:ctypes.sizeof(StateHeader)].tobytes())
+    off = ctypes.sizeof(StateHeader)
+    P = hdr.width * hdr.height
+    gmm = pbas = None
+    if hdr.methods & METHOD_GMM:
+        Kr, Kd = hdr.K_rgb, hdr.K_d
+        planes = blob[off:off + hdr.gmm_bytes].view(np.float32).reshape(5 * Kr + 3 * Kd, P)
+        off += hdr.gmm_bytes
+        gmm = dict(w_rgb=planes[0:Kr].T, mu_rgb=np.stack([planes[Kr:2 * Kr].T, planes[2 * Kr:3 * Kr].T,
+                                                           planes[3 * Kr:4 * Kr].T], axis=2),
+                   v_rgb=planes[4 * Kr:5 * Kr].T, w_d=planes[5 * Kr:5 * Kr + Kd].T,
+                   mu_d=planes[5 * Kr + Kd:5 * Kr + 2 * Kd].T, v_d=planes[5 * Kr + 2 * Kd:].T)
+    if hdr.methods & METHOD_PBAS:
+        N = hdr.N
+        s = blob[off:off + 4 * N * P * 2].view(np.uint16).reshape(4, N, P)
+        off += 4 * N * P * 2
+        D = blob[off:off + 4 * N * P * 2].view(np.uint16).reshape(4, N, P)
+        off += 4 * N * P * 2
+        R = blob[off:off + 16 * P].view(np.float32).reshape(4, P)
+        off += 16 * P
+        T = blob[off:off + 16 * P].view(np.float32).reshape(4, P)
+        off += 16 * P
+        S = blob[off:off + 16 * P].view(np.uint32).reshape(4, P)
+        off += 16 * P
+        gsum = blob[off:off + 32].view(np.uint64).copy()
+        pbas = dict(sv=(s & 0xFF).astype(np.uint8).transpose(2, 0, 1),
+                    sg=(s >> 8).astype(np.uint8).transpose(2, 0, 1),
+                    sD=D.transpose(2, 0, 1), R=R.T, T=T.T, S=S.T, gsum=gsum)
+    return StateView(hdr, gmm, pbas)

@@ -1,0 +1,127 @@
+"""GMM on the GPU (FP32) against the FP64 oracle, through the C ABI.
+
+Bar: after every frame the parameters agree within 1e-4 relative (abs floor
+1e-6) and the masks are equal, except at pixels where one of the frame's
+discrete decisions (match test, background-set prefix, final score, ranking)
+lies within 1e-5 relative of its threshold; the excluded fraction is
+reported and bounded.
+"""
+import numpy as np
+import pytest
+
+from _helpers import close, oracle_gmm_params, scene
+
+pytestmark = pytest.mark.gpu
+MARGIN = 1e-5
+
+
+def _seg(W, H, **kw):
+    from paper_2002_00250_gb300 import fos
+    kw.setdefault("methods", fos.METHOD_GMM)
+    return fos.Segmenter(W, H, **kw)
+
+
+def _load_oracle(g, st):
+    g.w_rgb[:] = st["w_rgb"]
+    g.mu_rgb[:] = st["mu_rgb"]
+    g.v_rgb[:] = st["v_rgb"]
+    g.w_d[:] = st["w_d"]
+    g.mu_d[:] = st["mu_d"]
+    g.v_d[:] = st["v_d"]
+
+
+def step_parity(orc, W, H, n, seed=0, max_excluded=0.002, **kw):
+    rgb, depth, _ = scene(W, H, n, seed=seed, n_objects=3)
+    seg = _seg(W, H, **kw)
+    g = orc.GMM(W, H, **oracle_gmm_params(seg.params))
+    excluded = 0
+    for t in range(n):
+        if t > 0:
+            _load_oracle(g, seg.decode_state().gmm)
+        mo, margin = g.step(rgb[t], depth[t], want_margin=True)
+        mg, _ = seg.process_host(rgb[t], depth[t])
+        st = seg.decode_state().gmm
+        ok = (margin >= MARGIN).ravel()
+        excluded += int((~ok).sum())
+        np.testing.assert_array_equal(mg.ravel()[ok], mo.ravel()[ok])
+        for name in ("w_rgb", "mu_rgb", "v_rgb", "w_d", "mu_d", "v_d"):
+            good = close(st[name], getattr(g, name))
+            bad = ~good.reshape(good.shape[0], -1).all(axis=1) & ok
+            assert not bad.any(), (t, name, np.flatnonzero(bad)[:5])
+    frac = excluded / (W * H * n)
+    assert frac <= max_excluded, frac
+    return frac
+
+
+def test_step_parity_ragged(orc):
+    # 67 x 45: width not a multiple of 4 (scalar path), several blocks, ragged tail
+    step_parity(orc, 67, 45, 12, alpha=0.05)
+
+
+def test_step_parity_vector_path(orc):
+    step_parity(orc, 128, 40, 12, alpha=0.05, seed=1)
+
+
+@pytest.mark.parametrize("Kr,Kd", [(1, 1), (2, 2), (5, 3), (7, 3), (3, 1)])
+def test_step_parity_component_counts(orc, Kr, Kd):
+    step_parity(orc, 36, 20, 10, alpha=0.05, K_rgb=Kr, K_d=Kd, seed=Kr * 10 + Kd)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (3, 5), (4, 1), (17, 13)])
+def test_tiny_frames(orc, W, H):
+    step_parity(orc, W, H, 6, alpha=0.2, max_excluded=0.05)
+
+
+def test_free_run_480p(orc):
+    # 640 x 480 x 50 frames, paper parameters (alpha = 0.001), device API, no
+    # re-sync: pixels whose oracle margin ever fell below 1e-5 are excluded.
+    import torch
+    from paper_2002_00250_gb300 import fos
+    W, H, n = 640, 480, 50
+    rgb, depth, _ = scene(W, H, n, seed=0)
+    seg = _seg(W, H)
+    g = orc.GMM(W, H, **oracle_gmm_params(seg.params))
+    d_rgb = torch.from_numpy(rgb).cuda()
+    d_dep = torch.from_numpy(depth).cuda()
+    d_mask = torch.empty((n, H, W), dtype=torch.uint8, device="cuda")
+    seg.process_device(d_rgb, d_dep, mask_gmm=d_mask)
+    torch.cuda.synchronize()
+    masks = d_mask.cpu().numpy()
+    bad = np.zeros(W * H, bool)
+    for t in range(n):
+        mo, margin = g.step(rgb[t], depth[t], want_margin=True)
+        bad |= (margin < MARGIN).ravel()
+        ok = ~bad
+        np.testing.assert_array_equal(masks[t].ravel()[ok], mo.ravel()[ok])
+    st = seg.decode_state().gmm
+    for name in ("w_rgb", "mu_rgb", "v_rgb", "w_d", "mu_d", "v_d"):
+        good = close(st[name], getattr(g, name)).reshape(W * H, -1).all(axis=1)
+        assert good[~bad].all(), name
+    assert bad.mean() < 0.01
+    assert masks[1:].mean() > 0  # objects were detected
+
+
+def test_invariants_on_device_state(orc):
+    W, H, n = 96, 64, 20
+    rgb, depth, _ = scene(W, H, n, seed=4)
+    seg = _seg(W, H, alpha=0.05)
+    for t in range(n):
+        seg.process_host(rgb[t], depth[t])
+        st = seg.decode_state().gmm
+        for w, v, vmin in ((st["w_rgb"], st["v_rgb"], 4.0), (st["w_d"], st["v_d"], 0.25)):
+            np.testing.assert_allclose(w.sum(axis=1), 1.0, atol=1e-5)
+            assert (w >= 0).all() and (w <= 1 + 1e-6).all()
+            assert (v >= np.float32(vmin)).all()
+
+
+def test_constant_input_closed_form():
+    W, H, n = 32, 8, 120
+    rgb = np.full((n, H, W, 3), 120, np.uint8)
+    depth = np.full((n, H, W), 2000, np.uint16)
+    seg = _seg(W, H, alpha=0.01)
+    mg, _ = seg.process_host(rgb, depth)
+    assert not mg.any()
+    st = seg.decode_state().gmm
+    np.testing.assert_allclose(st["w_rgb"][:, 0], 1.0, rtol=1e-6)
+    np.testing.assert_allclose(st["v_rgb"][:, 0], max(4.0, 36 * 0.99 ** (n - 1)), rtol=1e-4)
+    assert (st["mu_d"][:, 0] == 51).all()

@@ -1,0 +1,105 @@
+"""PBAS on the GPU against the oracle, through the C ABI: bit-exact.
+
+Masks, samples, D, S, R, T and the gradient sums must equal the oracle's
+after every frame (memcmp-equal arrays), on ragged and vectorised frame
+sizes, with the Philox draws and with the test-only forced draws.
+"""
+import numpy as np
+import pytest
+
+from _helpers import oracle_pbas_params, scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _seg(W, H, **kw):
+    from paper_2002_00250_gb300 import fos
+    kw.setdefault("methods", fos.METHOD_PBAS)
+    return fos.Segmenter(W, H, **kw)
+
+
+def assert_same(st, p, t):
+    for name in ("sv", "sg", "sD", "R", "T", "S"):
+        a, b = st[name], getattr(p, name)
+        if not np.array_equal(a, b):
+            idx = np.argwhere(a != b)[:5]
+            raise AssertionError(f"frame {t}: {name} differs at {idx.tolist()}")
+    np.testing.assert_array_equal(st["gsum"], p.gsum)
+
+
+def run_parity(orc, W, H, n, seed=0, every=1, **kw):
+    rgb, depth, _ = scene(W, H, n, seed=seed, n_objects=3, hole_fraction=0.05)
+    seg = _seg(W, H, **kw)
+    p = orc.PBAS(W, H, **oracle_pbas_params(seg.params))
+    fg = 0
+    for t in range(n):
+        mo = p.step(rgb[t], depth[t])
+        _, mp = seg.process_host(rgb[t], depth[t])
+        np.testing.assert_array_equal(mp, mo, err_msg=f"mask frame {t}")
+        fg += int(mo.astype(bool).sum())
+        if t % every == 0 or t == n - 1:
+            assert_same(seg.decode_state().pbas, p, t)
+    return fg
+
+
+def test_bit_exact_ragged(orc):
+    assert run_parity(orc, 67, 45, 15) > 0
+
+
+def test_bit_exact_vector_path(orc):
+    assert run_parity(orc, 136, 40, 15, seed=2) > 0
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (3, 5), (4, 1), (2, 9), (17, 13)])
+def test_tiny_frames(orc, W, H):
+    run_parity(orc, W, H, 8, seed=W + H)
+
+
+@pytest.mark.parametrize("N", [2, 7, 32])
+def test_other_sample_counts(orc, N):
+    run_parity(orc, 40, 12, 10, N=N, n_min=min(2, N), seed=N)
+
+
+def test_forced_draws_hand_trace(orc):
+    # the oracle's hand-traced 3x3 neighbour pattern, through the GPU
+    rgb = np.empty((2, 3, 3, 3), np.uint8)
+    rgb[0] = 50
+    rgb[1] = 50
+    rgb[1, ..., 0] = 60
+    depth = np.zeros((2, 3, 3), np.uint16)
+    seg = _seg(3, 3, N=2, forced_rng=1)
+    for t in range(2):
+        seg.process_host(rgb[t], depth[t])
+    sv = seg.decode_state().pbas["sv"][:, 0, :].reshape(3, 3, 2)
+    assert (sv[..., 1] == 60).all()
+    want0 = np.full((3, 3), 50)
+    for (x, y) in [(1, 0), (2, 0), (1, 1), (2, 1)]:
+        want0[y, x] = 60
+    np.testing.assert_array_equal(sv[..., 0], want0)
+
+
+def test_forced_draws_parity(orc):
+    run_parity(orc, 33, 21, 12, forced_rng=1, N=5)
+
+
+def test_480p_full_run(orc):
+    # 640 x 480 x 50 frames, both methods in one context via the device API
+    # (the launch configuration the benchmark times); PBAS bit-exact throughout.
+    import torch
+    from paper_2002_00250_gb300 import fos
+    W, H, n = 640, 480, 50
+    rgb, depth, _ = scene(W, H, n, seed=0)
+    seg = fos.Segmenter(W, H)
+    d_rgb = torch.from_numpy(rgb).cuda()
+    d_dep = torch.from_numpy(depth).cuda()
+    mg = torch.empty((n, H, W), dtype=torch.uint8, device="cuda")
+    mp = torch.empty_like(mg)
+    seg.process_device(d_rgb, d_dep, mg, mp)
+    torch.cuda.synchronize()
+    p = orc.PBAS(W, H, **oracle_pbas_params(seg.params))
+    masks = mp.cpu().numpy()
+    for t in range(n):
+        np.testing.assert_array_equal(masks[t], p.step(rgb[t], depth[t]), err_msg=f"frame {t}")
+    assert_same(seg.decode_state().pbas, p, n - 1)
+    c = seg.get_counters()
+    assert c["frames"] == n and c["own_updates"] > 0 and c["neighbour_writes"] > 0
