@@ -76,7 +76,7 @@ typedef struct fos_params {
     float v_init_rgb, v_init_d;/* variance of a new component */
     float v_min_rgb, v_min_d;  /* variance floor */
     /* ---- PBAS (Sec. 3.2) ---- */
-    int32_t N;                 /* samples per pixel, 1..32 (paper: 20) */
+    int32_t N;                 /* samples per pixel, 1..31 (paper: 20) */
     int32_t n_min;             /* matches needed for background */
     float R_lower_rgb, R_lower_d, R_scale, R_incdec;
     float T_lower, T_upper, T_inc, T_dec;

@@ -33,7 +33,9 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 struct fos_ctx {
     int W = 0, H = 0;
-    int64_t P = 0, plane = 0;
+    int64_t P = 0, plane = 0;       // GMM planes: P padded to 128
+    int Wp = 0, spr = 0;            // PBAS: row pitch, 128-pixel segments per row
+    int64_t nseg = 0, pplane = 0;   // PBAS: segments, plane stride (Wp * H)
     fos_params prm{};
     int64_t t = 0;
     int device = 0;
@@ -110,8 +112,9 @@ fos_status validate_params(const fos_params* p, std::string& why)
         }
     }
     if (p->methods & FOS_METHOD_PBAS) {
-        if (p->N < 1 || p->N > 32 || p->n_min < 1 || p->n_min > p->N) {
-            why = "PBAS needs 1 <= n_min <= N <= 32"; return FOS_ERR_INVALID_ARG;
+        // a neighbour request is one byte per channel: 1 + j*N + k2 <= 8N <= 255
+        if (p->N < 1 || p->N > 31 || p->n_min < 1 || p->n_min > p->N) {
+            why = "PBAS needs 1 <= n_min <= N <= 31"; return FOS_ERR_INVALID_ARG;
         }
         if (!(p->T_lower > 0.f) || !(p->T_upper >= p->T_lower) || !(p->eps_d > 0.f) ||
             !(p->R_lower_rgb > 0.f) || !(p->R_lower_d > 0.f) || !(p->R_incdec >= 0.f && p->R_incdec < 1.f)) {
@@ -174,7 +177,8 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
 {
     PbasArgs a{};
     const fos_params& p = c->prm;
-    a.W = c->W; a.H = c->H; a.P = c->P; a.plane = c->plane;
+    a.W = c->W; a.H = c->H; a.P = c->P;
+    a.Wp = c->Wp; a.spr = c->spr; a.nseg = c->nseg; a.plane = c->pplane;
     a.rgb = rgb; a.depth = depth; a.mask = mask;
     a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S; a.req = c->req;
     a.gsum_prev = c->aux + ((c->t + 1) & 1) * 4;  // buffer of frame t-1
@@ -277,6 +281,35 @@ void free_all(fos_ctx* c)
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
 
+// Sample / D planes: blocked device layout <-> unpadded [c][k][P] export layout.
+int64_t blocked_index(const fos_ctx* c, int ch, int k, int x, int y)
+{
+    const int64_t seg = int64_t(y) * c->spr + x / kSeg;
+    return ((int64_t(ch) * c->nseg + seg) * c->prm.N + k) * kSeg + x % kSeg;
+}
+
+void unblock_samples(const fos_ctx* c, const uint16_t* blocked, uint16_t* planes)
+{
+    const int N = c->prm.N;
+    for (int ch = 0; ch < 4; ++ch)
+        for (int k = 0; k < N; ++k)
+            for (int y = 0; y < c->H; ++y)
+                for (int x = 0; x < c->W; ++x)
+                    planes[(int64_t(ch) * N + k) * c->P + int64_t(y) * c->W + x] =
+                        blocked[blocked_index(c, ch, k, x, y)];
+}
+
+void block_samples(const fos_ctx* c, const uint16_t* planes, uint16_t* blocked)
+{
+    const int N = c->prm.N;
+    for (int ch = 0; ch < 4; ++ch)
+        for (int k = 0; k < N; ++k)
+            for (int y = 0; y < c->H; ++y)
+                for (int x = 0; x < c->W; ++x)
+                    blocked[blocked_index(c, ch, k, x, y)] =
+                        planes[(int64_t(ch) * N + k) * c->P + int64_t(y) * c->W + x];
+}
+
 }  // namespace
 
 extern "C" {
@@ -315,6 +348,10 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
     c->W = width; c->H = height;
     c->P = int64_t(width) * height;
     c->plane = round_up(c->P, 128);
+    c->spr = (width + kSeg - 1) / kSeg;
+    c->Wp = c->spr * kSeg;
+    c->nseg = int64_t(c->spr) * height;
+    c->pplane = int64_t(c->Wp) * height;
     c->prm = *params;
     auto bail = [&](const char* what, cudaError_t e) -> fos_ctx* {
         cuda_fail(nullptr, what, e);
@@ -332,13 +369,13 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
         if ((e = cudaMalloc(&c->gmm, n)) != cudaSuccess) return bail("cudaMalloc(gmm)", e);
     }
     if (pbas_on(c)) {
-        const size_t N = size_t(params->N);
-        if ((e = cudaMalloc(&c->samp, 4 * N * pl * 2)) != cudaSuccess) return bail("cudaMalloc(samples)", e);
-        if ((e = cudaMalloc(&c->Dq, 4 * N * pl * 2)) != cudaSuccess) return bail("cudaMalloc(D)", e);
-        if ((e = cudaMalloc(&c->R, 4 * pl * 4)) != cudaSuccess) return bail("cudaMalloc(R)", e);
-        if ((e = cudaMalloc(&c->T, 4 * pl * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
-        if ((e = cudaMalloc(&c->S, 4 * pl * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
-        if ((e = cudaMalloc(&c->req, pl * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
+        const size_t N = size_t(params->N), ns = size_t(c->nseg) * kSeg, pp = size_t(c->pplane);
+        if ((e = cudaMalloc(&c->samp, 4 * N * ns * 2)) != cudaSuccess) return bail("cudaMalloc(samples)", e);
+        if ((e = cudaMalloc(&c->Dq, 4 * N * ns * 2)) != cudaSuccess) return bail("cudaMalloc(D)", e);
+        if ((e = cudaMalloc(&c->R, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(R)", e);
+        if ((e = cudaMalloc(&c->T, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
+        if ((e = cudaMalloc(&c->S, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
+        if ((e = cudaMalloc(&c->req, pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
     }
     if ((e = cudaMalloc(&c->aux, 12 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
     if ((e = cudaMemset(c->aux, 0, 12 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
@@ -473,16 +510,17 @@ fos_status fos_get_state(fos_ctx* ctx, void* host_buf, size_t bytes)
     }
     if (pbas_on(ctx)) {
         const size_t N4 = 4 * size_t(ctx->prm.N);
-        FOS_TRY(ctx, cudaMemcpy2D(out, P * 2, ctx->samp, pl * 2, P * 2, N4, cudaMemcpyDeviceToHost));
-        out += N4 * P * 2;
-        FOS_TRY(ctx, cudaMemcpy2D(out, P * 2, ctx->Dq, pl * 2, P * 2, N4, cudaMemcpyDeviceToHost));
-        out += N4 * P * 2;
-        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->R, pl * 4, P * 4, 4, cudaMemcpyDeviceToHost));
-        out += 4 * P * 4;
-        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->T, pl * 4, P * 4, 4, cudaMemcpyDeviceToHost));
-        out += 4 * P * 4;
-        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->S, pl * 4, P * 4, 4, cudaMemcpyDeviceToHost));
-        out += 4 * P * 4;
+        const size_t W = size_t(ctx->W), Wp = size_t(ctx->Wp), H4 = 4 * size_t(ctx->H);
+        std::vector<uint16_t> tmp(N4 * size_t(ctx->nseg) * kSeg);
+        for (uint16_t* dev : {ctx->samp, ctx->Dq}) {
+            FOS_TRY(ctx, cudaMemcpy(tmp.data(), dev, tmp.size() * 2, cudaMemcpyDeviceToHost));
+            unblock_samples(ctx, tmp.data(), reinterpret_cast<uint16_t*>(out));
+            out += N4 * P * 2;
+        }
+        for (void* dev : {static_cast<void*>(ctx->R), static_cast<void*>(ctx->T), static_cast<void*>(ctx->S)}) {
+            FOS_TRY(ctx, cudaMemcpy2D(out, W * 4, dev, Wp * 4, W * 4, H4, cudaMemcpyDeviceToHost));
+            out += 4 * P * 4;
+        }
         if (ctx->t > 0) {
             FOS_TRY(ctx, cudaMemcpy(out, ctx->aux + ((ctx->t - 1) & 1) * 4, 32, cudaMemcpyDeviceToHost));
         } else {
@@ -515,16 +553,17 @@ fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes)
     }
     if (pbas_on(ctx)) {
         const size_t N4 = 4 * size_t(ctx->prm.N);
-        FOS_TRY(ctx, cudaMemcpy2D(ctx->samp, pl * 2, in, P * 2, P * 2, N4, cudaMemcpyHostToDevice));
-        in += N4 * P * 2;
-        FOS_TRY(ctx, cudaMemcpy2D(ctx->Dq, pl * 2, in, P * 2, P * 2, N4, cudaMemcpyHostToDevice));
-        in += N4 * P * 2;
-        FOS_TRY(ctx, cudaMemcpy2D(ctx->R, pl * 4, in, P * 4, P * 4, 4, cudaMemcpyHostToDevice));
-        in += 4 * P * 4;
-        FOS_TRY(ctx, cudaMemcpy2D(ctx->T, pl * 4, in, P * 4, P * 4, 4, cudaMemcpyHostToDevice));
-        in += 4 * P * 4;
-        FOS_TRY(ctx, cudaMemcpy2D(ctx->S, pl * 4, in, P * 4, P * 4, 4, cudaMemcpyHostToDevice));
-        in += 4 * P * 4;
+        const size_t W = size_t(ctx->W), Wp = size_t(ctx->Wp), H4 = 4 * size_t(ctx->H);
+        std::vector<uint16_t> tmp(N4 * size_t(ctx->nseg) * kSeg, 0);
+        for (uint16_t* dev : {ctx->samp, ctx->Dq}) {
+            block_samples(ctx, reinterpret_cast<const uint16_t*>(in), tmp.data());
+            FOS_TRY(ctx, cudaMemcpy(dev, tmp.data(), tmp.size() * 2, cudaMemcpyHostToDevice));
+            in += N4 * P * 2;
+        }
+        for (void* dev : {static_cast<void*>(ctx->R), static_cast<void*>(ctx->T), static_cast<void*>(ctx->S)}) {
+            FOS_TRY(ctx, cudaMemcpy2D(dev, Wp * 4, in, W * 4, W * 4, H4, cudaMemcpyHostToDevice));
+            in += 4 * P * 4;
+        }
         // gsum of the last frame goes where the next frame reads it; the other
         // buffer is the next frame's accumulator and starts at zero
         const int64_t t = h.frame_index;

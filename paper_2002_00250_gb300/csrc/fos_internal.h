@@ -31,12 +31,23 @@ struct GmmArgs {
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
 
-// PBAS device state: samples and D are uint16 planes [c*N + k]; R, T, S are
-// planes [c]; req is one uint32 plane (byte c = neighbour request of channel c:
-// 0 none, else 1 + j*N + k2).
+// PBAS device state.  Frames are cut into row segments of kSeg = 128 pixels
+// (spr = ceil(W / 128) segments per row, nseg = H * spr).  Samples and D are
+// uint16 in a blocked layout: element (c, k, x, y) sits at
+//   ((c * nseg + y * spr + x / 128) * N + k) * 128 + x % 128,
+// so the N slots of one channel of one segment are 256-byte rows of one
+// contiguous block: a warp reads each slot with one coalesced 256-byte access
+// and its random own/neighbour slot writes land in the block it just read.
+// R, T, S (per channel) and the request word are planes with row pitch
+// Wp = spr * 128; plane stride `plane` = Wp * H.  Request byte c of a pixel:
+// 0 none, else 1 + j * N + k2.
+constexpr int kSeg = 128;
+
 struct PbasArgs {
     int W, H;
-    int64_t P, plane;
+    int64_t P;
+    int Wp, spr;
+    int64_t nseg, plane;
     const uint8_t* rgb;
     const uint16_t* depth;
     uint8_t* mask;
@@ -48,7 +59,7 @@ struct PbasArgs {
     uint32_t* req;
     unsigned long long* gsum_prev;  // [4] gradient sums of the previous frame
     unsigned long long* gsum_cur;   // [4] accumulated for this frame (zeroed beforehand)
-    unsigned long long* counters;   // [4] own updates, neighbour writes, requests, frames
+    unsigned long long* counters;   // [3] own updates, neighbour writes, requests
     float R_lower_rgb, R_lower_d, R_scale, R_incdec;
     float T_lower, T_upper, T_inc, T_dec, alpha_g, eps_d;
     int N, n_min;
@@ -56,7 +67,7 @@ struct PbasArgs {
     int forced;
     uint32_t depth_fs;
     uint32_t t;   // frame index
-    int vec_ok;   // W % 4 == 0 and aligned pointers
+    int vec_ok;   // W % 4 == 0 and a 4-byte aligned mask
 };
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);

@@ -122,9 +122,10 @@ __device__ __forceinline__ void stu(uint32_t* p, const uint32_t (&o)[PX])
     else *p = o[0];
 }
 
-// Block-wide sum of NV per-thread counters, one atomicAdd per counter per block.
-template <int TY, int NV>
-__device__ __forceinline__ void block_add(uint32_t (&v)[NV], unsigned long long* const (&dst)[NV])
+// Block-wide sums of per-thread counters: v[q] is added to dst(q) with one
+// atomicAdd per counter per block (dst maps a counter index to its address).
+template <int TY, int NV, class Dst>
+__device__ __forceinline__ void block_add(const uint32_t (&v)[NV], Dst dst)
 {
     __shared__ uint32_t red[NV][TY];
 #pragma unroll
@@ -139,8 +140,15 @@ __device__ __forceinline__ void block_add(uint32_t (&v)[NV], unsigned long long*
         unsigned long long s = 0;
 #pragma unroll
         for (int w = 0; w < TY; ++w) s += red[threadIdx.x][w];
-        if (s) atomicAdd(dst[threadIdx.x], s);
+        if (s) atomicAdd(dst(threadIdx.x), s);
     }
+}
+
+// Index of sample / D element (c, k) of pixel (x, y) in the blocked layout.
+__device__ __forceinline__ int64_t sidx(const PbasArgs& a, int N, int c, int k, int x, int y)
+{
+    const int64_t seg = int64_t(y) * a.spr + (x >> 7);
+    return ((int64_t(c) * a.nseg + seg) * N + k) * kSeg + (x & (kSeg - 1));
 }
 
 struct Draws {
@@ -187,7 +195,8 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
     bool inb[PX];
 #pragma unroll
     for (int i = 0; i < PX; ++i) inb[i] = (y < a.H) && (x + i < a.W);
-    const int64_t p0 = int64_t(y) * a.W + x;
+    const int64_t q0 = int64_t(y) * a.Wp + x;   // index in the pitched planes
+    const uint32_t pix0 = uint32_t(y) * uint32_t(a.W) + uint32_t(x);  // Philox counter
     const bool vec = (PX == 4) && inb[0];  // W % 4 == 0 on this path: all PX in frame
 
     const float omr = __fsub_rn(1.0f, a.R_incdec), opr = __fadd_rn(1.0f, a.R_incdec);
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
 
         float Rv[PX], Tv[PX];
         uint32_t Sv[PX];
-        const int64_t pc = int64_t(c) * a.plane + p0;
+        const int64_t pc = int64_t(c) * a.plane + q0;
         if (vec) {
             ldf<PX>(a.R + pc, Rv);
             ldf<PX>(a.T + pc, Tv);
@@ -238,19 +247,21 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
             }
         }
 
+        // distances to the N samples: count within R, minimum
         int cnt[PX];
         float dmin[PX];
 #pragma unroll
         for (int i = 0; i < PX; ++i) { cnt[i] = 0; dmin[i] = INFINITY; }
-        const uint16_t* sp = a.samp + int64_t(c) * N * a.plane + p0;
+        const int64_t sb = inb[0] ? sidx(a, N, c, 0, x, y) : 0;  // slot 0 of pixel x
 #pragma unroll(NT > 0 ? NT : 4)
         for (int k = 0; k < N; ++k) {
             uint32_t s[PX];
             if (vec) {
-                ld16<PX>(sp + int64_t(k) * a.plane, s);
+                ld16<PX>(a.samp + sb + int64_t(k) * kSeg, s);
             } else {
 #pragma unroll
-                for (int i = 0; i < PX; ++i) s[i] = inb[i] ? sp[int64_t(k) * a.plane + i] : 0u;
+                for (int i = 0; i < PX; ++i)
+                    s[i] = inb[i] ? a.samp[sidx(a, N, c, k, x + i, y)] : 0u;
             }
 #pragma unroll
             for (int i = 0; i < PX; ++i) {
@@ -262,38 +273,56 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
             }
         }
 
+        // decisions and random draws
+        bool fg[PX];
+        int slot[PX];
+        int64_t oidx[PX];
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            fg[i] = act[i] && cnt[i] < a.n_min;
+            slot[i] = -1;
+            oidx[i] = 0;
+            if (act[i] && !fg[i]) {
+                const float prob = __fdiv_rn(1.0f, Tv[i]);
+                const Draws d = draws(a, pix0 + uint32_t(i), uint32_t(c), prob, N);
+                if (d.coin1) {
+                    slot[i] = int(d.k1);
+                    oidx[i] = sidx(a, N, c, int(d.k1), x + i, y);
+                }
+                if (d.coin2) {
+                    reqw[i] |= (1u + d.j * uint32_t(N) + d.k2) << (8 * c);
+                    cnt6[5] += 1;
+                }
+            }
+            anyfg[i] |= fg[i];
+        }
+        // own updates: all D reads first (independent), then the writes
+        uint32_t dold[PX];
+#pragma unroll
+        for (int i = 0; i < PX; ++i) dold[i] = slot[i] >= 0 ? uint32_t(a.Dq[oidx[i]]) : 0u;
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if (slot[i] < 0) continue;
+            a.samp[oidx[i]] = uint16_t(v[i] | (g[i] << 8));
+            const float q16 = __fmul_rn(dmin[i], 16.0f);
+            const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
+            Sv[i] = Sv[i] + q - dold[i];
+            a.Dq[oidx[i]] = uint16_t(q);
+            cnt6[4] += 1;
+        }
+        // adaptive threshold R and learning parameter T
         const float Rlo = c < 3 ? a.R_lower_rgb : a.R_lower_d;
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             if (!act[i]) continue;
-            const bool fg = cnt[i] < a.n_min;
-            anyfg[i] |= fg;
-            Draws d{false, false, 0u, 0u, 0u};
-            if (!fg) {
-                const float prob = __fdiv_rn(1.0f, Tv[i]);
-                d = draws(a, uint32_t(p0 + i), uint32_t(c), prob, N);
-                if (d.coin1) {
-                    const int64_t o = (int64_t(c) * N + d.k1) * a.plane + p0 + i;
-                    a.samp[o] = uint16_t(v[i] | (g[i] << 8));
-                    const float q16 = __fmul_rn(dmin[i], 16.0f);
-                    const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
-                    Sv[i] = Sv[i] + q - uint32_t(a.Dq[o]);
-                    a.Dq[o] = uint16_t(q);
-                    cnt6[4] += 1;
-                }
-            }
             const float dbar = fmaxf(__fdiv_rn(__uint2float_rn(Sv[i]), n16), a.eps_d);
             const float Rs = __fmul_rn(dbar, a.R_scale);
-            float Rn = Rv[i] > Rs ? __fmul_rn(Rv[i], omr) : __fmul_rn(Rv[i], opr);
+            const float Rn = Rv[i] > Rs ? __fmul_rn(Rv[i], omr) : __fmul_rn(Rv[i], opr);
             Rv[i] = Rn < Rlo ? Rlo : Rn;
-            float Tn = fg ? __fadd_rn(Tv[i], __fdiv_rn(a.T_inc, dbar))
-                          : __fsub_rn(Tv[i], __fdiv_rn(a.T_dec, dbar));
+            float Tn = fg[i] ? __fadd_rn(Tv[i], __fdiv_rn(a.T_inc, dbar))
+                             : __fsub_rn(Tv[i], __fdiv_rn(a.T_dec, dbar));
             Tn = Tn < a.T_lower ? a.T_lower : Tn;
             Tv[i] = Tn > a.T_upper ? a.T_upper : Tn;
-            if (!fg && d.coin2) {
-                reqw[i] |= (1u + d.j * uint32_t(N) + d.k2) << (8 * c);
-                cnt6[5] += 1;
-            }
         }
         if (vec) {
             stf<PX>(a.R + pc, Rv);
@@ -306,26 +335,20 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
         }
     }
 
+    const int64_t p0 = int64_t(y) * a.W + x;  // mask index (unpadded frame)
     if (vec) {
         uint32_t m = 0;
 #pragma unroll
         for (int i = 0; i < PX; ++i) m |= (anyfg[i] ? 255u : 0u) << (8 * i);
-        if (a.vec_ok) {
-            *reinterpret_cast<uint32_t*>(a.mask + p0) = m;
-        } else {
-#pragma unroll
-            for (int i = 0; i < PX; ++i) a.mask[p0 + i] = anyfg[i] ? 255 : 0;
-        }
-        stu<PX>(a.req + p0, reqw);
+        *reinterpret_cast<uint32_t*>(a.mask + p0) = m;
+        stu<PX>(a.req + q0, reqw);
     } else {
 #pragma unroll
         for (int i = 0; i < PX; ++i)
-            if (inb[i]) { a.mask[p0 + i] = anyfg[i] ? 255 : 0; a.req[p0 + i] = reqw[i]; }
+            if (inb[i]) { a.mask[p0 + i] = anyfg[i] ? 255 : 0; a.req[q0 + i] = reqw[i]; }
     }
 
-    unsigned long long* const dst[6] = {a.gsum_cur, a.gsum_cur + 1, a.gsum_cur + 2, a.gsum_cur + 3,
-                                        a.counters, a.counters + 2};
-    block_add<TY, 6>(cnt6, dst);
+    block_add<TY, 6>(cnt6, [&](int q) { return q < 4 ? a.gsum_cur + q : a.counters + (q == 4 ? 0 : 2); });
 }
 
 template <int NT, int PX, int TY>
@@ -342,7 +365,7 @@ __global__ void __launch_bounds__(32 * TY) pbas_neighbour_kernel(const PbasArgs 
         const int r = idx / G::SW, col = idx - r * G::SW;
         const int gx = x0 - 1 + col, gy = y0 - 1 + r;
         const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
-        sreq[idx] = in ? a.req[int64_t(gy) * a.W + gx] : 0u;
+        sreq[idx] = in ? a.req[int64_t(gy) * a.Wp + gx] : 0u;
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && tid < 4) {
         // this frame's classify pass has consumed the previous frame's sums;
@@ -358,11 +381,11 @@ __global__ void __launch_bounds__(32 * TY) pbas_neighbour_kernel(const PbasArgs 
     for (int i = 0; i < PX; ++i) {
         if (y >= a.H || x + i >= a.W) continue;
         const int col = lx0 + i + 1;
-        const int64_t p = int64_t(y) * a.W + x + i;
         const bool dvalid = sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0;
         uint32_t cached[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
+            // the neighbour at -dir(j) targets this pixel when its direction is j
             const uint32_t r = sreq[(ly + 1 - dir_dy(j)) * G::SW + (col - dir_dx(j))];
             if (r == 0) continue;
 #pragma unroll
@@ -377,13 +400,12 @@ __global__ void __launch_bounds__(32 * TY) pbas_neighbour_kernel(const PbasArgs 
                     const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
                     cached[c] = v | (sobel(sm + c * G::CH, G::SWP, ly + 1, col) << 8);
                 }
-                a.samp[(int64_t(c) * N + k2) * a.plane + p] = uint16_t(cached[c]);
+                a.samp[sidx(a, N, c, int(k2), x + i, y)] = uint16_t(cached[c]);
                 applied[0] += 1;
             }
         }
     }
-    unsigned long long* const dst[1] = {a.counters + 1};
-    block_add<TY, 1>(applied, dst);
+    block_add<TY, 1>(applied, [&](int) { return a.counters + 1; });
 }
 
 template <int NT, int PX, int TY>
@@ -402,26 +424,26 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
     for (int i = 0; i < PX; ++i) {
         if (y >= a.H || x + i >= a.W) continue;
         const int col = lx0 + i + 1;
-        const int64_t p = int64_t(y) * a.W + x + i;
-#pragma unroll 1
+        const int64_t q = int64_t(y) * a.Wp + x + i;
+#pragma unroll
         for (int c = 0; c < 4; ++c) {
             const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
             const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
             gs[c] += g;
             const uint16_t sv = uint16_t(v | (g << 8));
+            const int64_t b = sidx(a, N, c, 0, x + i, y);
             for (int k = 0; k < N; ++k) {
-                a.samp[(int64_t(c) * N + k) * a.plane + p] = sv;
-                a.Dq[(int64_t(c) * N + k) * a.plane + p] = 0;
+                a.samp[b + int64_t(k) * kSeg] = sv;
+                a.Dq[b + int64_t(k) * kSeg] = 0;
             }
-            a.R[int64_t(c) * a.plane + p] = c < 3 ? a.R_lower_rgb : a.R_lower_d;
-            a.T[int64_t(c) * a.plane + p] = a.T_lower;
-            a.S[int64_t(c) * a.plane + p] = 0u;
+            a.R[int64_t(c) * a.plane + q] = c < 3 ? a.R_lower_rgb : a.R_lower_d;
+            a.T[int64_t(c) * a.plane + q] = a.T_lower;
+            a.S[int64_t(c) * a.plane + q] = 0u;
         }
-        a.mask[p] = 0;
-        a.req[p] = 0u;
+        a.mask[int64_t(y) * a.W + x + i] = 0;
+        a.req[q] = 0u;
     }
-    unsigned long long* const dst[4] = {a.gsum_cur, a.gsum_cur + 1, a.gsum_cur + 2, a.gsum_cur + 3};
-    block_add<TY, 4>(gs, dst);
+    block_add<TY, 4>(gs, [&](int q) { return a.gsum_cur + q; });
 }
 
 template <int PX, int TY>

@@ -73,7 +73,7 @@ def test_invalid_arguments_rejected_before_any_device_call(fos):
     p = fos.default_params()
     assert not lib.fos_create(0, 10, ctypes.byref(p))
     assert b"width" in lib.fos_last_error(None)
-    p.N = 40
+    p.N = 32
     assert not lib.fos_create(16, 16, ctypes.byref(p))
     assert b"N" in lib.fos_last_error(None)
     p = fos.default_params(K_rgb=4)
