@@ -195,8 +195,10 @@ fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes);
  * Measurement hooks.
  * ------------------------------------------------------------------------- */
 #define FOS_KERNEL_GMM 0        /* GMM classify + update (Sec. 3.1) */
-#define FOS_KERNEL_PBAS_CLASSIFY 1 /* PBAS gradient, classify, own update */
-#define FOS_KERNEL_PBAS_NEIGHBOUR 2 /* PBAS neighbour update */
+#define FOS_KERNEL_PBAS_CLASSIFY 1 /* PBAS: the previous frame's neighbour
+                                      updates, gradient, classify, own update */
+#define FOS_KERNEL_PBAS_FLUSH 2  /* PBAS pending neighbour updates applied
+                                    outside a frame (before a state export) */
 #define FOS_KERNEL_INIT 3       /* frame-0 initialisation */
 #define FOS_KERNEL_COUNT 4
 
@@ -210,6 +212,23 @@ fos_status fos_set_timing(fos_ctx* ctx, uint32_t kernel_mask);
 /* Waits for the timed launches and writes FOS_KERNEL_COUNT entries; then
  * clears the accumulators. */
 fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT]);
+
+/* ---------------------------------------------------------------------------
+ * Kernel shapes (tuning).  Results do not depend on them: every shape computes
+ * the same bits.  Defaults: GMM 4 pixels per thread, 128 threads per block;
+ * PBAS 2 pixels per thread (when the width is a multiple of it), 4 rows.
+ * ------------------------------------------------------------------------- */
+#define FOS_OPT_GMM_PX 1   /* GMM pixels per thread: 1, 2, 4 (3+3 components) */
+#define FOS_OPT_GMM_TPB 2  /* GMM threads per block: 64, 128, 256 */
+#define FOS_OPT_PBAS_PX 3  /* PBAS pixels per thread: 1, 2, 4 */
+#define FOS_OPT_PBAS_TY 4  /* PBAS tile rows: 2, 4, 8 (2 only with 4 px/thread) */
+#define FOS_OPT_COUNT 5
+
+/* Sets a kernel-shape option; FOS_ERR_INVALID_ARG for unknown options or
+ * values, FOS_ERR_UNSUPPORTED for shapes not compiled in. */
+fos_status fos_set_option(fos_ctx* ctx, int32_t option, int32_t value);
+/* Current value of an option, -1 for an unknown option or NULL ctx. */
+int32_t fos_get_option(const fos_ctx* ctx, int32_t option);
 
 /*
  * PBAS update counters since the last call (then cleared):

@@ -47,8 +47,11 @@ struct fos_ctx {
     float* R = nullptr;
     float* T = nullptr;
     uint32_t* S = nullptr;
-    uint32_t* req = nullptr;
-    unsigned long long* aux = nullptr;  // gsum[2][4], counters[4]
+    uint32_t* req = nullptr;            // [2][pplane] requests of even / odd frames
+    uint16_t* prev = nullptr;           // [4][pplane]
+    bool pending = false;               // requests of the last frame not yet applied
+    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 4};  // kernel shapes (fos_set_option)
+    unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
     uint8_t* h_rgb[2] = {nullptr, nullptr};  // device staging for host frames
     uint16_t* h_depth[2] = {nullptr, nullptr};
     uint8_t* h_mg[2] = {nullptr, nullptr};
@@ -180,17 +183,24 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     a.W = c->W; a.H = c->H; a.P = c->P;
     a.Wp = c->Wp; a.spr = c->spr; a.nseg = c->nseg; a.plane = c->pplane;
     a.rgb = rgb; a.depth = depth; a.mask = mask;
-    a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S; a.req = c->req;
-    a.gsum_prev = c->aux + ((c->t + 1) & 1) * 4;  // buffer of frame t-1
-    a.gsum_cur = c->aux + (c->t & 1) * 4;
-    a.counters = c->aux + 8;
+    a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S; a.prev = c->prev;
+    const int64_t t = c->t;
+    a.req_cur = c->req + (t & 1) * c->pplane;
+    a.req_prev = c->req + ((t + 1) & 1) * c->pplane;      // buffer of frame t-1
+    a.gsum_prev = c->aux + ((t + 2) % 3) * 4;             // frame t-1
+    a.gsum_cur = c->aux + (t % 3) * 4;
+    a.gsum_next = c->aux + ((t + 1) % 3) * 4;
+    a.counters = c->aux + 12;
+    a.apply = c->pending ? 1 : 0;
     a.R_lower_rgb = p.R_lower_rgb; a.R_lower_d = p.R_lower_d; a.R_scale = p.R_scale;
     a.R_incdec = p.R_incdec; a.T_lower = p.T_lower; a.T_upper = p.T_upper;
     a.T_inc = p.T_inc; a.T_dec = p.T_dec; a.alpha_g = p.alpha_g; a.eps_d = p.eps_d;
     a.N = p.N; a.n_min = p.n_min; a.seed = p.seed; a.stream_id = p.stream_id;
     a.forced = p.forced_rng; a.depth_fs = p.depth_full_scale_mm;
     a.t = uint32_t(c->t);
-    a.vec_ok = (c->W % 4 == 0) && aligned(mask, 4);
+    a.px = c->opt[FOS_OPT_PBAS_PX];
+    a.ty = c->opt[FOS_OPT_PBAS_TY];
+    a.mask_vec = aligned(mask, uintptr_t(a.px)) ? 1 : 0;
     return a;
 }
 
@@ -201,7 +211,7 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     if (gmm_on(c) && !mg) return fail(c, FOS_ERR_INVALID_ARG, "GMM enabled: mask_gmm must be non-NULL");
     if (pbas_on(c) && !mp) return fail(c, FOS_ERR_INVALID_ARG, "PBAS enabled: mask_pbas must be non-NULL");
     const bool first = c->t == 0;
-    if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 8 * sizeof(unsigned long long), s));
+    if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
     if (gmm_on(c)) {
         GmmArgs a{};
         const fos_params& p = c->prm;
@@ -213,6 +223,8 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
         a.depth_fs = p.depth_full_scale_mm;
         a.init = first ? 1 : 0;
         a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4);
+        a.px = c->opt[FOS_OPT_GMM_PX];
+        a.tpb = c->opt[FOS_OPT_GMM_TPB];
         TimedScope ts(c, first ? FOS_KERNEL_INIT : FOS_KERNEL_GMM, s);
         fos_status st = launch_result(c, launch_gmm(a, p.K_rgb, p.K_d, s), "gmm");
         if (st != FOS_OK) return st;
@@ -223,17 +235,12 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
             TimedScope ts(c, FOS_KERNEL_INIT, s);
             fos_status st = launch_result(c, launch_pbas_init(a, s), "pbas_init");
             if (st != FOS_OK) return st;
+            c->pending = false;
         } else {
-            {
-                TimedScope ts(c, FOS_KERNEL_PBAS_CLASSIFY, s);
-                fos_status st = launch_result(c, launch_pbas_classify(a, s), "pbas_classify");
-                if (st != FOS_OK) return st;
-            }
-            {
-                TimedScope ts(c, FOS_KERNEL_PBAS_NEIGHBOUR, s);
-                fos_status st = launch_result(c, launch_pbas_neighbour(a, s), "pbas_neighbour");
-                if (st != FOS_OK) return st;
-            }
+            TimedScope ts(c, FOS_KERNEL_PBAS_CLASSIFY, s);
+            fos_status st = launch_result(c, launch_pbas_classify(a, s), "pbas_classify");
+            if (st != FOS_OK) return st;
+            c->pending = true;
         }
     }
     c->t += 1;
@@ -270,7 +277,7 @@ size_t pbas_bytes(const fos_ctx* c)
 void free_all(fos_ctx* c)
 {
     cudaFree(c->gmm); cudaFree(c->samp); cudaFree(c->Dq); cudaFree(c->R); cudaFree(c->T);
-    cudaFree(c->S); cudaFree(c->req); cudaFree(c->aux);
+    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
@@ -375,10 +382,11 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
         if ((e = cudaMalloc(&c->R, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(R)", e);
         if ((e = cudaMalloc(&c->T, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
         if ((e = cudaMalloc(&c->S, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
-        if ((e = cudaMalloc(&c->req, pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
+        if ((e = cudaMalloc(&c->req, 2 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
+        if ((e = cudaMalloc(&c->prev, 4 * pp * 2)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
-    if ((e = cudaMalloc(&c->aux, 12 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
-    if ((e = cudaMemset(c->aux, 0, 12 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
+    if ((e = cudaMalloc(&c->aux, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
+    if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
     return c;
 }
 
@@ -400,6 +408,7 @@ fos_status fos_reset(fos_ctx* ctx)
 {
     if (!ctx) return FOS_ERR_INVALID_ARG;
     ctx->t = 0;
+    ctx->pending = false;
     return FOS_OK;
 }
 
@@ -494,6 +503,16 @@ fos_status fos_get_state(fos_ctx* ctx, void* host_buf, size_t bytes)
     fos_state_size(ctx, &need);
     if (bytes < need) return fail(ctx, FOS_ERR_INVALID_ARG, "state buffer too small");
     FOS_TRY(ctx, cudaDeviceSynchronize());
+    if (pbas_on(ctx) && ctx->pending) {
+        // the last frame's neighbour updates are applied lazily by the next
+        // frame; apply them now so the exported state is complete
+        const PbasArgs a = pbas_args(ctx, nullptr, nullptr, nullptr);
+        TimedScope ts(ctx, FOS_KERNEL_PBAS_FLUSH, nullptr);
+        fos_status st = launch_result(ctx, launch_pbas_flush(a, nullptr), "pbas_flush");
+        if (st != FOS_OK) return st;
+        ctx->pending = false;
+        FOS_TRY(ctx, cudaDeviceSynchronize());
+    }
     uint8_t* out = static_cast<uint8_t*>(host_buf);
     fos_state_header h{};
     h.magic = 0x53534F46u; h.abi_version = FOS_ABI_VERSION;
@@ -522,7 +541,7 @@ fos_status fos_get_state(fos_ctx* ctx, void* host_buf, size_t bytes)
             out += 4 * P * 4;
         }
         if (ctx->t > 0) {
-            FOS_TRY(ctx, cudaMemcpy(out, ctx->aux + ((ctx->t - 1) & 1) * 4, 32, cudaMemcpyDeviceToHost));
+            FOS_TRY(ctx, cudaMemcpy(out, ctx->aux + ((ctx->t + 2) % 3) * 4, 32, cudaMemcpyDeviceToHost));
         } else {
             std::memset(out, 0, 32);
         }
@@ -564,12 +583,13 @@ fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes)
             FOS_TRY(ctx, cudaMemcpy2D(dev, Wp * 4, in, W * 4, W * 4, H4, cudaMemcpyHostToDevice));
             in += 4 * P * 4;
         }
-        // gsum of the last frame goes where the next frame reads it; the other
-        // buffer is the next frame's accumulator and starts at zero
+        // gsum of the last frame goes where the next frame reads it; the
+        // other buffers are accumulators and start at zero; nothing pending
         const int64_t t = h.frame_index;
-        unsigned long long g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (t > 0) std::memcpy(g + ((t - 1) & 1) * 4, in, 32);
+        unsigned long long g[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        if (t > 0) std::memcpy(g + ((t + 2) % 3) * 4, in, 32);
         FOS_TRY(ctx, cudaMemcpy(ctx->aux, g, sizeof g, cudaMemcpyHostToDevice));
+        ctx->pending = false;
     }
     ctx->t = h.frame_index;
     return FOS_OK;
@@ -598,14 +618,41 @@ fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
     return FOS_OK;
 }
 
+fos_status fos_set_option(fos_ctx* ctx, int32_t option, int32_t value)
+{
+    if (!ctx) return FOS_ERR_INVALID_ARG;
+    bool ok = false;
+    switch (option) {
+    case FOS_OPT_GMM_PX: ok = value == 1 || value == 2 || value == 4; break;
+    case FOS_OPT_GMM_TPB: ok = value == 64 || value == 128 || value == 256; break;
+    case FOS_OPT_PBAS_PX: ok = value == 1 || value == 2 || value == 4; break;
+    case FOS_OPT_PBAS_TY: ok = value == 2 || value == 4 || value == 8; break;
+    default: return fail(ctx, FOS_ERR_INVALID_ARG, "unknown option");
+    }
+    if (!ok) return fail(ctx, FOS_ERR_INVALID_ARG, "option value not supported");
+    if (option == FOS_OPT_PBAS_PX || option == FOS_OPT_PBAS_TY) {
+        const int px = option == FOS_OPT_PBAS_PX ? value : ctx->opt[FOS_OPT_PBAS_PX];
+        const int ty = option == FOS_OPT_PBAS_TY ? value : ctx->opt[FOS_OPT_PBAS_TY];
+        if (px == 2 && ty == 2) return fail(ctx, FOS_ERR_UNSUPPORTED, "PBAS tile 2 x 2 not compiled in");
+    }
+    ctx->opt[option] = value;
+    return FOS_OK;
+}
+
+int32_t fos_get_option(const fos_ctx* ctx, int32_t option)
+{
+    if (!ctx || option < 1 || option >= FOS_OPT_COUNT) return -1;
+    return ctx->opt[option];
+}
+
 fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4])
 {
     if (!ctx || !out) return FOS_ERR_INVALID_ARG;
     FOS_TRY(ctx, cudaDeviceSynchronize());
     unsigned long long c[4];
-    FOS_TRY(ctx, cudaMemcpy(c, ctx->aux + 8, sizeof c, cudaMemcpyDeviceToHost));
+    FOS_TRY(ctx, cudaMemcpy(c, ctx->aux + 12, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = ctx->frames_since_counters;
-    FOS_TRY(ctx, cudaMemset(ctx->aux + 8, 0, 4 * sizeof(unsigned long long)));
+    FOS_TRY(ctx, cudaMemset(ctx->aux + 12, 0, 3 * sizeof(unsigned long long)));
     ctx->frames_since_counters = 0;
     return FOS_OK;
 }

@@ -27,6 +27,8 @@ struct GmmArgs {
     uint32_t depth_fs;  // depth full scale (mm)
     int init;           // 1: frame 0 (bootstrap)
     int vec_ok;         // 1: pointers aligned for the vectorised path
+    int px;             // pixels per thread: 1, 2 or 4
+    int tpb;            // threads per block: 64, 128 or 256
 };
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
@@ -38,10 +40,13 @@ LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
 // so the N slots of one channel of one segment are 256-byte rows of one
 // contiguous block: a warp reads each slot with one coalesced 256-byte access
 // and its random own/neighbour slot writes land in the block it just read.
-// R, T, S (per channel) and the request word are planes with row pitch
-// Wp = spr * 128; plane stride `plane` = Wp * H.  Request byte c of a pixel:
-// 0 none, else 1 + j * N + k2.
+// R, T, S, prev (per channel) and the request words are planes with row pitch
+// Wp = spr * 128; plane stride `plane` = Wp * H.
+// Request word of a pixel: byte c = (direction << 5) | slot for channel c, or
+// 0x1F for no request.  prev holds (value | gradient << 8) per channel of the
+// last processed frame (the value neighbour requests write).
 constexpr int kSeg = 128;
+constexpr uint32_t kReqNone4 = 0x1F1F1F1Fu;
 
 struct PbasArgs {
     int W, H;
@@ -56,9 +61,12 @@ struct PbasArgs {
     float* R;
     float* T;
     uint32_t* S;
-    uint32_t* req;
-    unsigned long long* gsum_prev;  // [4] gradient sums of the previous frame
-    unsigned long long* gsum_cur;   // [4] accumulated for this frame (zeroed beforehand)
+    uint16_t* prev;
+    const uint32_t* req_prev;       // requests of frame t-1 (read)
+    uint32_t* req_cur;              // requests of frame t (written)
+    unsigned long long* gsum_prev;  // [4] gradient sums of frame t-1
+    unsigned long long* gsum_cur;   // [4] accumulated for frame t (zero on entry)
+    unsigned long long* gsum_next;  // [4] zeroed for frame t+1
     unsigned long long* counters;   // [3] own updates, neighbour writes, requests
     float R_lower_rgb, R_lower_d, R_scale, R_incdec;
     float T_lower, T_upper, T_inc, T_dec, alpha_g, eps_d;
@@ -66,12 +74,14 @@ struct PbasArgs {
     uint32_t seed, stream_id;
     int forced;
     uint32_t depth_fs;
-    uint32_t t;   // frame index
-    int vec_ok;   // W % 4 == 0 and a 4-byte aligned mask
+    uint32_t t;    // frame index
+    int apply;     // 1: requests of frame t-1 are pending
+    int px, ty;    // tile shape: pixels per thread (used when W % px == 0), rows
+    int mask_vec;  // mask pointer aligned for PX-wide stores
 };
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
-LaunchResult launch_pbas_neighbour(const PbasArgs& a, cudaStream_t s);
+LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);
 
 }  // namespace fos

@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
 {
     const int64_t p0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * PX;
     if (p0 >= a.P) return;
-    if (PX > 1 && a.vec_ok && p0 + PX <= a.P) {
+    // PX = 4 reads the inputs as 32/64-bit words: needs aligned frame buffers
+    if (PX > 1 && (PX != 4 || a.vec_ok) && p0 + PX <= a.P) {
         Mix<KR, 3> mr[PX];
         Mix<KD, 1> md[PX];
         if (!a.init) move_state<KR, KD, PX, false>(a.state, a.plane, p0, mr, md);
@@ -263,26 +264,33 @@ __global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
     }
 }
 
-template <int KR, int KD>
+template <int KR, int KD, int PX>
 LaunchResult launch_k(const GmmArgs& a, cudaStream_t s)
 {
-    constexpr int PX = 4, TPB = 128;
+    const int tpb = (a.tpb == 64 || a.tpb == 256) ? a.tpb : 128;
     const int64_t threads = (a.P + PX - 1) / PX;
-    const int64_t blocks = (threads + TPB - 1) / TPB;
-    gmm_kernel<KR, KD, PX><<<dim3(unsigned(blocks)), TPB, 0, s>>>(a);
+    const int64_t blocks = (threads + tpb - 1) / tpb;
+    gmm_kernel<KR, KD, PX><<<dim3(unsigned(blocks)), tpb, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
 }
 
 }  // namespace
 
+// Pixels per thread: the requested px for the 3+3 model; mixtures with more
+// components keep fewer pixels per thread so the state stays in registers.
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s)
 {
     if (a.P == 0) return kLaunchOk;
-#define FOS_CASE(R, D) \
-    if (Kr == R && Kd == D) return launch_k<R, D>(a, s);
-    FOS_CASE(3, 3) FOS_CASE(7, 3) FOS_CASE(5, 3) FOS_CASE(2, 2) FOS_CASE(1, 1)
-    FOS_CASE(2, 1) FOS_CASE(3, 1) FOS_CASE(3, 2) FOS_CASE(5, 2) FOS_CASE(7, 2)
-    FOS_CASE(1, 2) FOS_CASE(1, 3) FOS_CASE(2, 3) FOS_CASE(5, 1) FOS_CASE(7, 1)
+    if (Kr == 3 && Kd == 3) {
+        if (a.px == 1) return launch_k<3, 3, 1>(a, s);
+        if (a.px == 2) return launch_k<3, 3, 2>(a, s);
+        return launch_k<3, 3, 4>(a, s);
+    }
+#define FOS_CASE(R, D, PX) \
+    if (Kr == R && Kd == D) return launch_k<R, D, PX>(a, s);
+    FOS_CASE(7, 3, 2) FOS_CASE(5, 3, 2) FOS_CASE(2, 2, 4) FOS_CASE(1, 1, 4)
+    FOS_CASE(2, 1, 4) FOS_CASE(3, 1, 4) FOS_CASE(3, 2, 4) FOS_CASE(5, 2, 2) FOS_CASE(7, 2, 2)
+    FOS_CASE(1, 2, 4) FOS_CASE(1, 3, 4) FOS_CASE(2, 3, 4) FOS_CASE(5, 1, 2) FOS_CASE(7, 1, 2)
 #undef FOS_CASE
     return kLaunchUnsupported;
 }

@@ -4,16 +4,21 @@
 // its own decision threshold R(x), learning parameter T(x) and minimal-
 // distance record D(x) (base method: Hofmann et al., cited by the paper); the
 // depth channel only where the depth reading is valid; the pixel is
-// foreground if any processed channel is.  Two launches per frame realise the
-// two-phase semantics (every pixel is classified against the model of the
-// previous frame, then the neighbour updates land):
-//   classify : stage the frame tile plus a 1-pixel halo in shared memory,
-//              Sobel gradient per channel, distance to the N samples, own
-//              update, R/T/D update, neighbour-update request, mask, and the
-//              per-channel gradient sums for the next frame's weight;
-//   neighbour: every pixel gathers the requests of its 8 neighbours that point
-//              at it and writes its own (value, gradient) into the slots asked
-//              for.
+// foreground if any processed channel is.
+//
+// Two-phase semantics (every pixel of frame t is classified against the model
+// as it stood after frame t-1, including frame t-1's neighbour updates) with
+// one launch per frame:
+//   classify(t): stage the frame tile plus a 1-pixel halo in shared memory;
+//     apply the neighbour updates requested during frame t-1 to this pixel's
+//     slots (each writes the pixel's own frame-(t-1) value, kept in `prev`);
+//     Sobel gradient per channel; distance to the N samples; own update;
+//     R/T/D update; this frame's neighbour requests; mask; per-channel
+//     gradient sums for the next frame's weight.
+//   flush: applies pending requests without classifying (before the state is
+//     exported).
+// The pending writes go to memory just before the same thread reads those
+// slots, so they merge into sectors the kernel is reading anyway.
 // Arithmetic is IEEE single precision with every operation rounded once
 // (explicit _rn intrinsics, no contraction), so results are bit-exact against
 // a plain C implementation of the same steps.
@@ -63,6 +68,21 @@ __device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, u
     }
 }
 
+// Stage the neighbour-request words of the previous frame with a 1-pixel
+// halo; outside the frame there are no requests.
+template <int PX, int TY>
+__device__ __forceinline__ void stage_requests(const PbasArgs& a, int x0, int y0, uint32_t* sreq)
+{
+    using G = Geo<PX, TY>;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int idx = tid; idx < G::SH * G::SW; idx += 32 * TY) {
+        const int r = idx / G::SW, col = idx - r * G::SW;
+        const int gx = x0 - 1 + col, gy = y0 - 1 + r;
+        const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
+        sreq[idx] = in ? a.req_prev[int64_t(gy) * a.Wp + gx] : kReqNone4;
+    }
+}
+
 // Gradient magnitude: 3x3 Sobel, |gx| + |gy|, >> 3, clamped to 255.
 __device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int c)
 {
@@ -75,14 +95,66 @@ __device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int 
     return uint32_t(m > 255 ? 255 : m);
 }
 
+// Pending neighbour writes for the pixel at staged column `col`, row ly+1:
+// pend[c] gets bit k for every neighbour whose request of channel c points at
+// this pixel with slot k.  A request byte is (direction << 5) | slot; 0x1F is
+// "no request".
+template <int SW>
+__device__ __forceinline__ void pending_masks(const uint32_t* sreq, int ly, int col, uint32_t (&pend)[4])
+{
+    pend[0] = pend[1] = pend[2] = pend[3] = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t r = sreq[(ly + 1 - dir_dy(j)) * SW + (col - dir_dx(j))];
+        const uint32_t m = __vcmpeq4(r & 0xE0E0E0E0u, uint32_t(j << 5) * 0x01010101u) &
+                           ~__vcmpeq4(r & 0x1F1F1F1Fu, 0x1F1F1F1Fu);
+        if (m) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if ((m >> (8 * c)) & 0xFFu) pend[c] |= 1u << ((r >> (8 * c)) & 31u);
+        }
+    }
+}
+
+// PX pixels of uint16 / float / uint32 planes; PX = 4 uses one vector access.
 template <int PX>
 __device__ __forceinline__ void ld16(const uint16_t* p, uint32_t (&o)[PX])
 {
     if constexpr (PX == 4) {
         const uint2 v = *reinterpret_cast<const uint2*>(p);
         o[0] = v.x & 0xFFFFu; o[1] = v.x >> 16; o[2] = v.y & 0xFFFFu; o[3] = v.y >> 16;
+    } else if constexpr (PX == 2) {
+        const uint32_t v = *reinterpret_cast<const uint32_t*>(p);
+        o[0] = v & 0xFFFFu; o[1] = v >> 16;
     } else {
         o[0] = *p;
+    }
+}
+
+template <int PX>
+__device__ __forceinline__ void st16(uint16_t* p, const uint32_t (&o)[PX])
+{
+    if constexpr (PX == 4) *reinterpret_cast<uint2*>(p) = make_uint2(o[0] | (o[1] << 16), o[2] | (o[3] << 16));
+    else if constexpr (PX == 2) *reinterpret_cast<uint32_t*>(p) = o[0] | (o[1] << 16);
+    else *p = uint16_t(o[0]);
+}
+
+// Sample words: slot k of PX pixels as packed (value, gradient) byte pairs.
+template <int PX>
+struct SWords {
+    static constexpr int NW = (PX + 1) / 2;
+};
+
+template <int PX>
+__device__ __forceinline__ void ldw(const uint16_t* p, uint32_t (&w)[SWords<PX>::NW])
+{
+    if constexpr (PX == 4) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        w[0] = v.x; w[1] = v.y;
+    } else if constexpr (PX == 2) {
+        w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else {
+        w[0] = *p;
     }
 }
 
@@ -92,6 +164,9 @@ __device__ __forceinline__ void ldf(const float* p, float (&o)[PX])
     if constexpr (PX == 4) {
         const float4 v = *reinterpret_cast<const float4*>(p);
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (PX == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        o[0] = v.x; o[1] = v.y;
     } else {
         o[0] = *p;
     }
@@ -101,6 +176,7 @@ template <int PX>
 __device__ __forceinline__ void stf(float* p, const float (&o)[PX])
 {
     if constexpr (PX == 4) *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    else if constexpr (PX == 2) *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
     else *p = o[0];
 }
 
@@ -110,6 +186,9 @@ __device__ __forceinline__ void ldu(const uint32_t* p, uint32_t (&o)[PX])
     if constexpr (PX == 4) {
         const uint4 v = *reinterpret_cast<const uint4*>(p);
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (PX == 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        o[0] = v.x; o[1] = v.y;
     } else {
         o[0] = *p;
     }
@@ -119,6 +198,7 @@ template <int PX>
 __device__ __forceinline__ void stu(uint32_t* p, const uint32_t (&o)[PX])
 {
     if constexpr (PX == 4) *reinterpret_cast<uint4*>(p) = make_uint4(o[0], o[1], o[2], o[3]);
+    else if constexpr (PX == 2) *reinterpret_cast<uint2*>(p) = make_uint2(o[0], o[1]);
     else *p = o[0];
 }
 
@@ -180,14 +260,36 @@ __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c
     return d;
 }
 
+// Exact float of a small non-negative integer (< 2^23) without a conversion
+// instruction: 2^23 + v is representable, so subtracting 2^23 is exact.
+__device__ __forceinline__ float small_u2f(uint32_t v)
+{
+    return __fsub_rn(__uint_as_float(0x4B000000u | v), 8388608.0f);
+}
+
 template <int NT, int PX, int TY>
 __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
 {
     using G = Geo<PX, TY>;
+    constexpr int NW = SWords<PX>::NW;
     __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    __shared__ uint32_t sreq[G::SH * G::SW];
+    __shared__ float wtab[4][256];  // fl(wg_c * dg) for every gradient difference dg
+    __shared__ float wgs[4];
     const int N = NT > 0 ? NT : a.N;
     const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     stage_input<PX, TY>(a, x0, y0, sm);
+    if (a.apply) stage_requests<PX, TY>(a, x0, y0, sreq);
+    if (tid < 4) {
+        // gradient weight: alpha_g / mean gradient magnitude of the previous frame
+        float mean = __fdiv_rn(__ull2float_rn(a.gsum_prev[tid]), __ll2float_rn(a.P));
+        mean = fmaxf(mean, 1.0f);
+        wgs[tid] = __fdiv_rn(a.alpha_g, mean);
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid >= 4 && tid < 8) a.gsum_next[tid - 4] = 0ull;
+    __syncthreads();
+    for (int e = tid; e < 1024; e += 32 * TY) wtab[e >> 8][e & 255] = __fmul_rn(wgs[e >> 8], __int2float_rn(e & 255));
     __syncthreads();
 
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
@@ -197,7 +299,14 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
     for (int i = 0; i < PX; ++i) inb[i] = (y < a.H) && (x + i < a.W);
     const int64_t q0 = int64_t(y) * a.Wp + x;   // index in the pitched planes
     const uint32_t pix0 = uint32_t(y) * uint32_t(a.W) + uint32_t(x);  // Philox counter
-    const bool vec = (PX == 4) && inb[0];  // W % 4 == 0 on this path: all PX in frame
+    const bool vec = (PX > 1) && inb[0];  // W % PX == 0 on this path: all PX in frame
+
+    uint32_t pend[PX][4];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+        pend[i][0] = pend[i][1] = pend[i][2] = pend[i][3] = 0u;
+        if (a.apply && inb[i]) pending_masks<G::SW>(sreq, ly, lx0 + i + 1, pend[i]);
+    }
 
     const float omr = __fsub_rn(1.0f, a.R_incdec), opr = __fadd_rn(1.0f, a.R_incdec);
     const float n16 = __int2float_rn(16 * N);
@@ -205,35 +314,64 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
     uint32_t reqw[PX];
     bool anyfg[PX];
 #pragma unroll
-    for (int i = 0; i < PX; ++i) { reqw[i] = 0; anyfg[i] = false; }
-    uint32_t cnt6[6] = {0, 0, 0, 0, 0, 0};  // gsum R,G,B,D; own updates; requests
+    for (int i = 0; i < PX; ++i) { reqw[i] = kReqNone4; anyfg[i] = false; }
+    uint32_t cnt7[7] = {0, 0, 0, 0, 0, 0, 0};  // gsum R,G,B,D; own; neighbour writes; requests
 
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
-        // gradient weight: alpha_g / mean gradient magnitude of the previous frame
-        float mean = __fdiv_rn(__ull2float_rn(a.gsum_prev[c]), __ll2float_rn(a.P));
-        mean = fmaxf(mean, 1.0f);
-        const float wgc = __fdiv_rn(a.alpha_g, mean);
-        uint32_t gsc = 0;
-        uint32_t v[PX], g[PX];
+        const float* tab = wtab[c];
+        uint32_t pv[PX];   // this frame's (value | gradient << 8)
         bool act[PX];
         bool any = false;
+        uint32_t gsc = 0;
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             const int col = lx0 + i + 1;
-            v[i] = sm[c * G::CH + (ly + 1) * G::SWP + col];
-            g[i] = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
+            const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
+            const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
+            pv[i] = v | (g << 8);
             act[i] = inb[i] && (c < 3 || sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0);
-            if (inb[i]) gsc += g[i];
+            if (inb[i]) gsc += g;
             any |= act[i];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) cnt6[q] += (q == c) ? gsc : 0u;
+        for (int q = 0; q < 4; ++q) cnt7[q] += (q == c) ? gsc : 0u;
+
+        // neighbour updates of frame t-1: the pixel's own frame-(t-1) value
+        // goes into every slot a neighbour asked for (depth only if it was valid)
+        const int64_t pc = int64_t(c) * a.plane + q0;
+        uint32_t pprev[PX];
+        if (a.apply) {
+            if (vec) {
+                ld16<PX>(a.prev + pc, pprev);
+            } else {
+#pragma unroll
+                for (int i = 0; i < PX; ++i) pprev[i] = inb[i] ? a.prev[pc + i] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < PX; ++i) {
+                // select channel c without dynamic register indexing
+                uint32_t m = c == 0 ? pend[i][0] : (c == 1 ? pend[i][1] : (c == 2 ? pend[i][2] : pend[i][3]));
+                if (c == 3 && (pprev[i] & 0xFFu) == 0u) m = 0u;
+                while (m) {
+                    const int k = __ffs(m) - 1;
+                    m &= m - 1u;
+                    a.samp[sidx(a, N, c, k, x + i, y)] = uint16_t(pprev[i]);
+                    cnt7[5] += 1;
+                }
+            }
+        }
+        if (vec) {
+            st16<PX>(a.prev + pc, pv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PX; ++i)
+                if (inb[i]) a.prev[pc + i] = uint16_t(pv[i]);
+        }
         if (!any) continue;
 
         float Rv[PX], Tv[PX];
         uint32_t Sv[PX];
-        const int64_t pc = int64_t(c) * a.plane + q0;
         if (vec) {
             ldf<PX>(a.R + pc, Rv);
             ldf<PX>(a.T + pc, Tv);
@@ -247,7 +385,11 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
             }
         }
 
-        // distances to the N samples: count within R, minimum
+        // distances to the N samples: count within R, minimum.
+        // dist = fl(fl(wg * |dg|) + |dv|): the product comes from the table.
+        uint32_t own[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) own[w] = pv[2 * w] | (2 * w + 1 < PX ? pv[2 * w + 1] << 16 : 0u);
         int cnt[PX];
         float dmin[PX];
 #pragma unroll
@@ -255,21 +397,25 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
         const int64_t sb = inb[0] ? sidx(a, N, c, 0, x, y) : 0;  // slot 0 of pixel x
 #pragma unroll(NT > 0 ? NT : 4)
         for (int k = 0; k < N; ++k) {
-            uint32_t s[PX];
+            uint32_t s[NW];
             if (vec) {
-                ld16<PX>(a.samp + sb + int64_t(k) * kSeg, s);
+                ldw<PX>(a.samp + sb + int64_t(k) * kSeg, s);
             } else {
-#pragma unroll
-                for (int i = 0; i < PX; ++i)
-                    s[i] = inb[i] ? a.samp[sidx(a, N, c, k, x + i, y)] : 0u;
+                s[0] = inb[0] ? a.samp[sidx(a, N, c, k, x, y)] : 0u;
             }
 #pragma unroll
-            for (int i = 0; i < PX; ++i) {
-                const int dv = abs(int(v[i]) - int(s[i] & 0xFFu));
-                const int dg = abs(int(g[i]) - int(s[i] >> 8));
-                const float dist = __fadd_rn(__fmul_rn(wgc, __int2float_rn(dg)), __int2float_rn(dv));
-                cnt[i] += dist < Rv[i] ? 1 : 0;
-                dmin[i] = fminf(dmin[i], dist);
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t d = __vabsdiffu4(s[w], own[w]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = 2 * w + h;
+                    if (i >= PX) break;
+                    const uint32_t dv = (d >> (16 * h)) & 0xFFu;
+                    const uint32_t dg = (d >> (16 * h + 8)) & 0xFFu;
+                    const float dist = __fadd_rn(tab[dg], small_u2f(dv));
+                    cnt[i] += dist < Rv[i] ? 1 : 0;
+                    dmin[i] = fminf(dmin[i], dist);
+                }
             }
         }
 
@@ -283,15 +429,16 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
             slot[i] = -1;
             oidx[i] = 0;
             if (act[i] && !fg[i]) {
-                const float prob = __fdiv_rn(1.0f, Tv[i]);
+                const float prob = __frcp_rn(Tv[i]);
                 const Draws d = draws(a, pix0 + uint32_t(i), uint32_t(c), prob, N);
                 if (d.coin1) {
                     slot[i] = int(d.k1);
                     oidx[i] = sidx(a, N, c, int(d.k1), x + i, y);
                 }
                 if (d.coin2) {
-                    reqw[i] |= (1u + d.j * uint32_t(N) + d.k2) << (8 * c);
-                    cnt6[5] += 1;
+                    const uint32_t byte = (d.j << 5) | d.k2;
+                    reqw[i] = (reqw[i] & ~(0xFFu << (8 * c))) | (byte << (8 * c));
+                    cnt7[6] += 1;
                 }
             }
             anyfg[i] |= fg[i];
@@ -303,12 +450,12 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             if (slot[i] < 0) continue;
-            a.samp[oidx[i]] = uint16_t(v[i] | (g[i] << 8));
+            a.samp[oidx[i]] = uint16_t(pv[i]);
             const float q16 = __fmul_rn(dmin[i], 16.0f);
             const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
             Sv[i] = Sv[i] + q - dold[i];
             a.Dq[oidx[i]] = uint16_t(q);
-            cnt6[4] += 1;
+            cnt7[4] += 1;
         }
         // adaptive threshold R and learning parameter T
         const float Rlo = c < 3 ? a.R_lower_rgb : a.R_lower_d;
@@ -336,71 +483,56 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
     }
 
     const int64_t p0 = int64_t(y) * a.W + x;  // mask index (unpadded frame)
-    if (vec) {
+    if (vec && a.mask_vec) {
         uint32_t m = 0;
 #pragma unroll
         for (int i = 0; i < PX; ++i) m |= (anyfg[i] ? 255u : 0u) << (8 * i);
-        *reinterpret_cast<uint32_t*>(a.mask + p0) = m;
-        stu<PX>(a.req + q0, reqw);
+        if constexpr (PX == 4) *reinterpret_cast<uint32_t*>(a.mask + p0) = m;
+        else *reinterpret_cast<uint16_t*>(a.mask + p0) = uint16_t(m);
     } else {
 #pragma unroll
         for (int i = 0; i < PX; ++i)
-            if (inb[i]) { a.mask[p0 + i] = anyfg[i] ? 255 : 0; a.req[q0 + i] = reqw[i]; }
+            if (inb[i]) a.mask[p0 + i] = anyfg[i] ? 255 : 0;
+    }
+    if (vec) {
+        stu<PX>(a.req_cur + q0, reqw);
+    } else {
+#pragma unroll
+        for (int i = 0; i < PX; ++i)
+            if (inb[i]) a.req_cur[q0 + i] = reqw[i];
     }
 
-    block_add<TY, 6>(cnt6, [&](int q) { return q < 4 ? a.gsum_cur + q : a.counters + (q == 4 ? 0 : 2); });
+    block_add<TY, 7>(cnt7, [&](int q) {
+        return q < 4 ? a.gsum_cur + q : a.counters + (q == 4 ? 0 : (q == 5 ? 1 : 2));
+    });
 }
 
-template <int NT, int PX, int TY>
-__global__ void __launch_bounds__(32 * TY) pbas_neighbour_kernel(const PbasArgs a)
+// Applies the pending neighbour requests of the last frame to the samples
+// without classifying (so that an exported state includes them).
+template <int NT, int TY>
+__global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
 {
-    using G = Geo<PX, TY>;
-    __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    using G = Geo<1, TY>;
     __shared__ uint32_t sreq[G::SH * G::SW];
     const int N = NT > 0 ? NT : a.N;
     const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
-    stage_input<PX, TY>(a, x0, y0, sm);
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int idx = tid; idx < G::SH * G::SW; idx += 32 * TY) {
-        const int r = idx / G::SW, col = idx - r * G::SW;
-        const int gx = x0 - 1 + col, gy = y0 - 1 + r;
-        const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
-        sreq[idx] = in ? a.req[int64_t(gy) * a.Wp + gx] : 0u;
-    }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid < 4) {
-        // this frame's classify pass has consumed the previous frame's sums;
-        // the buffer becomes the next frame's accumulator
-        a.gsum_prev[tid] = 0ull;
-    }
+    stage_requests<1, TY>(a, x0, y0, sreq);
     __syncthreads();
-
-    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
-    const int x = x0 + lx0, y = y0 + ly;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     uint32_t applied[1] = {0};
+    if (x < a.W && y < a.H) {
+        uint32_t pend[4];
+        pending_masks<G::SW>(sreq, threadIdx.y, threadIdx.x + 1, pend);
+        const int64_t q = int64_t(y) * a.Wp + x;
 #pragma unroll
-    for (int i = 0; i < PX; ++i) {
-        if (y >= a.H || x + i >= a.W) continue;
-        const int col = lx0 + i + 1;
-        const bool dvalid = sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0;
-        uint32_t cached[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            // the neighbour at -dir(j) targets this pixel when its direction is j
-            const uint32_t r = sreq[(ly + 1 - dir_dy(j)) * G::SW + (col - dir_dx(j))];
-            if (r == 0) continue;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t b = (r >> (8 * c)) & 0xFFu;
-                if (b == 0) continue;
-                const uint32_t code = b - 1u;
-                const uint32_t jj = code / uint32_t(N);
-                if (jj != uint32_t(j) || (c == 3 && !dvalid)) continue;
-                const uint32_t k2 = code - jj * uint32_t(N);
-                if (cached[c] == 0xFFFFFFFFu) {
-                    const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
-                    cached[c] = v | (sobel(sm + c * G::CH, G::SWP, ly + 1, col) << 8);
-                }
-                a.samp[sidx(a, N, c, int(k2), x + i, y)] = uint16_t(cached[c]);
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t pv = a.prev[int64_t(c) * a.plane + q];
+            uint32_t m = pend[c];
+            if (c == 3 && (pv & 0xFFu) == 0u) m = 0u;
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1u;
+                a.samp[sidx(a, N, c, k, x, y)] = uint16_t(pv);
                 applied[0] += 1;
             }
         }
@@ -415,7 +547,9 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
     __shared__ __align__(16) uint8_t sm[4 * G::CH];
     const int N = NT > 0 ? NT : a.N;
     const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     stage_input<PX, TY>(a, x0, y0, sm);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid < 4) a.gsum_next[tid] = 0ull;
     __syncthreads();
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
     const int x = x0 + lx0, y = y0 + ly;
@@ -439,9 +573,9 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
             a.R[int64_t(c) * a.plane + q] = c < 3 ? a.R_lower_rgb : a.R_lower_d;
             a.T[int64_t(c) * a.plane + q] = a.T_lower;
             a.S[int64_t(c) * a.plane + q] = 0u;
+            a.prev[int64_t(c) * a.plane + q] = sv;
         }
         a.mask[int64_t(y) * a.W + x + i] = 0;
-        a.req[q] = 0u;
     }
     block_add<TY, 4>(gs, [&](int q) { return a.gsum_cur + q; });
 }
@@ -452,25 +586,56 @@ dim3 grid_for(const PbasArgs& a)
     return dim3(unsigned((a.W + 32 * PX - 1) / (32 * PX)), unsigned((a.H + TY - 1) / TY));
 }
 
+// Tile shapes: PX pixels per thread (vector accesses) when W is a multiple of
+// PX, TY rows per block; otherwise one pixel per thread, 8 rows, with bounds
+// checks on every access.
+#define FOS_PBAS_LAUNCHER(NAME, KERNEL)                                                   \
+    template <int NT, int PX, int TY>                                                     \
+    void NAME##_go(const PbasArgs& a, cudaStream_t s)                                     \
+    {                                                                                     \
+        KERNEL<NT, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a);               \
+    }                                                                                     \
+    template <int NT>                                                                     \
+    bool NAME##_shape(const PbasArgs& a, cudaStream_t s, int px, int ty)                  \
+    {                                                                                     \
+        if (px == 4 && ty == 4) NAME##_go<NT, 4, 4>(a, s);                                \
+        else if (px == 4 && ty == 2) NAME##_go<NT, 4, 2>(a, s);                           \
+        else if (px == 4 && ty == 8) NAME##_go<NT, 4, 8>(a, s);                           \
+        else if (px == 2 && ty == 4) NAME##_go<NT, 2, 4>(a, s);                           \
+        else if (px == 2 && ty == 8) NAME##_go<NT, 2, 8>(a, s);                           \
+        else if (px == 1) NAME##_go<NT, 1, 8>(a, s);                                      \
+        else return false;                                                                \
+        return true;                                                                      \
+    }                                                                                     \
+    LaunchResult NAME(const PbasArgs& a, cudaStream_t s)                                  \
+    {                                                                                     \
+        if (a.P == 0) return kLaunchOk;                                                   \
+        const int px = (a.px > 1 && a.W % a.px == 0) ? a.px : 1;                          \
+        const bool ok = a.N == 20 ? NAME##_shape<20>(a, s, px, a.ty) : NAME##_shape<0>(a, s, px, a.ty); \
+        if (!ok) return kLaunchUnsupported;                                               \
+        return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;          \
+    }
+
 }  // namespace
 
-#define FOS_PBAS_DISPATCH(KERNEL)                                                       \
-    if (a.P == 0) return kLaunchOk;                                                     \
-    if (a.vec_ok) {                                                                     \
-        constexpr int PX = 4, TY = 4;                                                   \
-        if (a.N == 20) KERNEL<20, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a); \
-        else KERNEL<0, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a);          \
-    } else {                                                                            \
-        constexpr int PX = 1, TY = 8;                                                   \
-        if (a.N == 20) KERNEL<20, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a); \
-        else KERNEL<0, PX, TY><<<grid_for<PX, TY>(a), dim3(32, TY), 0, s>>>(a);          \
-    }                                                                                   \
+namespace {
+FOS_PBAS_LAUNCHER(init_launch, pbas_init_kernel)
+FOS_PBAS_LAUNCHER(classify_launch, pbas_classify_kernel)
+}  // namespace
+
+LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s) { return init_launch(a, s); }
+LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s) { return classify_launch(a, s); }
+
+LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s)
+{
+    if (a.P == 0) return kLaunchOk;
+    constexpr int TY = 8;
+    const dim3 grid = grid_for<1, TY>(a);
+    if (a.N == 20) pbas_flush_kernel<20, TY><<<grid, dim3(32, TY), 0, s>>>(a);
+    else pbas_flush_kernel<0, TY><<<grid, dim3(32, TY), 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+}
 
-LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s) { FOS_PBAS_DISPATCH(pbas_init_kernel) }
-LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s) { FOS_PBAS_DISPATCH(pbas_classify_kernel) }
-LaunchResult launch_pbas_neighbour(const PbasArgs& a, cudaStream_t s) { FOS_PBAS_DISPATCH(pbas_neighbour_kernel) }
-
-#undef FOS_PBAS_DISPATCH
+#undef FOS_PBAS_LAUNCHER
 
 }  // namespace fos

@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_PKG, "libfos.so")
 
 METHOD_GMM = 1
 METHOD_PBAS = 2
-KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_NEIGHBOUR, KERNEL_INIT = 0, 1, 2, 3
-KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_neighbour", "init")
+KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_FLUSH, KERNEL_INIT = 0, 1, 2, 3
+KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_flush", "init")
 STATUS = {0: "FOS_OK", 1: "FOS_ERR_INVALID_ARG", 2: "FOS_ERR_CUDA", 3: "FOS_ERR_OOM",
           4: "FOS_ERR_TIMEOUT", 5: "FOS_ERR_BUDGET", 6: "FOS_ERR_STATE", 7: "FOS_ERR_UNSUPPORTED"}
 
@@ -87,7 +87,10 @@ SIGNATURES = {
     "fos_set_timing": (_st, [_vp, _u32]),
     "fos_get_timing": (_st, [_vp, ctypes.POINTER(KernelTiming)]),
     "fos_get_counters": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "fos_set_option": (_st, [_vp, _i32, _i32]),
+    "fos_get_option": (_i32, [_vp, _i32]),
 }
+OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY = 1, 2, 3, 4
 
 _lib = None
 
@@ -254,6 +257,12 @@ class Segmenter:
         arr = (KernelTiming * 4)()
         self._check(self.lib.fos_get_timing(self.h, arr))
         return {KERNEL_NAMES[k]: (arr[k].launches, arr[k].total_ms) for k in range(4)}
+
+    def set_option(self, option: int, value: int) -> None:
+        self._check(self.lib.fos_set_option(self.h, option, value))
+
+    def get_option(self, option: int) -> int:
+        return int(self.lib.fos_get_option(self.h, option))
 
     def get_counters(self) -> dict:
         arr = (ctypes.c_uint64 * 4)()

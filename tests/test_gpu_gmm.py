@@ -125,3 +125,18 @@ def test_constant_input_closed_form():
     np.testing.assert_allclose(st["w_rgb"][:, 0], 1.0, rtol=1e-6)
     np.testing.assert_allclose(st["v_rgb"][:, 0], max(4.0, 36 * 0.99 ** (n - 1)), rtol=1e-4)
     assert (st["mu_d"][:, 0] == 51).all()
+
+
+@pytest.mark.parametrize("px,tpb", [(1, 128), (2, 64), (2, 256), (4, 256)])
+def test_kernel_shapes_give_identical_bits(px, tpb):
+    from paper_2002_00250_gb300 import fos
+    W, H, n = 200, 30, 8
+    rgb, depth, _ = scene(W, H, n, seed=6)
+    ref = _seg(W, H, alpha=0.05)
+    mr, _ = ref.process_host(rgb, depth)
+    seg = _seg(W, H, alpha=0.05)
+    seg.set_option(fos.OPT_GMM_PX, px)
+    seg.set_option(fos.OPT_GMM_TPB, tpb)
+    ms, _ = seg.process_host(rgb, depth)
+    np.testing.assert_array_equal(ms, mr)
+    np.testing.assert_array_equal(seg.get_state(), ref.get_state())

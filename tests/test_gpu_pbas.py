@@ -103,3 +103,23 @@ def test_480p_full_run(orc):
     assert_same(seg.decode_state().pbas, p, n - 1)
     c = seg.get_counters()
     assert c["frames"] == n and c["own_updates"] > 0 and c["neighbour_writes"] > 0
+
+
+def test_pending_updates_applied_by_next_frame(orc):
+    # state read back only every 4th frame: the neighbour updates of the other
+    # frames are applied inside the next frame's classify pass, not by a flush
+    run_parity(orc, 96, 30, 17, seed=5, every=4)
+
+
+@pytest.mark.parametrize("px,ty", [(4, 2), (4, 8), (2, 4), (2, 8), (1, 8)])
+def test_tile_shapes_give_identical_bits(px, ty):
+    from paper_2002_00250_gb300 import fos
+    W, H, n = 136, 40, 9
+    rgb, depth, _ = scene(W, H, n, seed=3)
+    ref = _seg(W, H)
+    ref.process_host(rgb, depth)
+    seg = _seg(W, H)
+    seg.set_option(fos.OPT_PBAS_PX, px)
+    seg.set_option(fos.OPT_PBAS_TY, ty)
+    seg.process_host(rgb, depth)
+    np.testing.assert_array_equal(seg.get_state(), ref.get_state())
