@@ -216,7 +216,7 @@ fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
 /* ---------------------------------------------------------------------------
  * Kernel shapes (tuning).  Results do not depend on them: every shape computes
  * the same bits.  Defaults: GMM 4 pixels per thread, 128 threads per block;
- * PBAS 2 pixels per thread (when the width is a multiple of it), 4 rows.
+ * PBAS 2 pixels per thread (when the width is a multiple of it), 8 rows.
  * ------------------------------------------------------------------------- */
 #define FOS_OPT_GMM_PX 1   /* GMM pixels per thread: 1, 2, 4 (3+3 components) */
 #define FOS_OPT_GMM_TPB 2  /* GMM threads per block: 64, 128, 256 */

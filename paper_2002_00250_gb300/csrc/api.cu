@@ -48,9 +48,9 @@ struct fos_ctx {
     float* T = nullptr;
     uint32_t* S = nullptr;
     uint32_t* req = nullptr;            // [2][pplane] requests of even / odd frames
-    uint16_t* prev = nullptr;           // [4][pplane]
+    uint64_t* prev = nullptr;           // [pplane]
     bool pending = false;               // requests of the last frame not yet applied
-    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 4};  // kernel shapes (fos_set_option)
+    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8};  // kernel shapes (fos_set_option)
     unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
     uint8_t* h_rgb[2] = {nullptr, nullptr};  // device staging for host frames
     uint16_t* h_depth[2] = {nullptr, nullptr};
@@ -383,7 +383,7 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
         if ((e = cudaMalloc(&c->T, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
         if ((e = cudaMalloc(&c->S, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
         if ((e = cudaMalloc(&c->req, 2 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
-        if ((e = cudaMalloc(&c->prev, 4 * pp * 2)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
+        if ((e = cudaMalloc(&c->prev, pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
     if ((e = cudaMalloc(&c->aux, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
     if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);

@@ -40,11 +40,12 @@ LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
 // so the N slots of one channel of one segment are 256-byte rows of one
 // contiguous block: a warp reads each slot with one coalesced 256-byte access
 // and its random own/neighbour slot writes land in the block it just read.
-// R, T, S, prev (per channel) and the request words are planes with row pitch
+// R, T, S (per channel), prev and the request words are planes with row pitch
 // Wp = spr * 128; plane stride `plane` = Wp * H.
 // Request word of a pixel: byte c = (direction << 5) | slot for channel c, or
-// 0x1F for no request.  prev holds (value | gradient << 8) per channel of the
-// last processed frame (the value neighbour requests write).
+// 0x1F for no request.  prev holds, per pixel, 16 bits (value | gradient << 8)
+// for each channel c at bit 16c, of the last processed frame (the value the
+// neighbour requests write).
 constexpr int kSeg = 128;
 constexpr uint32_t kReqNone4 = 0x1F1F1F1Fu;
 
@@ -61,7 +62,7 @@ struct PbasArgs {
     float* R;
     float* T;
     uint32_t* S;
-    uint16_t* prev;
+    uint64_t* prev;                 // [pplane] 4 x (value | gradient << 8) of frame t-1
     const uint32_t* req_prev;       // requests of frame t-1 (read)
     uint32_t* req_cur;              // requests of frame t (written)
     unsigned long long* gsum_prev;  // [4] gradient sums of frame t-1

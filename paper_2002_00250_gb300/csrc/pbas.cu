@@ -95,25 +95,32 @@ __device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int 
     return uint32_t(m > 255 ? 255 : m);
 }
 
-// Pending neighbour writes for the pixel at staged column `col`, row ly+1:
-// pend[c] gets bit k for every neighbour whose request of channel c points at
-// this pixel with slot k.  A request byte is (direction << 5) | slot; 0x1F is
-// "no request".
+// Neighbour requests that point at the pixel at staged column `col`, row
+// ly+1, as a 32-bit mask: bit 4*j + c is set when the neighbour at -dir(j)
+// asked, for channel c, to write into this pixel (its request byte for c is
+// (j << 5) | slot; 0x1F means no request).
 template <int SW>
-__device__ __forceinline__ void pending_masks(const uint32_t* sreq, int ly, int col, uint32_t (&pend)[4])
+__device__ __forceinline__ uint32_t request_matches(const uint32_t* sreq, int ly, int col)
 {
-    pend[0] = pend[1] = pend[2] = pend[3] = 0u;
+    uint32_t mm = 0u;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const uint32_t r = sreq[(ly + 1 - dir_dy(j)) * SW + (col - dir_dx(j))];
-        const uint32_t m = __vcmpeq4(r & 0xE0E0E0E0u, uint32_t(j << 5) * 0x01010101u) &
-                           ~__vcmpeq4(r & 0x1F1F1F1Fu, 0x1F1F1F1Fu);
-        if (m) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if ((m >> (8 * c)) & 0xFFu) pend[c] |= 1u << ((r >> (8 * c)) & 31u);
-        }
+        const uint32_t dir_ok = __vcmpeq4(r & 0xE0E0E0E0u, uint32_t(j << 5) * 0x01010101u);
+        const uint32_t has = __vcmpne4(r & 0x1F1F1F1Fu, 0x1F1F1F1Fu);
+        const uint32_t m = dir_ok & has & 0x08040201u;  // bit c of byte c
+        mm |= ((m * 0x01010101u) >> 24) << (4 * j);     // gather the 4 bits
     }
+    return mm;
+}
+
+// Slot requested by the neighbour at -dir(j) for channel c (a match exists).
+template <int SW>
+__device__ __forceinline__ int request_slot(const uint32_t* sreq, int ly, int col, int j, int c)
+{
+    const int dy = (j == 2 || j == 6) ? 0 : ((j < 2 || j == 7) ? -1 : 1);
+    const int dx = (j == 0 || j == 4) ? 0 : (j < 4 ? 1 : -1);
+    return int((sreq[(ly + 1 - dy) * SW + (col - dx)] >> (8 * c)) & 31u);
 }
 
 // PX pixels of uint16 / float / uint32 planes; PX = 4 uses one vector access.
@@ -260,13 +267,6 @@ __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c
     return d;
 }
 
-// Exact float of a small non-negative integer (< 2^23) without a conversion
-// instruction: 2^23 + v is representable, so subtracting 2^23 is exact.
-__device__ __forceinline__ float small_u2f(uint32_t v)
-{
-    return __fsub_rn(__uint_as_float(0x4B000000u | v), 8388608.0f);
-}
-
 template <int NT, int PX, int TY>
 __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
 {
@@ -300,22 +300,52 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
     const int64_t q0 = int64_t(y) * a.Wp + x;   // index in the pitched planes
     const uint32_t pix0 = uint32_t(y) * uint32_t(a.W) + uint32_t(x);  // Philox counter
     const bool vec = (PX > 1) && inb[0];  // W % PX == 0 on this path: all PX in frame
-
-    uint32_t pend[PX][4];
-#pragma unroll
-    for (int i = 0; i < PX; ++i) {
-        pend[i][0] = pend[i][1] = pend[i][2] = pend[i][3] = 0u;
-        if (a.apply && inb[i]) pending_masks<G::SW>(sreq, ly, lx0 + i + 1, pend[i]);
-    }
-
-    const float omr = __fsub_rn(1.0f, a.R_incdec), opr = __fadd_rn(1.0f, a.R_incdec);
-    const float n16 = __int2float_rn(16 * N);
-
     uint32_t reqw[PX];
     bool anyfg[PX];
 #pragma unroll
     for (int i = 0; i < PX; ++i) { reqw[i] = kReqNone4; anyfg[i] = false; }
     uint32_t cnt7[7] = {0, 0, 0, 0, 0, 0, 0};  // gsum R,G,B,D; own; neighbour writes; requests
+
+    // Neighbour updates of frame t-1: this pixel's own frame-(t-1) value (prev,
+    // 4 channels x (value | gradient << 8)) goes into every slot a neighbour
+    // asked for; depth only if it was valid.  Written before any sample of
+    // this pixel is read below, so this frame sees the updated model.
+    if (a.apply) {
+        uint64_t pw[PX];
+        if (vec) {
+            if constexpr (PX == 4) {
+                const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(a.prev + q0);
+                const ulonglong2 u1 = *reinterpret_cast<const ulonglong2*>(a.prev + q0 + 2);
+                pw[0] = u0.x; pw[1] = u0.y; pw[2] = u1.x; pw[3] = u1.y;
+            } else if constexpr (PX == 2) {
+                const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(a.prev + q0);
+                pw[0] = u0.x; pw[1] = u0.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < PX; ++i) pw[i] = inb[i] ? a.prev[q0 + i] : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            uint32_t mm = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1) : 0u;
+            if (((pw[i] >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;  // depth was invalid
+            while (mm) {
+                const int b = __ffs(mm) - 1;
+                mm &= mm - 1u;
+                const int j = b >> 2, c = b & 3;
+                const int k = request_slot<G::SW>(sreq, ly, lx0 + i + 1, j, c);
+                a.samp[sidx(a, N, c, k, x + i, y)] = uint16_t(pw[i] >> (16 * c));
+                cnt7[5] += 1;
+            }
+        }
+    }
+    uint64_t pnew[PX];  // this frame's (value | gradient << 8) per channel
+#pragma unroll
+    for (int i = 0; i < PX; ++i) pnew[i] = 0ull;
+
+    const float omr = __fsub_rn(1.0f, a.R_incdec), opr = __fadd_rn(1.0f, a.R_incdec);
+    const float n16 = __int2float_rn(16 * N);
+
 
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
@@ -337,37 +367,9 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
 #pragma unroll
         for (int q = 0; q < 4; ++q) cnt7[q] += (q == c) ? gsc : 0u;
 
-        // neighbour updates of frame t-1: the pixel's own frame-(t-1) value
-        // goes into every slot a neighbour asked for (depth only if it was valid)
         const int64_t pc = int64_t(c) * a.plane + q0;
-        uint32_t pprev[PX];
-        if (a.apply) {
-            if (vec) {
-                ld16<PX>(a.prev + pc, pprev);
-            } else {
 #pragma unroll
-                for (int i = 0; i < PX; ++i) pprev[i] = inb[i] ? a.prev[pc + i] : 0u;
-            }
-#pragma unroll
-            for (int i = 0; i < PX; ++i) {
-                // select channel c without dynamic register indexing
-                uint32_t m = c == 0 ? pend[i][0] : (c == 1 ? pend[i][1] : (c == 2 ? pend[i][2] : pend[i][3]));
-                if (c == 3 && (pprev[i] & 0xFFu) == 0u) m = 0u;
-                while (m) {
-                    const int k = __ffs(m) - 1;
-                    m &= m - 1u;
-                    a.samp[sidx(a, N, c, k, x + i, y)] = uint16_t(pprev[i]);
-                    cnt7[5] += 1;
-                }
-            }
-        }
-        if (vec) {
-            st16<PX>(a.prev + pc, pv);
-        } else {
-#pragma unroll
-            for (int i = 0; i < PX; ++i)
-                if (inb[i]) a.prev[pc + i] = uint16_t(pv[i]);
-        }
+        for (int i = 0; i < PX; ++i) pnew[i] |= uint64_t(pv[i]) << (16 * c);
         if (!any) continue;
 
         float Rv[PX], Tv[PX];
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
                     if (i >= PX) break;
                     const uint32_t dv = (d >> (16 * h)) & 0xFFu;
                     const uint32_t dg = (d >> (16 * h + 8)) & 0xFFu;
-                    const float dist = __fadd_rn(tab[dg], small_u2f(dv));
+                    const float dist = __fadd_rn(tab[dg], __uint2float_rn(dv));
                     cnt[i] += dist < Rv[i] ? 1 : 0;
                     dmin[i] = fminf(dmin[i], dist);
                 }
@@ -482,6 +484,19 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
         }
     }
 
+    if (vec) {
+        if constexpr (PX == 4) {
+            *reinterpret_cast<ulonglong2*>(a.prev + q0) = make_ulonglong2(pnew[0], pnew[1]);
+            *reinterpret_cast<ulonglong2*>(a.prev + q0 + 2) = make_ulonglong2(pnew[2], pnew[3]);
+        } else if constexpr (PX == 2) {
+            *reinterpret_cast<ulonglong2*>(a.prev + q0) = make_ulonglong2(pnew[0], pnew[1]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < PX; ++i)
+            if (inb[i]) a.prev[q0 + i] = pnew[i];
+    }
+
     const int64_t p0 = int64_t(y) * a.W + x;  // mask index (unpadded frame)
     if (vec && a.mask_vec) {
         uint32_t m = 0;
@@ -521,20 +536,16 @@ __global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     uint32_t applied[1] = {0};
     if (x < a.W && y < a.H) {
-        uint32_t pend[4];
-        pending_masks<G::SW>(sreq, threadIdx.y, threadIdx.x + 1, pend);
-        const int64_t q = int64_t(y) * a.Wp + x;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const uint32_t pv = a.prev[int64_t(c) * a.plane + q];
-            uint32_t m = pend[c];
-            if (c == 3 && (pv & 0xFFu) == 0u) m = 0u;
-            while (m) {
-                const int k = __ffs(m) - 1;
-                m &= m - 1u;
-                a.samp[sidx(a, N, c, k, x, y)] = uint16_t(pv);
-                applied[0] += 1;
-            }
+        const uint64_t pw = a.prev[int64_t(y) * a.Wp + x];
+        uint32_t mm = request_matches<G::SW>(sreq, threadIdx.y, threadIdx.x + 1);
+        if (((pw >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;  // depth was invalid
+        while (mm) {
+            const int b = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            const int j = b >> 2, c = b & 3;
+            const int k = request_slot<G::SW>(sreq, threadIdx.y, threadIdx.x + 1, j, c);
+            a.samp[sidx(a, N, c, k, x, y)] = uint16_t(pw >> (16 * c));
+            applied[0] += 1;
         }
     }
     block_add<TY, 1>(applied, [&](int) { return a.counters + 1; });
@@ -559,6 +570,7 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
         if (y >= a.H || x + i >= a.W) continue;
         const int col = lx0 + i + 1;
         const int64_t q = int64_t(y) * a.Wp + x + i;
+        uint64_t pw = 0ull;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
@@ -573,8 +585,9 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
             a.R[int64_t(c) * a.plane + q] = c < 3 ? a.R_lower_rgb : a.R_lower_d;
             a.T[int64_t(c) * a.plane + q] = a.T_lower;
             a.S[int64_t(c) * a.plane + q] = 0u;
-            a.prev[int64_t(c) * a.plane + q] = sv;
+            pw |= uint64_t(sv) << (16 * c);
         }
+        a.prev[q] = pw;
         a.mask[int64_t(y) * a.W + x + i] = 0;
     }
     block_add<TY, 4>(gs, [&](int q) { return a.gsum_cur + q; });
