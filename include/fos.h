@@ -108,7 +108,7 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params);
 void fos_destroy(fos_ctx* ctx);
 
 /* Text of the context's last error ("" if none); ctx == NULL gives the calling
- * thread's last fos_create error.  The pointer stays valid until the next call
+ * thread's last fos_create or fos_pbas_step_noalloc error.  The pointer stays valid until the next call
  * on the same context / thread. */
 const char* fos_last_error(const fos_ctx* ctx);
 
@@ -236,6 +236,54 @@ int32_t fos_get_option(const fos_ctx* ctx, int32_t option);
  * out[2] neighbour requests issued, out[3] frames.
  */
 fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4]);
+
+/* ---------------------------------------------------------------------------
+ * One PBAS frame step that allocates nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory while they process frames -- plug-ins whose
+ * host framework owns all device memory and forbids allocation while its
+ * pipeline runs, real-time capture callbacks that cannot afford cudaMalloc's
+ * implicit synchronisation and latency, and code that must leave the
+ * allocator alone while other work may be capturing streams.  The caller owns
+ * the model and the frame buffers; the library keeps its per-frame scratch
+ * (neighbour-request words, the frame's value/gradient words, counters) in a
+ * fixed array in device memory that every GPU loading the library holds until
+ * the process exits (about 24 MB).  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *
+ * Computes exactly what a context with methods = FOS_METHOD_PBAS computes for
+ * frame `frame_index` (same parameters, same bits), and additionally applies
+ * this frame's neighbour updates before returning, so the model it leaves
+ * equals fos_get_state of such a context after the same frame.
+ *
+ * width, height: 128*ceil(width/128)*height must not exceed
+ *     FOS_NOALLOC_MAX_PIXELS, else FOS_ERR_INVALID_ARG.
+ * params: PBAS fields are used (methods is ignored).
+ * frame_index: 0 initialises the model from the frame; later calls must come
+ *     in order 1, 2, ... on the same model.
+ * d_rgb, d_depth, d_mask: device frame buffers as for fos_process_frame_device.
+ * d_model: caller-allocated device buffer of
+ *     16*N*Sp + 48*Sp + 96 bytes, Sp = 128*ceil(width/128)*height, holding
+ *     (offsets in bytes) samples uint16 [4][Sp/128 segments][N][128] at 0,
+ *     D uint16 (same shape) at 8*N*Sp, R float32 [4][Sp] at 16*N*Sp,
+ *     T float32 [4][Sp] at 16*N*Sp + 16*Sp, S uint32 [4][Sp] at
+ *     16*N*Sp + 32*Sp, gradient sums uint64 [3][4] at 16*N*Sp + 48*Sp.
+ *     256-byte aligned.  Its contents need no initialisation before frame 0.
+ * stream: cudaStream_t (NULL = legacy default stream); asynchronous.
+ *
+ * The first call on a device looks up the scratch array's device address;
+ * make that first call before any stream capture begins.  All calls share
+ * the one scratch array: calls whose kernels may overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Errors: status code, text from fos_last_error(NULL) on the calling thread.
+ * ------------------------------------------------------------------------- */
+#define FOS_NOALLOC_MAX_PIXELS 2097152
+
+fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const fos_params* params,
+                                 int64_t frame_index, const uint8_t* d_rgb,
+                                 const uint16_t* d_depth, void* d_model, uint8_t* d_mask,
+                                 void* stream);
 
 #ifdef __cplusplus
 }

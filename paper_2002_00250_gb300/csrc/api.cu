@@ -319,6 +319,8 @@ void block_samples(const fos_ctx* c, const uint16_t* planes, uint16_t* blocked)
 
 }  // namespace
 
+void fos::set_thread_error(const char* msg) { g_create_error = msg; }
+
 extern "C" {
 
 void fos_default_params(fos_params* p)

@@ -85,4 +85,7 @@ LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);
 
+// Sets the text fos_last_error(NULL) returns on the calling thread.
+void set_thread_error(const char* msg);
+
 }  // namespace fos

@@ -89,6 +89,7 @@ SIGNATURES = {
     "fos_get_counters": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "fos_set_option": (_st, [_vp, _i32, _i32]),
     "fos_get_option": (_i32, [_vp, _i32]),
+    "fos_pbas_step_noalloc": (_st, [_i32, _i32, ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp]),
 }
 OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY = 1, 2, 3, 4
 
