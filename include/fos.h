@@ -238,6 +238,71 @@ int32_t fos_get_option(const fos_ctx* ctx, int32_t option);
 fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4]);
 
 /* ---------------------------------------------------------------------------
+ * Batched multi-stream processing.  No counterpart in the paper (one stream
+ * there); many camera streams share one GPU.
+ *
+ * A batch owns up to max_streams stream contexts that share every parameter
+ * except stream_id.  fos_batch_process_device runs one frame of any subset of
+ * them as ONE CUDA graph replay on the caller's stream: a copy of the
+ * per-stream kernel arguments, then a persistent GMM kernel and a persistent
+ * PBAS kernel that walk all streams' tiles.  Per-stream results are
+ * bit-identical to fos_process_frame_device on a lone context.  Streams may
+ * join at any time (their first frame is their frame 0) and leave between
+ * steps.  A batch is not thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct fos_batch fos_batch;
+
+typedef struct fos_batch_tuning {
+    int32_t gmm_px;     /* GMM pixels per thread in the batched kernel (1, 2) */
+    int32_t pbas_px;    /* PBAS pixels per thread (1, 2, 4) */
+    int32_t pbas_ty;    /* PBAS tile rows (4, 8) */
+    float ms_per_step;  /* measured time of one step with that shape */
+} fos_batch_tuning;
+
+/* Device memory one stream context of this size holds (its models and
+ * scratch planes; frame and mask buffers not included).  0 on bad input. */
+size_t fos_stream_device_bytes(int32_t width, int32_t height, const fos_params* params);
+
+/* Creates an empty batch (device argument buffers, pinned host buffers).
+ * NULL on error (reason in fos_last_error(NULL)). */
+fos_batch* fos_batch_create(int32_t max_streams, const fos_params* params);
+/* Destroys the batch and every stream it still holds.  NULL-safe. */
+void fos_batch_destroy(fos_batch* b);
+/* Last error of the batch ("" if none). */
+const char* fos_batch_last_error(const fos_batch* b);
+/* Adds a width x height stream with the batch's parameters and this Philox
+ * stream id; returns its slot (>= 0), or -1 (batch full: the batch error says
+ * so; device memory exhausted: FOS_ERR_OOM text). */
+int32_t fos_batch_add_stream(fos_batch* b, int32_t width, int32_t height, uint32_t stream_id);
+/* Removes a stream between steps (waits for steps in flight) and frees it. */
+fos_status fos_batch_remove_stream(fos_batch* b, int32_t slot);
+/* The context of a slot (owned by the batch): for fos_get_state, fos_reset,
+ * fos_frame_index.  NULL for an empty slot. */
+fos_ctx* fos_batch_stream(fos_batch* b, int32_t slot);
+/*
+ * One frame of n distinct streams: for i < n, stream slots[i] processes the
+ * device frame d_rgb[i], d_depth[i] and writes d_mask_gmm[i] / d_mask_pbas[i]
+ * (host arrays of device pointers; mask arrays may be NULL for a disabled
+ * method).  Asynchronous on `stream`; the pointer arrays are read before the
+ * call returns.
+ */
+fos_status fos_batch_process_device(fos_batch* b, int32_t n, const int32_t* slots,
+                                    const uint8_t* const* d_rgb, const uint16_t* const* d_depth,
+                                    uint8_t* const* d_mask_gmm, uint8_t* const* d_mask_pbas,
+                                    void* stream);
+/* Sets the kernel shapes of the batched launch (see fos_batch_tuning). */
+fos_status fos_batch_set_shape(fos_batch* b, int32_t gmm_px, int32_t pbas_px, int32_t pbas_ty);
+/*
+ * Autotuner: times every compiled shape on copies of the listed streams fed
+ * the given frames (throwaway contexts; the batch's own models are not
+ * touched), picks the fastest and sets it on the batch.  Synchronous;
+ * allocates temporary device memory.  `out` (nullable) receives the choice.
+ */
+fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
+                              const uint8_t* const* d_rgb, const uint16_t* const* d_depth,
+                              void* stream, fos_batch_tuning* out);
+
+/* ---------------------------------------------------------------------------
  * One PBAS frame step that allocates nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that

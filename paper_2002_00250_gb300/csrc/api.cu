@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "fos.h"
 #include "fos_internal.h"
 
@@ -22,48 +23,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
-struct TimedLaunch {
-    int kind;
-    cudaEvent_t start, stop;
-};
-
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
-struct fos_ctx {
-    int W = 0, H = 0;
-    int64_t P = 0, plane = 0;       // GMM planes: P padded to 128
-    int Wp = 0, spr = 0;            // PBAS: row pitch, 128-pixel segments per row
-    int64_t nseg = 0, pplane = 0;   // PBAS: segments, plane stride (Wp * H)
-    fos_params prm{};
-    int64_t t = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;       // host-pointer API: kernels + mask copies
-    cudaStream_t copy_stream = nullptr;  // host-pointer API: input copies
-    float* gmm = nullptr;
-    uint16_t* samp = nullptr;
-    uint16_t* Dq = nullptr;
-    float* R = nullptr;
-    float* T = nullptr;
-    uint32_t* S = nullptr;
-    uint32_t* req = nullptr;            // [2][pplane] requests of even / odd frames
-    uint64_t* prev = nullptr;           // [pplane]
-    bool pending = false;               // requests of the last frame not yet applied
-    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8};  // kernel shapes (fos_set_option)
-    unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
-    uint8_t* h_rgb[2] = {nullptr, nullptr};  // device staging for host frames
-    uint16_t* h_depth[2] = {nullptr, nullptr};
-    uint8_t* h_mg[2] = {nullptr, nullptr};
-    uint8_t* h_mp[2] = {nullptr, nullptr};
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
-    uint32_t timing_mask = 0;
-    std::vector<TimedLaunch> timed;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    uint64_t frames_since_counters = 0;
-    std::string err;
-};
 
 namespace {
 
@@ -204,6 +167,23 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     return a;
 }
 
+GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mg)
+{
+    GmmArgs a{};
+    const fos_params& p = c->prm;
+    a.P = c->P; a.plane = c->plane; a.state = c->gmm;
+    a.rgb = rgb; a.depth = depth; a.mask = mg;
+    a.alpha = p.alpha; a.lam2 = p.lambda * p.lambda; a.w_depth = p.w_depth; a.T_bg = p.T_bg;
+    a.v_init_rgb = p.v_init_rgb; a.v_init_d = p.v_init_d;
+    a.v_min_rgb = p.v_min_rgb; a.v_min_d = p.v_min_d;
+    a.depth_fs = p.depth_full_scale_mm;
+    a.init = c->t == 0 ? 1 : 0;
+    a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4);
+    a.px = c->opt[FOS_OPT_GMM_PX];
+    a.tpb = c->opt[FOS_OPT_GMM_TPB];
+    return a;
+}
+
 fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mg,
                           uint8_t* mp, cudaStream_t s)
 {
@@ -213,18 +193,8 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     const bool first = c->t == 0;
     if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
     if (gmm_on(c)) {
-        GmmArgs a{};
+        const GmmArgs a = gmm_args(c, rgb, depth, mg);
         const fos_params& p = c->prm;
-        a.P = c->P; a.plane = c->plane; a.state = c->gmm;
-        a.rgb = rgb; a.depth = depth; a.mask = mg;
-        a.alpha = p.alpha; a.lam2 = p.lambda * p.lambda; a.w_depth = p.w_depth; a.T_bg = p.T_bg;
-        a.v_init_rgb = p.v_init_rgb; a.v_init_d = p.v_init_d;
-        a.v_min_rgb = p.v_min_rgb; a.v_min_d = p.v_min_d;
-        a.depth_fs = p.depth_full_scale_mm;
-        a.init = first ? 1 : 0;
-        a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4);
-        a.px = c->opt[FOS_OPT_GMM_PX];
-        a.tpb = c->opt[FOS_OPT_GMM_TPB];
         TimedScope ts(c, first ? FOS_KERNEL_INIT : FOS_KERNEL_GMM, s);
         fos_status st = launch_result(c, launch_gmm(a, p.K_rgb, p.K_d, s), "gmm");
         if (st != FOS_OK) return st;
@@ -320,6 +290,31 @@ void block_samples(const fos_ctx* c, const uint16_t* planes, uint16_t* blocked)
 }  // namespace
 
 void fos::set_thread_error(const char* msg) { g_create_error = msg; }
+
+GmmArgs fos::ctx_gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mask)
+{
+    return gmm_args(c, rgb, depth, mask);
+}
+
+PbasArgs fos::ctx_pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mask)
+{
+    return pbas_args(c, rgb, depth, mask);
+}
+
+void fos::ctx_frame_done(fos_ctx* c)
+{
+    if (pbas_on(c)) c->pending = c->t > 0;
+    c->t += 1;
+    c->frames_since_counters += 1;
+}
+
+bool fos::ctx_gmm_on(const fos_ctx* c) { return gmm_on(c); }
+bool fos::ctx_pbas_on(const fos_ctx* c) { return pbas_on(c); }
+
+fos_status fos::ctx_validate_params(const fos_params* p, std::string& why)
+{
+    return validate_params(p, why);
+}
 
 extern "C" {
 

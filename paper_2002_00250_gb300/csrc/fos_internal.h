@@ -33,6 +33,21 @@ struct GmmArgs {
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
 
+// One stream of a batched GMM launch (device memory).
+struct GmmBatchEntry {
+    GmmArgs a;
+    int block_off;  // first block of this stream in the launch
+    int pad[3];
+};
+// Persistent batched GMM launch over hdr[0] entries and hdr[2] blocks of
+// kGmmBatchThreads threads; every stream uses the same (Kr, Kd) and pixels
+// per thread.
+constexpr int kGmmBatchThreads = 128;
+LaunchResult launch_gmm_batch(const GmmBatchEntry* E, const int* hdr, int blocks, int Kr, int Kd,
+                              int px, cudaStream_t s);
+int gmm_batch_px(int Kr, int Kd, int px);
+int gmm_batch_blocks_per_sm(int Kr, int Kd, int px);
+
 // PBAS device state.  Frames are cut into row segments of kSeg = 128 pixels
 // (spr = ceil(W / 128) segments per row, nseg = H * spr).  Samples and D are
 // uint16 in a blocked layout: element (c, k, x, y) sits at
@@ -84,6 +99,19 @@ struct PbasArgs {
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);
+
+// One stream of a batched launch (device memory, one entry per stream).
+struct PbasBatchEntry {
+    PbasArgs a;
+    int tile_off;  // first tile of this stream in the launch
+    int tiles_x;   // tiles per row
+    int init;      // 1: frame 0 of this stream
+    int pad;
+};
+// Persistent batched PBAS launch over hdr[0] entries and hdr[1] tiles.
+LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const int* hdr, int blocks, int N, int px,
+                               int ty, cudaStream_t s);
+int pbas_batch_blocks_per_sm(int N, int px, int ty);
 
 // Sets the text fos_last_error(NULL) returns on the calling thread.
 void set_thread_error(const char* msg);

@@ -210,10 +210,10 @@ __device__ __forceinline__ uint8_t gmm_pixel(Mix<KR, 3>& mr, Mix<KD, 1>& md, uin
     return Q >= a.lam2 ? 255 : 0;
 }
 
+// PX consecutive pixels per thread starting at pixel p0 of one stream.
 template <int KR, int KD, int PX>
-__global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
+__device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
 {
-    const int64_t p0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * PX;
     if (p0 >= a.P) return;
     // PX = 4 reads the inputs as 32/64-bit words: needs aligned frame buffers
     if (PX > 1 && (PX != 4 || a.vec_ok) && p0 + PX <= a.P) {
@@ -265,6 +265,41 @@ __global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
 }
 
 template <int KR, int KD, int PX>
+__global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
+{
+    gmm_pixels<KR, KD, PX>(a, (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * PX);
+}
+
+// Many streams in one persistent launch: entry i holds stream i's arguments
+// and its first block in the launch; blocks walk the launch's blocks with a
+// grid stride (counts read from device memory, see the PBAS batch kernel).
+template <int KR, int KD, int PX>
+__global__ void __launch_bounds__(kGmmBatchThreads) gmm_batch_kernel(const GmmBatchEntry* __restrict__ E,
+                                                        const int* __restrict__ hdr)
+{
+    __shared__ __align__(16) GmmArgs sa;
+    const int n = hdr[0], total = hdr[2];
+    int cur = -1;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (E[mid].block_off <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {
+            __syncthreads();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&E[lo].a);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+            for (int w = threadIdx.x; w < int(sizeof(GmmArgs) / 4); w += blockDim.x) dst[w] = src[w];
+            __syncthreads();
+            cur = lo;
+        }
+        gmm_pixels<KR, KD, PX>(sa, (int64_t(it - E[lo].block_off) * blockDim.x + threadIdx.x) * PX);
+    }
+}
+
+template <int KR, int KD, int PX>
 LaunchResult launch_k(const GmmArgs& a, cudaStream_t s)
 {
     const int tpb = (a.tpb == 64 || a.tpb == 256) ? a.tpb : 128;
@@ -294,5 +329,49 @@ LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s)
 #undef FOS_CASE
     return kLaunchUnsupported;
 }
+
+// Pixels per thread of the batched launch: the kernel keeps the per-stream
+// arguments in registers, so the 3+3 model runs 1 or 2 pixels per thread
+// (px option, default 2) and larger mixtures one pixel per thread.
+int gmm_batch_px(int Kr, int Kd, int px)
+{
+    if (Kr == 3 && Kd == 3) return px == 1 ? 1 : 2;
+    return 1;
+}
+
+#define FOS_GMM_BATCH_CASES(X)                                                        \
+    X(3, 3, 2) X(3, 3, 1) X(7, 3, 1) X(5, 3, 1) X(2, 2, 1) X(1, 1, 1) X(2, 1, 1)        \
+    X(3, 1, 1) X(3, 2, 1) X(5, 2, 1) X(7, 2, 1) X(1, 2, 1) X(1, 3, 1) X(2, 3, 1)        \
+    X(5, 1, 1) X(7, 1, 1)
+
+LaunchResult launch_gmm_batch(const GmmBatchEntry* E, const int* hdr, int blocks, int Kr, int Kd,
+                              int px, cudaStream_t s)
+{
+    const int p = gmm_batch_px(Kr, Kd, px);
+#define FOS_B(R, D, PX)                                                                    \
+    if (Kr == R && Kd == D && p == PX) {                                                   \
+        gmm_batch_kernel<R, D, PX><<<blocks, kGmmBatchThreads, 0, s>>>(E, hdr);            \
+        return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;           \
+    }
+    FOS_GMM_BATCH_CASES(FOS_B)
+#undef FOS_B
+    return kLaunchUnsupported;
+}
+
+int gmm_batch_blocks_per_sm(int Kr, int Kd, int px)
+{
+    const int p = gmm_batch_px(Kr, Kd, px);
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define FOS_O(R, D, PX)                                                                    \
+    if (Kr == R && Kd == D && p == PX)                                                     \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gmm_batch_kernel<R, D, PX>, \
+                                                          kGmmBatchThreads, 0);
+    FOS_GMM_BATCH_CASES(FOS_O)
+#undef FOS_O
+    return e == cudaSuccess ? nb : 0;
+}
+
+#undef FOS_GMM_BATCH_CASES
 
 }  // namespace fos

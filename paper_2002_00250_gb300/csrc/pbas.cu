@@ -267,30 +267,43 @@ __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c
     return d;
 }
 
+// Shared memory of one classify tile.
+template <int PX, int TY>
+struct ClassifySmem {
+    using G = Geo<PX, TY>;
+    __align__(16) uint8_t sm[4 * G::CH];  // staged channels with halo
+    uint32_t sreq[G::SH * G::SW];         // staged request words with halo
+    float wtab[4][256];                   // fl(wg_c * dg) for every gradient difference dg
+    float wgs[4];
+};
+
+// One tile (32*PX x TY pixels at x0, y0) of the classify pass of one stream.
+// build_table: recompute the gradient-weight table (the stream changed).
 template <int NT, int PX, int TY>
-__global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
+__device__ __forceinline__ void classify_tile(const PbasArgs& a, int x0, int y0,
+                                              ClassifySmem<PX, TY>& S, bool build_table)
 {
     using G = Geo<PX, TY>;
     constexpr int NW = SWords<PX>::NW;
-    __shared__ __align__(16) uint8_t sm[4 * G::CH];
-    __shared__ uint32_t sreq[G::SH * G::SW];
-    __shared__ float wtab[4][256];  // fl(wg_c * dg) for every gradient difference dg
-    __shared__ float wgs[4];
+    uint8_t* sm = S.sm;
+    uint32_t* sreq = S.sreq;
     const int N = NT > 0 ? NT : a.N;
-    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     stage_input<PX, TY>(a, x0, y0, sm);
     if (a.apply) stage_requests<PX, TY>(a, x0, y0, sreq);
-    if (tid < 4) {
+    if (build_table && tid < 4) {
         // gradient weight: alpha_g / mean gradient magnitude of the previous frame
         float mean = __fdiv_rn(__ull2float_rn(a.gsum_prev[tid]), __ll2float_rn(a.P));
         mean = fmaxf(mean, 1.0f);
-        wgs[tid] = __fdiv_rn(a.alpha_g, mean);
+        S.wgs[tid] = __fdiv_rn(a.alpha_g, mean);
     }
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid >= 4 && tid < 8) a.gsum_next[tid - 4] = 0ull;
+    if (x0 == 0 && y0 == 0 && tid >= 4 && tid < 8) a.gsum_next[tid - 4] = 0ull;
     __syncthreads();
-    for (int e = tid; e < 1024; e += 32 * TY) wtab[e >> 8][e & 255] = __fmul_rn(wgs[e >> 8], __int2float_rn(e & 255));
-    __syncthreads();
+    if (build_table) {
+        for (int e = tid; e < 1024; e += 32 * TY)
+            S.wtab[e >> 8][e & 255] = __fmul_rn(S.wgs[e >> 8], __int2float_rn(e & 255));
+        __syncthreads();
+    }
 
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
     const int x = x0 + lx0, y = y0 + ly;
@@ -349,7 +362,7 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
 
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
-        const float* tab = wtab[c];
+        const float* tab = S.wtab[c];
         uint32_t pv[PX];   // this frame's (value | gradient << 8)
         bool act[PX];
         bool any = false;
@@ -522,6 +535,13 @@ __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a
     });
 }
 
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
+{
+    __shared__ ClassifySmem<PX, TY> S;
+    classify_tile<NT, PX, TY>(a, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, S, true);
+}
+
 // Applies the pending neighbour requests of the last frame to the samples
 // without classifying (so that an exported state includes them).
 template <int NT, int TY>
@@ -551,16 +571,15 @@ __global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
     block_add<TY, 1>(applied, [&](int) { return a.counters + 1; });
 }
 
+// One tile of the frame-0 pass of one stream: every slot takes the frame.
 template <int NT, int PX, int TY>
-__global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
+__device__ __forceinline__ void init_tile(const PbasArgs& a, int x0, int y0, uint8_t* sm)
 {
     using G = Geo<PX, TY>;
-    __shared__ __align__(16) uint8_t sm[4 * G::CH];
     const int N = NT > 0 ? NT : a.N;
-    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     stage_input<PX, TY>(a, x0, y0, sm);
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid < 4) a.gsum_next[tid] = 0ull;
+    if (x0 == 0 && y0 == 0 && tid < 4) a.gsum_next[tid] = 0ull;
     __syncthreads();
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
     const int x = x0 + lx0, y = y0 + ly;
@@ -591,6 +610,52 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
         a.mask[int64_t(y) * a.W + x + i] = 0;
     }
     block_add<TY, 4>(gs, [&](int q) { return a.gsum_cur + q; });
+}
+
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
+{
+    __shared__ __align__(16) uint8_t sm[4 * Geo<PX, TY>::CH];
+    init_tile<NT, PX, TY>(a, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, sm);
+}
+
+// Many streams in one persistent launch.  Entry i of the batch holds stream
+// i's arguments, whether it is at frame 0, its tile offset in the launch
+// (prefix sum) and its tiles per row; blocks walk the launch's tiles with a
+// grid stride.  The count of entries and tiles is read from device memory, so
+// one captured graph serves any batch composition.
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
+pbas_batch_kernel(const PbasBatchEntry* __restrict__ E,
+                                                            const int* __restrict__ hdr)
+{
+    __shared__ ClassifySmem<PX, TY> S;
+    __shared__ __align__(16) PbasArgs sa;
+    const int n = hdr[0], total = hdr[1];
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    int cur = -1;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        int lo = 0, hi = n - 1;  // entry whose tile range holds `it`
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (E[mid].tile_off <= it) lo = mid;
+            else hi = mid - 1;
+        }
+        const bool fresh = lo != cur;
+        if (fresh) {
+            __syncthreads();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&E[lo].a);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
+            for (int w = tid; w < int(sizeof(PbasArgs) / 4); w += 32 * TY) dst[w] = src[w];
+            __syncthreads();
+            cur = lo;
+        }
+        const int local = it - E[lo].tile_off, tx = E[lo].tiles_x;
+        const int x0 = (local % tx) * Geo<PX, TY>::TW, y0 = (local / tx) * TY;
+        if (E[lo].init) init_tile<NT, PX, TY>(sa, x0, y0, S.sm);
+        else classify_tile<NT, PX, TY>(sa, x0, y0, S, fresh);
+        __syncthreads();
+    }
 }
 
 template <int PX, int TY>
@@ -638,6 +703,41 @@ FOS_PBAS_LAUNCHER(classify_launch, pbas_classify_kernel)
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s) { return init_launch(a, s); }
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s) { return classify_launch(a, s); }
+
+template <int NT>
+bool batch_shape(const PbasBatchEntry* E, const int* hdr, int blocks, int px, int ty, cudaStream_t s)
+{
+    if (px == 2 && ty == 8) pbas_batch_kernel<NT, 2, 8><<<blocks, dim3(32, 8), 0, s>>>(E, hdr);
+    else if (px == 2 && ty == 4) pbas_batch_kernel<NT, 2, 4><<<blocks, dim3(32, 4), 0, s>>>(E, hdr);
+    else if (px == 4 && ty == 4) pbas_batch_kernel<NT, 4, 4><<<blocks, dim3(32, 4), 0, s>>>(E, hdr);
+    else if (px == 4 && ty == 8) pbas_batch_kernel<NT, 4, 8><<<blocks, dim3(32, 8), 0, s>>>(E, hdr);
+    else if (px == 1 && ty == 8) pbas_batch_kernel<NT, 1, 8><<<blocks, dim3(32, 8), 0, s>>>(E, hdr);
+    else return false;
+    return true;
+}
+
+LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const int* hdr, int blocks, int N, int px,
+                               int ty, cudaStream_t s)
+{
+    const bool ok = N == 20 ? batch_shape<20>(E, hdr, blocks, px, ty, s)
+                            : batch_shape<0>(E, hdr, blocks, px, ty, s);
+    if (!ok) return kLaunchUnsupported;
+    return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+}
+
+int pbas_batch_blocks_per_sm(int N, int px, int ty)
+{
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    const int threads = 32 * ty;
+#define FOS_OCC(P, T)                                                                          \
+    if (px == P && ty == T)                                                                    \
+        e = N == 20 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<20, P, T>, threads, 0) \
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<0, P, T>, threads, 0);
+    FOS_OCC(2, 8) FOS_OCC(2, 4) FOS_OCC(4, 4) FOS_OCC(4, 8) FOS_OCC(1, 8)
+#undef FOS_OCC
+    return e == cudaSuccess ? nb : 0;
+}
 
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s)
 {

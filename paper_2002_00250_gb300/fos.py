@@ -60,6 +60,11 @@ class StateHeader(ctypes.Structure):
                 ("pbas_bytes", ctypes.c_uint64)]
 
 
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("gmm_px", ctypes.c_int32), ("pbas_px", ctypes.c_int32),
+                ("pbas_ty", ctypes.c_int32), ("ms_per_step", ctypes.c_float)]
+
+
 class KernelTiming(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -90,6 +95,16 @@ SIGNATURES = {
     "fos_set_option": (_st, [_vp, _i32, _i32]),
     "fos_get_option": (_i32, [_vp, _i32]),
     "fos_pbas_step_noalloc": (_st, [_i32, _i32, ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp]),
+    "fos_stream_device_bytes": (ctypes.c_size_t, [_i32, _i32, ctypes.POINTER(Params)]),
+    "fos_batch_create": (_vp, [_i32, ctypes.POINTER(Params)]),
+    "fos_batch_destroy": (None, [_vp]),
+    "fos_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "fos_batch_add_stream": (_i32, [_vp, _i32, _i32, _u32]),
+    "fos_batch_remove_stream": (_st, [_vp, _i32]),
+    "fos_batch_stream": (_vp, [_vp, _i32]),
+    "fos_batch_process_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fos_batch_set_shape": (_st, [_vp, _i32, _i32, _i32]),
+    "fos_batch_autotune": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(BatchTuning)]),
 }
 OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY = 1, 2, 3, 4
 
@@ -302,3 +317,81 @@ def decode_state(blob: np.ndarray) -> StateView:
                     sg=(s >> 8).astype(np.uint8).transpose(2, 0, 1),
                     sD=D.transpose(2, 0, 1), R=R.T, T=T.T, S=S.T, gsum=gsum)
     return StateView(hdr, gmm, pbas)
+
+
+class Batch:
+    """Many camera streams processed together: one graph replay per frame step."""
+
+    def __init__(self, max_streams: int, params: Params | None = None, **overrides):
+        self.lib = load()
+        self.params = params if params is not None else default_params(**overrides)
+        h = self.lib.fos_batch_create(max_streams, ctypes.byref(self.params))
+        if not h:
+            raise FosError(1, self.lib.fos_last_error(None).decode())
+        self.h = h
+        self.sizes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fos_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise FosError(st, self.lib.fos_batch_last_error(self.h).decode())
+
+    def add(self, width: int, height: int, stream_id: int) -> int:
+        slot = self.lib.fos_batch_add_stream(self.h, width, height, stream_id)
+        if slot < 0:
+            raise FosError(5, self.lib.fos_batch_last_error(self.h).decode())
+        self.sizes[slot] = (width, height)
+        return slot
+
+    def remove(self, slot: int) -> None:
+        self._check(self.lib.fos_batch_remove_stream(self.h, slot))
+        self.sizes.pop(slot, None)
+
+    def context(self, slot: int) -> int:
+        return self.lib.fos_batch_stream(self.h, slot)
+
+    @staticmethod
+    def _arr(ptrs):
+        return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+    def process(self, slots, rgb, depth, mask_gmm=None, mask_pbas=None, stream=None):
+        """One frame for each listed slot (lists of torch CUDA tensors)."""
+        n = len(slots)
+        sl = (ctypes.c_int32 * n)(*slots)
+        mg = self._arr([_ptr(m) for m in mask_gmm]) if mask_gmm is not None else None
+        mp = self._arr([_ptr(m) for m in mask_pbas]) if mask_pbas is not None else None
+        self._check(self.lib.fos_batch_process_device(
+            self.h, n, sl, self._arr([_ptr(r) for r in rgb]), self._arr([_ptr(d) for d in depth]),
+            mg, mp, _stream_handle(stream)))
+
+    def set_shape(self, gmm_px: int, pbas_px: int, pbas_ty: int) -> None:
+        self._check(self.lib.fos_batch_set_shape(self.h, gmm_px, pbas_px, pbas_ty))
+
+    def autotune(self, slots, rgb, depth, stream=None) -> dict:
+        n = len(slots)
+        out = BatchTuning()
+        self._check(self.lib.fos_batch_autotune(
+            self.h, n, (ctypes.c_int32 * n)(*slots), self._arr([_ptr(r) for r in rgb]),
+            self._arr([_ptr(d) for d in depth]), _stream_handle(stream), ctypes.byref(out)))
+        return dict(gmm_px=out.gmm_px, pbas_px=out.pbas_px, pbas_ty=out.pbas_ty,
+                    ms_per_step=out.ms_per_step)
+
+    def get_state(self, slot: int) -> np.ndarray:
+        c = self.context(slot)
+        n = ctypes.c_size_t()
+        st = self.lib.fos_state_size(c, ctypes.byref(n))
+        buf = np.empty(n.value, np.uint8)
+        st = st or self.lib.fos_get_state(c, _ptr(buf), buf.size)
+        if st != 0:
+            raise FosError(st, self.lib.fos_last_error(c).decode())
+        return buf
