@@ -35,6 +35,7 @@ METRIC = "Mpixel-frames/s (GMM+PBAS per frame)"
 ALGO_BYTES = {
     "gmm_step": 198.0,        # 96 B state read + 96 B written + 5 B input + 1 B mask
     "pbas_classify": 246.0,   # 160 B samples + 48 B R,T,S read + 32 B R,T written + 5 in + 1 mask
+    "fused_classify": 439.0,  # both of the above, the 5 B input read once
 }
 SPARSE_OWN = 10.0   # per own update: 2 B sample + 2 B D read + 2 B D write + 4 B S write
 SPARSE_NEIGH = 2.0  # per neighbour write: 2 B sample (applied inside pbas_classify)
@@ -114,9 +115,12 @@ def _traffic_for(kernel: str, pixels: int):
     path = os.path.join(ROOT, "profiles", f"{kernel}_1280x720.md")
     src = os.path.join(ROOT, "paper_2002_00250_gb300", "csrc",
                        "gmm.cu" if kernel == "gmm_step" else "pbas.cu")
+    if kernel == "fused_classify":  # the fused kernel also compiles the GMM device code
+        src = [src, os.path.join(ROOT, "paper_2002_00250_gb300", "csrc", "gmm_dev.cuh")]
     try:
         txt = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        srcs = src if isinstance(src, list) else [src]
+        sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         fields = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes_per_pixel:", "source_sha:")))
         if fields.get("source_sha", "").strip() != sha:
             return None
@@ -212,7 +216,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     seg.get_timing()
     seg.get_counters()
-    seg.set_timing(0b0011)  # time every GMM and PBAS-classify launch
+    seg.set_timing(0b10011)  # time every GMM, PBAS-classify and fused launch
 
     clocks = ClockSampler(local)
     barrier()
@@ -247,7 +251,7 @@ def run_ours(args):
         if name not in ALGO_BYTES or n == 0:
             continue
         bytes_px = ALGO_BYTES[name] * P
-        if name == "pbas_classify":
+        if name in ("pbas_classify", "fused_classify"):
             bytes_px += (SPARSE_OWN * counters["own_updates"] +
                          SPARSE_NEIGH * counters["neighbour_writes"]) / max(1, n)
         avg_s = tot / n / 1e3
@@ -318,7 +322,7 @@ def run_ours(args):
             nf = min(args.cpu_frames + 1, NFRAMES)
             host = [(_s.to_numpy(h_rgb[f]), _s.to_numpy(h_dep[f])) for f in range(nf)]
             cb = cpu_oracle_sample(args.cpu_frames, frames=host)
-        launches_per_step = 2 * NFRAMES  # frame 0: 2 init kernels; then GMM + PBAS per frame
+        launches_per_step = 2 + (NFRAMES - 1)  # frame 0: 2 init kernels; then one fused launch per frame
         out = {"metric": METRIC, "value": round(value, 1), "unit": "Mpixel-frames/s",
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
@@ -342,6 +346,98 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch16(args):
+    """16 mixed-size camera streams, 300 frames each: batched graph launch vs the
+    plain per-stream path (sequential on one CUDA stream, and one CUDA stream
+    per camera).  Prints one JSON line (a secondary workload, not the headline)."""
+    import torch
+    from paper_2002_00250_gb300 import fos, synth
+
+    nf = args.frames
+    sizes = synth.BATCH16_SIZES
+    dev = torch.device("cuda", 0)
+    frames = []
+    for s_id, (w, h) in enumerate(sizes):
+        sc = synth.RGBDScene(synth.config_stream(w, h, nf, seed=0, stream_id=s_id), device=dev)
+        r, d, _ = sc.sequence(0, nf)
+        frames.append((r, d, torch.empty((nf, h, w), dtype=torch.uint8, device=dev),
+                       torch.empty((nf, h, w), dtype=torch.uint8, device=dev)))
+    px_step = sum(w * h for w, h in sizes) * nf
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # plain path: one context per camera, every camera's frame launched in turn
+    segs = [fos.Segmenter(w, h, stream_id=i) for i, (w, h) in enumerate(sizes)]
+
+    def plain():
+        for sgm in segs:
+            sgm.reset()
+        for f in range(nf):
+            for i, sgm in enumerate(segs):
+                r, d, mg, mp = frames[i]
+                sgm.process_device(r[f], d[f], mg[f], mp[f], stream=stream)
+
+    ms_plain = timed(plain, args.steps)
+    # plain path with one CUDA stream per camera
+    cams = [torch.cuda.Stream(device=dev) for _ in sizes]
+
+    def plain_ms():
+        for sgm in segs:
+            sgm.reset()
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for c in cams:
+            c.wait_event(ev)
+        for f in range(nf):
+            for i, sgm in enumerate(segs):
+                r, d, mg, mp = frames[i]
+                sgm.process_device(r[f], d[f], mg[f], mp[f], stream=cams[i])
+        for c in cams:
+            e = torch.cuda.Event()
+            e.record(c)
+            stream.wait_event(e)
+
+    ms_multi = timed(plain_ms, args.steps)
+    del segs
+
+    b = fos.Batch(len(sizes))
+    slots = [b.add(w, h, stream_id=i) for i, (w, h) in enumerate(sizes)]
+    tune = b.autotune(slots, [f[0][0] for f in frames], [f[1][0] for f in frames], stream=stream)
+    torch.cuda.synchronize()
+
+    def batched():
+        for sl in slots:
+            b.lib.fos_reset(b.context(sl))
+        for f in range(nf):
+            b.process(slots, [fr[0][f] for fr in frames], [fr[1][f] for fr in frames],
+                      [fr[2][f] for fr in frames], [fr[3][f] for fr in frames], stream=stream)
+
+    ms_batch = timed(batched, args.steps)
+    out = {"metric": METRIC, "value": round(px_step / ms_batch / 1e3, 1), "unit": "Mpixel-frames/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_batch, 3),
+           "higher_is_better": True, "dtype": "f32+u8", "data": "synthetic",
+           "config": {"workload": f"16 mixed streams x {nf} frames (GMM 3+3 + PBAS 20)",
+                      "sizes": sizes, "mpx_per_step": px_step / 1e6},
+           "plain_sequential": round(px_step / ms_plain / 1e3, 1),
+           "plain_stream_per_camera": round(px_step / ms_multi / 1e3, 1),
+           "speedup_vs_plain": round(ms_plain / ms_batch, 2),
+           "speedup_vs_stream_per_camera": round(ms_multi / ms_batch, 2),
+           "autotune": tune}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,9 +450,13 @@ def main():
                     help="frames per step (a shorter sequence for profiler captures)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run the device-resident steps only (for profiler captures)")
+    ap.add_argument("--workload", default="720p", choices=["720p", "batch16"],
+                    help="720p: the headline single-stream sequence; batch16: 16 mixed streams")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch16":
+        run_batch16(args)
     else:
         run_ours(args)
 

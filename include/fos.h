@@ -200,7 +200,8 @@ fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes);
 #define FOS_KERNEL_PBAS_FLUSH 2  /* PBAS pending neighbour updates applied
                                     outside a frame (before a state export) */
 #define FOS_KERNEL_INIT 3       /* frame-0 initialisation */
-#define FOS_KERNEL_COUNT 4
+#define FOS_KERNEL_FUSED 4      /* GMM and PBAS of a frame in one launch */
+#define FOS_KERNEL_COUNT 5
 
 typedef struct fos_kernel_timing {
     int64_t launches;
@@ -222,7 +223,9 @@ fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
 #define FOS_OPT_GMM_TPB 2  /* GMM threads per block: 64, 128, 256 */
 #define FOS_OPT_PBAS_PX 3  /* PBAS pixels per thread: 1, 2, 4 */
 #define FOS_OPT_PBAS_TY 4  /* PBAS tile rows: 2, 4, 8 (2 only with 4 px/thread) */
-#define FOS_OPT_COUNT 5
+#define FOS_OPT_FUSE 5     /* 1 (default): with both methods and K = 3+3, frames >= 1
+                              run GMM and PBAS in one fused launch; 0: two launches */
+#define FOS_OPT_COUNT 6
 
 /* Sets a kernel-shape option; FOS_ERR_INVALID_ARG for unknown options or
  * values, FOS_ERR_UNSUPPORTED for shapes not compiled in. */

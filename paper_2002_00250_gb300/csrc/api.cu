@@ -184,6 +184,12 @@ GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t*
     return a;
 }
 
+// GMM and PBAS of a frame in one launch: both methods, the 3+3 model, option on.
+bool ctx_fused(const fos_ctx* c)
+{
+    return gmm_on(c) && pbas_on(c) && c->prm.K_rgb == 3 && c->prm.K_d == 3 && c->opt[FOS_OPT_FUSE] != 0;
+}
+
 fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mg,
                           uint8_t* mp, cudaStream_t s)
 {
@@ -192,6 +198,17 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     if (pbas_on(c) && !mp) return fail(c, FOS_ERR_INVALID_ARG, "PBAS enabled: mask_pbas must be non-NULL");
     const bool first = c->t == 0;
     if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
+    if (!first && ctx_fused(c)) {
+        const GmmArgs g = gmm_args(c, rgb, depth, mg);
+        const PbasArgs a = pbas_args(c, rgb, depth, mp);
+        TimedScope ts(c, FOS_KERNEL_FUSED, s);
+        fos_status st = launch_result(c, launch_fused_classify(a, g, s), "fused_classify");
+        if (st != FOS_OK) return st;
+        c->pending = true;
+        c->t += 1;
+        c->frames_since_counters += 1;
+        return FOS_OK;
+    }
     if (gmm_on(c)) {
         const GmmArgs a = gmm_args(c, rgb, depth, mg);
         const fos_params& p = c->prm;
@@ -624,6 +641,7 @@ fos_status fos_set_option(fos_ctx* ctx, int32_t option, int32_t value)
     case FOS_OPT_GMM_TPB: ok = value == 64 || value == 128 || value == 256; break;
     case FOS_OPT_PBAS_PX: ok = value == 1 || value == 2 || value == 4; break;
     case FOS_OPT_PBAS_TY: ok = value == 2 || value == 4 || value == 8; break;
+    case FOS_OPT_FUSE: ok = value == 0 || value == 1; break;
     default: return fail(ctx, FOS_ERR_INVALID_ARG, "unknown option");
     }
     if (!ok) return fail(ctx, FOS_ERR_INVALID_ARG, "option value not supported");

@@ -73,6 +73,8 @@ uint8_t* host_buf(fos_batch* b, int k) { return b->host + k * b->buf_bytes; }
 
 bool gmm_on(const fos_batch* b) { return b->prm.methods & FOS_METHOD_GMM; }
 bool pbas_on(const fos_batch* b) { return b->prm.methods & FOS_METHOD_PBAS; }
+// Both methods with the 3+3 model: every tile runs GMM and PBAS in one kernel.
+bool fused(const fos_batch* b) { return gmm_on(b) && pbas_on(b) && b->prm.K_rgb == 3 && b->prm.K_d == 3; }
 
 // Shapes usable for this set of streams: vector paths need every width to be
 // a multiple of the pixels per thread.
@@ -94,16 +96,18 @@ fos_status ensure_graph(fos_batch* b, int k, int pbas_px)
         b->graph[k] = nullptr;
     }
     int gblocks = 0, pblocks = 0;
-    if (gmm_on(b)) gblocks = b->sms * std::max(1, gmm_batch_blocks_per_sm(b->prm.K_rgb, b->prm.K_d, b->gmm_px));
-    if (pbas_on(b)) pblocks = b->sms * std::max(1, pbas_batch_blocks_per_sm(b->prm.N, pbas_px, b->pbas_ty));
+    const bool fz = fused(b);
+    if (gmm_on(b) && !fz) gblocks = b->sms * std::max(1, gmm_batch_blocks_per_sm(b->prm.K_rgb, b->prm.K_d, b->gmm_px));
+    if (pbas_on(b)) pblocks = b->sms * std::max(1, pbas_batch_blocks_per_sm(b->prm.N, pbas_px, b->pbas_ty, fz));
     FOS_BTRY(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemcpyAsync(b->dev + k * b->buf_bytes, host_buf(b, k), b->buf_bytes,
                                     cudaMemcpyHostToDevice, b->cap);
     LaunchResult r = kLaunchOk;
-    if (e == cudaSuccess && gmm_on(b))
+    if (e == cudaSuccess && gmm_on(b) && !fz)
         r = launch_gmm_batch(dev_gmm(b, k), dev_hdr(b, k), gblocks, b->prm.K_rgb, b->prm.K_d, b->gmm_px, b->cap);
     if (e == cudaSuccess && r == kLaunchOk && pbas_on(b))
-        r = launch_pbas_batch(dev_pbas(b, k), dev_hdr(b, k), pblocks, b->prm.N, pbas_px, b->pbas_ty, b->cap);
+        r = launch_pbas_batch(dev_pbas(b, k), fz ? dev_gmm(b, k) : nullptr, dev_hdr(b, k), pblocks, b->prm.N,
+                              pbas_px, b->pbas_ty, b->cap);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e != cudaSuccess) {

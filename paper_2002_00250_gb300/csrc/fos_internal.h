@@ -100,6 +100,9 @@ LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);
 
+// GMM (3+3 components) and PBAS of one frame in one launch (frames >= 1).
+LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStream_t s);
+
 // One stream of a batched launch (device memory, one entry per stream).
 struct PbasBatchEntry {
     PbasArgs a;
@@ -108,10 +111,11 @@ struct PbasBatchEntry {
     int init;      // 1: frame 0 of this stream
     int pad;
 };
-// Persistent batched PBAS launch over hdr[0] entries and hdr[1] tiles.
-LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const int* hdr, int blocks, int N, int px,
-                               int ty, cudaStream_t s);
-int pbas_batch_blocks_per_sm(int N, int px, int ty);
+// Persistent batched PBAS launch over hdr[0] entries and hdr[1] tiles; with
+// G non-NULL (3+3-component GMM) each tile also runs the GMM of its pixels.
+LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr,
+                               int blocks, int N, int px, int ty, cudaStream_t s);
+int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused);
 
 // Sets the text fos_last_error(NULL) returns on the calling thread.
 void set_thread_error(const char* msg);

@@ -10,205 +10,11 @@
 #include <cmath>
 
 #include "fos_internal.h"
+#include "gmm_dev.cuh"
 
 namespace fos {
 namespace {
-
-template <int K, int C>
-struct Mix {
-    float w[K];
-    float mu[C][K];
-    float v[K];
-};
-
-// Depth u16 (mm) -> u8 as Sec. 4.2 describes: 0 stays 0 (invalid), the full
-// scale maps onto 1..255 with round-half-up.
-__device__ __forceinline__ uint32_t depth_to_u8(uint32_t d, uint32_t fs)
-{
-    if (d == 0) return 0;
-    uint32_t q = (d * 255u + (fs >> 1)) / fs;
-    return q < 1u ? 1u : (q > 255u ? 255u : q);
-}
-
-template <int K, int C>
-__device__ __forceinline__ void mix_init(Mix<K, C>& m, const float (&x)[C], float v_init)
-{
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        m.w[k] = k == 0 ? 1.f : 0.f;
-#pragma unroll
-        for (int c = 0; c < C; ++c) m.mu[c][k] = k == 0 ? x[c] : 0.f;
-        m.v[k] = v_init;
-    }
-}
-
-// One frame of one mixture at one pixel.  Returns the distance of x to the
-// background set of the model as it stood before this frame's update.
-// Steps: squared Mahalanobis distance per component; background set = shortest
-// ranked prefix whose weight exceeds T_bg; first ranked match within lambda^2;
-// weight decay toward the match; matched component moves toward x with
-// rho = alpha / w (else the last-ranked component is replaced by x);
-// normalisation; stable re-ranking by w / sqrt(v).
-template <int K, int C>
-__device__ __forceinline__ float mix_step(Mix<K, C>& m, const float (&x)[C], float alpha,
-                                          float lam2, float T_bg, float v_init, float v_min)
-{
-    float ss[K], d2[K], diff[C][K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        float s = 0.f;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-            diff[c][k] = x[c] - m.mu[c][k];
-            s = fmaf(diff[c][k], diff[c][k], s);
-        }
-        ss[k] = s;
-        d2[k] = s / (float(C) * m.v[k]);
-    }
-    float cum = 0.f, dB = INFINITY;
-    bool open = true;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        if (open) {
-            dB = fminf(dB, d2[k]);
-            cum += m.w[k];
-            open = !(cum > T_bg);
-        }
-    }
-    int match = -1;
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        if (match < 0 && d2[k] < lam2) match = k;
-
-    const float oma = 1.f - alpha;
-#pragma unroll
-    for (int k = 0; k < K; ++k) m.w[k] = oma * m.w[k] + (k == match ? alpha : 0.f);
-    if (match >= 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            if (k == match) {
-                const float rho = alpha / m.w[k];
-#pragma unroll
-                for (int c = 0; c < C; ++c) m.mu[c][k] = fmaf(rho, diff[c][k], m.mu[c][k]);
-                const float v = fmaf(rho, ss[k] * (1.f / float(C)) - m.v[k], m.v[k]);
-                m.v[k] = fmaxf(v, v_min);
-            }
-        }
-    } else {
-        m.w[K - 1] = alpha;
-#pragma unroll
-        for (int c = 0; c < C; ++c) m.mu[c][K - 1] = x[c];
-        m.v[K - 1] = v_init;
-    }
-    float s = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) s += m.w[k];
-#pragma unroll
-    for (int k = 0; k < K; ++k) m.w[k] = m.w[k] / s;
-
-    float key[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) key[k] = m.w[k] * rsqrtf(m.v[k]);
-#pragma unroll
-    for (int pass = 0; pass < K - 1; ++pass) {
-#pragma unroll
-        for (int j = 0; j < K - 1 - pass; ++j) {
-            if (key[j + 1] > key[j]) {
-                float t;
-                t = key[j]; key[j] = key[j + 1]; key[j + 1] = t;
-                t = m.w[j]; m.w[j] = m.w[j + 1]; m.w[j + 1] = t;
-                t = m.v[j]; m.v[j] = m.v[j + 1]; m.v[j + 1] = t;
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    t = m.mu[c][j]; m.mu[c][j] = m.mu[c][j + 1]; m.mu[c][j + 1] = t;
-                }
-            }
-        }
-    }
-    return dB;
-}
-
-template <int PX>
-__device__ __forceinline__ void ldv(const float* p, float (&o)[PX])
-{
-    if constexpr (PX == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-    } else if constexpr (PX == 2) {
-        const float2 v = *reinterpret_cast<const float2*>(p);
-        o[0] = v.x; o[1] = v.y;
-    } else {
-        o[0] = *p;
-    }
-}
-
-template <int PX>
-__device__ __forceinline__ void stv(float* p, const float (&o)[PX])
-{
-    if constexpr (PX == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    } else if constexpr (PX == 2) {
-        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-    } else {
-        *p = o[0];
-    }
-}
-
-// Per-plane load/store of PX pixels of one parameter into the mixtures.
-template <int KR, int KD, int PX, bool STORE>
-__device__ __forceinline__ void move_state(float* st, int64_t plane, int64_t p0,
-                                           Mix<KR, 3> (&mr)[PX], Mix<KD, 1> (&md)[PX])
-{
-    float tmp[PX];
-#define FOS_MOVE(QIDX, FIELD_I)                                            \
-    {                                                                      \
-        float* ptr = st + (int64_t)(QIDX) * plane + p0;                    \
-        if (STORE) {                                                       \
-            _Pragma("unroll") for (int i = 0; i < PX; ++i) tmp[i] = FIELD_I; \
-            stv<PX>(ptr, tmp);                                             \
-        } else {                                                           \
-            ldv<PX>(ptr, tmp);                                             \
-            _Pragma("unroll") for (int i = 0; i < PX; ++i) FIELD_I = tmp[i]; \
-        }                                                                  \
-    }
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-        FOS_MOVE(k, mr[i].w[k]);
-        FOS_MOVE(KR + k, mr[i].mu[0][k]);
-        FOS_MOVE(2 * KR + k, mr[i].mu[1][k]);
-        FOS_MOVE(3 * KR + k, mr[i].mu[2][k]);
-        FOS_MOVE(4 * KR + k, mr[i].v[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < KD; ++k) {
-        FOS_MOVE(5 * KR + k, md[i].w[k]);
-        FOS_MOVE(5 * KR + KD + k, md[i].mu[0][k]);
-        FOS_MOVE(5 * KR + 2 * KD + k, md[i].v[k]);
-    }
-#undef FOS_MOVE
-}
-
-template <int KR, int KD>
-__device__ __forceinline__ uint8_t gmm_pixel(Mix<KR, 3>& mr, Mix<KD, 1>& md, uint32_t r,
-                                             uint32_t g, uint32_t b, uint32_t d16,
-                                             const GmmArgs& a)
-{
-    const float xr[3] = {float(r), float(g), float(b)};
-    const uint32_t d8 = depth_to_u8(d16, a.depth_fs);
-    const float xd[1] = {float(d8)};
-    if (a.init) {
-        mix_init(mr, xr, a.v_init_rgb);
-        mix_init(md, xd, a.v_init_d);
-        return 0;
-    }
-    const float dB_rgb = mix_step(mr, xr, a.alpha, a.lam2, a.T_bg, a.v_init_rgb, a.v_min_rgb);
-    float Q = dB_rgb;
-    if (d16 != 0) {
-        const float dB_d = mix_step(md, xd, a.alpha, a.lam2, a.T_bg, a.v_init_d, a.v_min_d);
-        Q = (1.f - a.w_depth) * dB_rgb + a.w_depth * dB_d;
-    }
-    return Q >= a.lam2 ? 255 : 0;
-}
+using namespace gmmdev;
 
 // PX consecutive pixels per thread starting at pixel p0 of one stream.
 template <int KR, int KD, int PX>
@@ -279,8 +85,10 @@ __global__ void __launch_bounds__(kGmmBatchThreads) gmm_batch_kernel(const GmmBa
 {
     __shared__ __align__(16) GmmArgs sa;
     const int n = hdr[0], total = hdr[2];
+    const int chunk = (total + int(gridDim.x) - 1) / int(gridDim.x);
+    const int it0 = int(blockIdx.x) * chunk, it1 = min(total, it0 + chunk);
     int cur = -1;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    for (int it = it0; it < it1; ++it) {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;

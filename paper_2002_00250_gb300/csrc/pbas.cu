@@ -23,6 +23,7 @@
 // (explicit _rn intrinsics, no contraction), so results are bit-exact against
 // a plain C implementation of the same steps.
 #include "fos_internal.h"
+#include "gmm_dev.cuh"
 #include "philox.cuh"
 
 namespace fos {
@@ -267,6 +268,27 @@ __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c
     return d;
 }
 
+// GMM classify + update (Sec. 3.1) of the tile's own pixels, reading the
+// colour and the converted depth from the staged tile (fused GMM+PBAS path).
+// The model state and the mask are addressed as in the GMM kernels.
+template <int KR, int KD, int PX, int TY>
+__device__ __forceinline__ void gmm_tile_part(const GmmArgs& g, const PbasArgs& a, int x0, int y0,
+                                              const uint8_t* sm)
+{
+    using G = Geo<PX, TY>;
+    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
+    const int x = x0 + lx0, y = y0 + ly;
+    if (y >= a.H || x >= a.W) return;
+    const int64_t p0 = int64_t(y) * a.W + x;
+    const int o = (ly + 1) * G::SWP + lx0 + 1;
+#pragma unroll 1
+    for (int i = 0; i < PX; ++i) {
+        if (x + i >= a.W) break;
+        g.mask[p0 + i] = gmmdev::gmm_pixel_lowreg<KR, KD>(g, p0 + i, sm[o + i], sm[G::CH + o + i],
+                                                          sm[2 * G::CH + o + i], sm[3 * G::CH + o + i]);
+    }
+}
+
 // Shared memory of one classify tile.
 template <int PX, int TY>
 struct ClassifySmem {
@@ -279,8 +301,8 @@ struct ClassifySmem {
 
 // One tile (32*PX x TY pixels at x0, y0) of the classify pass of one stream.
 // build_table: recompute the gradient-weight table (the stream changed).
-template <int NT, int PX, int TY>
-__device__ __forceinline__ void classify_tile(const PbasArgs& a, int x0, int y0,
+template <int NT, int PX, int TY, int KR = 0, int KD = 0>
+__device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* gm, int x0, int y0,
                                               ClassifySmem<PX, TY>& S, bool build_table)
 {
     using G = Geo<PX, TY>;
@@ -304,6 +326,7 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, int x0, int y0,
             S.wtab[e >> 8][e & 255] = __fmul_rn(S.wgs[e >> 8], __int2float_rn(e & 255));
         __syncthreads();
     }
+    if constexpr (KR > 0) gmm_tile_part<KR, KD, PX, TY>(*gm, a, x0, y0, sm);
 
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
     const int x = x0 + lx0, y = y0 + ly;
@@ -539,7 +562,16 @@ template <int NT, int PX, int TY>
 __global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
 {
     __shared__ ClassifySmem<PX, TY> S;
-    classify_tile<NT, PX, TY>(a, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, S, true);
+    classify_tile<NT, PX, TY>(a, nullptr, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, S, true);
+}
+
+// GMM and PBAS of one frame in one pass over the frame (inputs staged once).
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
+fused_classify_kernel(const PbasArgs a, const GmmArgs g)
+{
+    __shared__ ClassifySmem<PX, TY> S;
+    classify_tile<NT, PX, TY, 3, 3>(a, &g, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, S, true);
 }
 
 // Applies the pending neighbour requests of the last frame to the samples
@@ -572,8 +604,8 @@ __global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
 }
 
 // One tile of the frame-0 pass of one stream: every slot takes the frame.
-template <int NT, int PX, int TY>
-__device__ __forceinline__ void init_tile(const PbasArgs& a, int x0, int y0, uint8_t* sm)
+template <int NT, int PX, int TY, int KR = 0, int KD = 0>
+__device__ __forceinline__ void init_tile(const PbasArgs& a, const GmmArgs* gm, int x0, int y0, uint8_t* sm)
 {
     using G = Geo<PX, TY>;
     const int N = NT > 0 ? NT : a.N;
@@ -581,6 +613,7 @@ __device__ __forceinline__ void init_tile(const PbasArgs& a, int x0, int y0, uin
     stage_input<PX, TY>(a, x0, y0, sm);
     if (x0 == 0 && y0 == 0 && tid < 4) a.gsum_next[tid] = 0ull;
     __syncthreads();
+    if constexpr (KR > 0) gmm_tile_part<KR, KD, PX, TY>(*gm, a, x0, y0, sm);
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
     const int x = x0 + lx0, y = y0 + ly;
     uint32_t gs[4] = {0, 0, 0, 0};
@@ -616,7 +649,7 @@ template <int NT, int PX, int TY>
 __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
 {
     __shared__ __align__(16) uint8_t sm[4 * Geo<PX, TY>::CH];
-    init_tile<NT, PX, TY>(a, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, sm);
+    init_tile<NT, PX, TY>(a, nullptr, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, sm);
 }
 
 // Many streams in one persistent launch.  Entry i of the batch holds stream
@@ -624,17 +657,23 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
 // (prefix sum) and its tiles per row; blocks walk the launch's tiles with a
 // grid stride.  The count of entries and tiles is read from device memory, so
 // one captured graph serves any batch composition.
-template <int NT, int PX, int TY>
+template <int NT, int PX, int TY, int KR>
 __global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
-pbas_batch_kernel(const PbasBatchEntry* __restrict__ E,
-                                                            const int* __restrict__ hdr)
+pbas_batch_kernel(const PbasBatchEntry* __restrict__ E, const GmmBatchEntry* __restrict__ GE,
+                  const int* __restrict__ hdr)
 {
+    constexpr int KD = KR;
     __shared__ ClassifySmem<PX, TY> S;
     __shared__ __align__(16) PbasArgs sa;
+    __shared__ __align__(16) GmmArgs sg;
     const int n = hdr[0], total = hdr[1];
     const int tid = threadIdx.y * 32 + threadIdx.x;
+    // each block takes a contiguous run of tiles, so consecutive tiles mostly
+    // belong to the same stream (arguments and weight table are reused)
+    const int chunk = (total + int(gridDim.x) - 1) / int(gridDim.x);
+    const int it0 = int(blockIdx.x) * chunk, it1 = min(total, it0 + chunk);
     int cur = -1;
-    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+    for (int it = it0; it < it1; ++it) {
         int lo = 0, hi = n - 1;  // entry whose tile range holds `it`
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -647,13 +686,18 @@ pbas_batch_kernel(const PbasBatchEntry* __restrict__ E,
             const uint32_t* src = reinterpret_cast<const uint32_t*>(&E[lo].a);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
             for (int w = tid; w < int(sizeof(PbasArgs) / 4); w += 32 * TY) dst[w] = src[w];
+            if constexpr (KR > 0) {
+                const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(&GE[lo].a);
+                uint32_t* gdst = reinterpret_cast<uint32_t*>(&sg);
+                for (int w = tid; w < int(sizeof(GmmArgs) / 4); w += 32 * TY) gdst[w] = gsrc[w];
+            }
             __syncthreads();
             cur = lo;
         }
         const int local = it - E[lo].tile_off, tx = E[lo].tiles_x;
         const int x0 = (local % tx) * Geo<PX, TY>::TW, y0 = (local / tx) * TY;
-        if (E[lo].init) init_tile<NT, PX, TY>(sa, x0, y0, S.sm);
-        else classify_tile<NT, PX, TY>(sa, x0, y0, S, fresh);
+        if (E[lo].init) init_tile<NT, PX, TY, KR, KD>(sa, &sg, x0, y0, S.sm);
+        else classify_tile<NT, PX, TY, KR, KD>(sa, &sg, x0, y0, S, fresh);
         __syncthreads();
     }
 }
@@ -699,44 +743,75 @@ dim3 grid_for(const PbasArgs& a)
 namespace {
 FOS_PBAS_LAUNCHER(init_launch, pbas_init_kernel)
 FOS_PBAS_LAUNCHER(classify_launch, pbas_classify_kernel)
+
+template <int NT>
+bool fused_shape(const PbasArgs& a, const GmmArgs& g, cudaStream_t s, int px, int ty)
+{
+#define FOS_F(P, T)                                                                        \
+    if (px == P && ty == T) {                                                              \
+        fused_classify_kernel<NT, P, T><<<grid_for<P, T>(a), dim3(32, T), 0, s>>>(a, g);   \
+        return true;                                                                       \
+    }
+    FOS_F(2, 8) FOS_F(2, 4) FOS_F(4, 4) FOS_F(4, 8) FOS_F(1, 8)
+#undef FOS_F
+    return false;
+}
 }  // namespace
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s) { return init_launch(a, s); }
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s) { return classify_launch(a, s); }
 
-template <int NT>
-bool batch_shape(const PbasBatchEntry* E, const int* hdr, int blocks, int px, int ty, cudaStream_t s)
+LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStream_t s)
 {
-    if (px == 2 && ty == 8) pbas_batch_kernel<NT, 2, 8><<<blocks, dim3(32, 8), 0, s>>>(E, hdr);
-    else if (px == 2 && ty == 4) pbas_batch_kernel<NT, 2, 4><<<blocks, dim3(32, 4), 0, s>>>(E, hdr);
-    else if (px == 4 && ty == 4) pbas_batch_kernel<NT, 4, 4><<<blocks, dim3(32, 4), 0, s>>>(E, hdr);
-    else if (px == 4 && ty == 8) pbas_batch_kernel<NT, 4, 8><<<blocks, dim3(32, 8), 0, s>>>(E, hdr);
-    else if (px == 1 && ty == 8) pbas_batch_kernel<NT, 1, 8><<<blocks, dim3(32, 8), 0, s>>>(E, hdr);
-    else return false;
-    return true;
-}
-
-LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const int* hdr, int blocks, int N, int px,
-                               int ty, cudaStream_t s)
-{
-    const bool ok = N == 20 ? batch_shape<20>(E, hdr, blocks, px, ty, s)
-                            : batch_shape<0>(E, hdr, blocks, px, ty, s);
+    if (a.P == 0) return kLaunchOk;
+    const int px = (a.px > 1 && a.W % a.px == 0) ? a.px : 1;
+    const int ty = px == 1 ? 8 : a.ty;
+    const bool ok = a.N == 20 ? fused_shape<20>(a, g, s, px, ty) : fused_shape<0>(a, g, s, px, ty);
     if (!ok) return kLaunchUnsupported;
     return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
 }
 
-int pbas_batch_blocks_per_sm(int N, int px, int ty)
+template <int NT, int KR>
+bool batch_shape(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr, int blocks, int px,
+                 int ty, cudaStream_t s)
+{
+    if (px == 2 && ty == 8) pbas_batch_kernel<NT, 2, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
+    else if (px == 2 && ty == 4) pbas_batch_kernel<NT, 2, 4, KR><<<blocks, dim3(32, 4), 0, s>>>(E, G, hdr);
+    else if (px == 4 && ty == 4) pbas_batch_kernel<NT, 4, 4, KR><<<blocks, dim3(32, 4), 0, s>>>(E, G, hdr);
+    else if (px == 4 && ty == 8) pbas_batch_kernel<NT, 4, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
+    else if (px == 1 && ty == 8) pbas_batch_kernel<NT, 1, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
+    else return false;
+    return true;
+}
+
+LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr,
+                               int blocks, int N, int px, int ty, cudaStream_t s)
+{
+    bool ok;
+    if (G) ok = N == 20 ? batch_shape<20, 3>(E, G, hdr, blocks, px, ty, s) : batch_shape<0, 3>(E, G, hdr, blocks, px, ty, s);
+    else ok = N == 20 ? batch_shape<20, 0>(E, G, hdr, blocks, px, ty, s) : batch_shape<0, 0>(E, G, hdr, blocks, px, ty, s);
+    if (!ok) return kLaunchUnsupported;
+    return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+}
+
+template <int NT, int P, int T>
+int occ_of(int threads, bool fused)
 {
     int nb = 0;
-    cudaError_t e = cudaErrorInvalidValue;
+    const cudaError_t e = fused
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<NT, P, T, 3>, threads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<NT, P, T, 0>, threads, 0);
+    return e == cudaSuccess ? nb : 0;
+}
+
+int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused)
+{
     const int threads = 32 * ty;
-#define FOS_OCC(P, T)                                                                          \
-    if (px == P && ty == T)                                                                    \
-        e = N == 20 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<20, P, T>, threads, 0) \
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<0, P, T>, threads, 0);
+#define FOS_OCC(P, T) \
+    if (px == P && ty == T) return N == 20 ? occ_of<20, P, T>(threads, fused) : occ_of<0, P, T>(threads, fused);
     FOS_OCC(2, 8) FOS_OCC(2, 4) FOS_OCC(4, 4) FOS_OCC(4, 8) FOS_OCC(1, 8)
 #undef FOS_OCC
-    return e == cudaSuccess ? nb : 0;
+    return 0;
 }
 
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s)

@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_PKG, "libfos.so")
 
 METHOD_GMM = 1
 METHOD_PBAS = 2
-KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_FLUSH, KERNEL_INIT = 0, 1, 2, 3
-KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_flush", "init")
+KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_FLUSH, KERNEL_INIT, KERNEL_FUSED = 0, 1, 2, 3, 4
+KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_flush", "init", "fused_classify")
 STATUS = {0: "FOS_OK", 1: "FOS_ERR_INVALID_ARG", 2: "FOS_ERR_CUDA", 3: "FOS_ERR_OOM",
           4: "FOS_ERR_TIMEOUT", 5: "FOS_ERR_BUDGET", 6: "FOS_ERR_STATE", 7: "FOS_ERR_UNSUPPORTED"}
 
@@ -106,7 +106,7 @@ SIGNATURES = {
     "fos_batch_set_shape": (_st, [_vp, _i32, _i32, _i32]),
     "fos_batch_autotune": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(BatchTuning)]),
 }
-OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY = 1, 2, 3, 4
+OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY, OPT_FUSE = 1, 2, 3, 4, 5
 
 _lib = None
 
@@ -270,9 +270,9 @@ class Segmenter:
         self._check(self.lib.fos_set_timing(self.h, kernel_mask))
 
     def get_timing(self) -> dict:
-        arr = (KernelTiming * 4)()
+        arr = (KernelTiming * len(KERNEL_NAMES))()
         self._check(self.lib.fos_get_timing(self.h, arr))
-        return {KERNEL_NAMES[k]: (arr[k].launches, arr[k].total_ms) for k in range(4)}
+        return {KERNEL_NAMES[k]: (arr[k].launches, arr[k].total_ms) for k in range(len(KERNEL_NAMES))}
 
     def set_option(self, option: int, value: int) -> None:
         self._check(self.lib.fos_set_option(self.h, option, value))

@@ -123,3 +123,19 @@ def test_tile_shapes_give_identical_bits(px, ty):
     seg.set_option(fos.OPT_PBAS_TY, ty)
     seg.process_host(rgb, depth)
     np.testing.assert_array_equal(seg.get_state(), ref.get_state())
+
+
+@pytest.mark.parametrize("W,H", [(136, 40), (67, 45)])
+def test_fused_gmm_pbas_launch_gives_identical_bits(W, H):
+    # both methods, 3+3 model: frames >= 1 run as one fused launch; the same
+    # context with the option off runs the two separate kernels
+    from paper_2002_00250_gb300 import fos
+    rgb, depth, _ = scene(W, H, 8, seed=17)
+    a = fos.Segmenter(W, H)
+    b = fos.Segmenter(W, H)
+    b.set_option(fos.OPT_FUSE, 0)
+    ma = a.process_host(rgb, depth)
+    mb = b.process_host(rgb, depth)
+    np.testing.assert_array_equal(ma[0], mb[0])
+    np.testing.assert_array_equal(ma[1], mb[1])
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
