@@ -306,6 +306,57 @@ fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
                               void* stream, fos_batch_tuning* out);
 
 /* ---------------------------------------------------------------------------
+ * Differentiable (soft) GMM: parameter tuning against ground-truth masks.
+ * No counterpart in the paper, which runs the hard GMM of Sec. 3.1 with fixed
+ * parameters.  The hard match test d_k < L is replaced by sigmoid((L - d_k)/tau)
+ * (first-match and no-match weights follow from it), the mask by
+ * sigmoid((Q - L)/tau), and the loss is the mean binary cross-entropy against
+ * ground truth over frames 1..T-1 of every sequence.  Gradients are taken
+ * with respect to theta = (alpha, L = lambda^2, w_depth, v_init_rgb); the
+ * depth model starts at v_init_rgb * v_init_d_ratio.  Ranks, background sets,
+ * arg-mins and the v_min floor are decisions of the forward pass.  As tau -> 0
+ * the forward equals the hard GMM (colour K = 3, depth K = 3).
+ * ------------------------------------------------------------------------- */
+typedef struct fos_softgmm_params {
+    float alpha, lambda2, w_depth, v_init_rgb;  /* theta */
+    float tau;                                  /* sigmoid temperature */
+    float T_bg, v_min_rgb, v_min_d, v_init_d_ratio;
+    int32_t K_rgb, K_d;                         /* must be 3 and 3 */
+    int32_t ckpt_every;                         /* frames between checkpoints, 1..16 */
+    uint32_t depth_full_scale_mm;
+} fos_softgmm_params;
+
+typedef struct fos_softgmm fos_softgmm;
+
+void fos_softgmm_default_params(fos_softgmm_params* p);
+/* Workspace for `batch` sequences of `frames` frames of width x height:
+ * checkpoints of the model every ckpt_every frames (24 floats per pixel each). */
+fos_softgmm* fos_softgmm_create(int32_t width, int32_t height, int32_t batch, int32_t frames,
+                                const fos_softgmm_params* params);
+void fos_softgmm_destroy(fos_softgmm* g);
+const char* fos_softgmm_last_error(const fos_softgmm* g);
+/* Replaces theta (alpha, lambda2, w_depth, v_init_rgb); the next backward
+ * needs a forward with the new values. */
+fos_status fos_softgmm_set_theta(fos_softgmm* g, const float theta[4]);
+/*
+ * Forward over device sequences rgb [batch][frames][H][W][3] u8,
+ * depth [batch][frames][H][W] u16 (mm, 0 invalid), gt [batch][frames][H][W]
+ * u8 (nonzero = foreground; frame 0 unused).  Stores the checkpoints and
+ * writes the loss to *loss_out (host).  Synchronous on `stream`.
+ */
+fos_status fos_softgmm_forward(fos_softgmm* g, const uint8_t* d_rgb, const uint16_t* d_depth,
+                               const uint8_t* d_gt, double* loss_out, void* stream);
+/*
+ * Adjoint of the last forward (same inputs): writes d loss / d theta to
+ * grad_out[4] (host); d_pixel_grad (nullable, device, [batch][H][W][4] float)
+ * receives every pixel's contribution.  Sums are reduced in a fixed order
+ * (deterministic).  Synchronous on `stream`.
+ */
+fos_status fos_softgmm_backward(fos_softgmm* g, const uint8_t* d_rgb, const uint16_t* d_depth,
+                                const uint8_t* d_gt, double grad_out[4], float* d_pixel_grad,
+                                void* stream);
+
+/* ---------------------------------------------------------------------------
  * One PBAS frame step that allocates nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -215,3 +215,92 @@ def fingerprint(rgb, depth, gt, theta, **kw):
             out.append(torch.sort(key, dim=1, descending=True, stable=True).indices.numpy().tobytes())
             mr, md = mr2, _where(valid[t], md2, md)
     return hash(tuple(out))
+
+
+def decision_margins(rgb, depth, gt, theta, w_sig=1e-6, **kw):
+    """Per pixel (B, P): the smallest relative distance of any consequential
+    hard decision of the forward run from its threshold (background-set prefix
+    sums vs T_bg, arg-min over the background set, ranking comparisons and
+    v_min floors of components with weight >= w_sig), for excluding near-tie
+    pixels when comparing with a lower-precision implementation.  Decisions
+    among components of negligible weight (soft-match ghosts) change the loss
+    only in proportion to that weight and are not counted."""
+    o = dict(DEFAULTS)
+    o.update(kw)
+    Bn, T = rgb.shape[:2]
+    P = rgb.shape[2] * rgb.shape[3]
+    alpha, L, w, v0 = (torch.tensor(float(v), dtype=torch.float64) for v in theta)
+    out = np.full((Bn, P), np.inf)
+
+    def rel(a, b):
+        # exact ties (identical untouched components) resolve the same way in
+        # any precision: not a near-tie
+        den = torch.maximum(torch.maximum(a.abs(), b.abs()), torch.full_like(a, 1e-300))
+        r = ((a - b).abs() / den).numpy()
+        return np.where((a == b).numpy(), np.inf, r)
+
+    def upd(b, mask, r_):
+        out[b] = np.where(mask, np.minimum(out[b], r_), out[b])
+
+    for b in range(Bn):
+        xs = torch.from_numpy(rgb[b].reshape(T, P, 3).astype(np.float64))
+        d8 = depth_to_u8(depth[b], o["depth_full_scale_mm"]).reshape(T, P)
+        xd = torch.from_numpy(d8.astype(np.float64))[:, :, None]
+        valid = torch.from_numpy(d8 != 0)
+        mr = _init(xs[0], o["K_rgb"], v0)
+        md = _init(xd[0], o["K_d"], v0 * o["v_init_d_ratio"])
+        for t in range(1, T):
+            for m, x, vmin, vi, msk in ((mr, xs[t], o["v_min_rgb"], v0, torch.ones(P, dtype=torch.bool)),
+                                        (md, xd[t], o["v_min_d"], v0 * o["v_init_d_ratio"], valid[t])):
+                K = m.w.shape[1]
+                mk_np = msk.numpy()
+                sig = (m.w >= w_sig).numpy()
+                cum = torch.cumsum(m.w, 1)
+                for k in range(K - 1):
+                    upd(b, mk_np, rel(cum[:, k], torch.full_like(cum[:, k], o["T_bg"])))
+                s = ((x[:, None, :] - m.mu) ** 2).sum(-1)
+                d = s / (x.shape[1] * m.v)
+                inB = ((cum - m.w) <= o["T_bg"]).numpy()
+                for i in range(K):
+                    for j in range(i + 1, K):
+                        upd(b, mk_np & inB[:, i] & inB[:, j], rel(d[:, i], d[:, j]))
+                mkk = torch.sigmoid((L - d) / o["tau"])
+                rr, Pr = [], torch.ones(P, dtype=torch.float64)
+                for k in range(K):
+                    rr.append(mkk[:, k] * Pr)
+                    Pr = Pr * (1 - mkk[:, k])
+                r = torch.stack(rr, 1)
+                w1 = (1 - alpha) * m.w + alpha * r
+                rho = _rho(m.w, w1, r, alpha)
+                u = m.v + rho * (s / x.shape[1] - m.v)
+                for k in range(K):
+                    # a component already at the floor moves by rho * (...) only;
+                    # either branch changes the loss by terms proportional to rho
+                    at_floor = (m.v[:, k] == vmin).numpy()
+                    upd(b, mk_np & sig[:, k] & ~at_floor, rel(u[:, k], torch.full_like(u[:, k], vmin)))
+                nm = _step(m, x, d, s, alpha, L, o["tau"], vi, vmin)
+                key = nm.w / torch.sqrt(nm.v)
+                nsig = (nm.w >= w_sig).numpy()
+                for i in range(K):
+                    for j in range(i + 1, K):
+                        upd(b, mk_np & (nsig[:, i] | nsig[:, j]), rel(key[:, i], key[:, j]))
+            dB_r, d_r, s_r = _classify(mr, xs[t], o["T_bg"])
+            dB_d, d_d, s_d = _classify(md, xd[t], o["T_bg"])
+            mr2 = _step(mr, xs[t], d_r, s_r, alpha, L, o["tau"], v0, o["v_min_rgb"])
+            md2 = _step(md, xd[t], d_d, s_d, alpha, L, o["tau"], v0 * o["v_init_d_ratio"], o["v_min_d"])
+            mr, md = mr2, _where(valid[t], md2, md)
+    return out
+
+
+def pixel_grads(rgb, depth, gt, theta, pixels, **kw):
+    """d loss / d theta restricted to the listed (sequence, pixel) pairs, each
+    pixel run alone (pixels are independent), normalised as in the full loss."""
+    Bn, T, H, W = rgb.shape[:4]
+    P = H * W
+    out = []
+    for b, p in pixels:
+        y, x = divmod(int(p), W)
+        _, g = loss_and_grad(rgb[b:b + 1, :, y:y + 1, x:x + 1], depth[b:b + 1, :, y:y + 1, x:x + 1],
+                             gt[b:b + 1, :, y:y + 1, x:x + 1], theta, **kw)
+        out.append(g / (Bn * P))
+    return np.array(out)

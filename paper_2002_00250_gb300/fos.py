@@ -65,6 +65,17 @@ class BatchTuning(ctypes.Structure):
                 ("pbas_ty", ctypes.c_int32), ("ms_per_step", ctypes.c_float)]
 
 
+class SoftParams(ctypes.Structure):
+    """Mirror of fos_softgmm_params."""
+    _fields_ = [("alpha", ctypes.c_float), ("lambda2", ctypes.c_float),
+                ("w_depth", ctypes.c_float), ("v_init_rgb", ctypes.c_float),
+                ("tau", ctypes.c_float), ("T_bg", ctypes.c_float),
+                ("v_min_rgb", ctypes.c_float), ("v_min_d", ctypes.c_float),
+                ("v_init_d_ratio", ctypes.c_float), ("K_rgb", ctypes.c_int32),
+                ("K_d", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
+                ("depth_full_scale_mm", ctypes.c_uint32)]
+
+
 class KernelTiming(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -105,6 +116,13 @@ SIGNATURES = {
     "fos_batch_process_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fos_batch_set_shape": (_st, [_vp, _i32, _i32, _i32]),
     "fos_batch_autotune": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(BatchTuning)]),
+    "fos_softgmm_default_params": (None, [ctypes.POINTER(SoftParams)]),
+    "fos_softgmm_create": (_vp, [_i32, _i32, _i32, _i32, ctypes.POINTER(SoftParams)]),
+    "fos_softgmm_destroy": (None, [_vp]),
+    "fos_softgmm_last_error": (ctypes.c_char_p, [_vp]),
+    "fos_softgmm_set_theta": (_st, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "fos_softgmm_forward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "fos_softgmm_backward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
 }
 OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY, OPT_FUSE = 1, 2, 3, 4, 5
 

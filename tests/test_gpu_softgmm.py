@@ -1,0 +1,100 @@
+"""Soft-GMM forward and hand-written adjoint on the GPU (FP32) against the
+FP64 oracle (PyTorch autograd), through the C ABI and the autograd.Function.
+
+Tolerances from the arithmetic: one FP32 step rounds each quantity to ~1e-7
+relative; over T = 12-16 frames of the recurrence and the sigmoid/BCE chain
+the per-pixel gradient drifts to ~1e-5..1e-4 relative, so per-pixel
+gradients must agree to 2e-3 relative (+ 1e-4 of the largest pixel
+gradient) and the loss to 1e-4; pixels where a hard decision of the forward
+(ranks, background sets, arg-mins, v_min floors) lies within 1e-4 relative
+of its threshold in the FP64 run are excluded from the per-pixel check (the
+FP32 run may take the other branch there).
+"""
+import numpy as np
+import pytest
+
+from _helpers import scene
+
+pytestmark = pytest.mark.gpu
+THETA = (0.05, 6.25, 0.5, 36.0)
+
+
+def _data(B, W, H, T, seed):
+    rgb, depth, gt = [], [], []
+    for b in range(B):
+        r, d, g = scene(W, H, T, seed=seed + b, n_objects=2, hole_fraction=0.05)
+        rgb.append(r); depth.append(d); gt.append(g)
+    return np.stack(rgb), np.stack(depth), np.stack(gt)
+
+
+def _run_gpu(rgb, depth, gt, theta, ck=8, pixel=True):
+    import torch
+    from paper_2002_00250_gb300 import softgmm
+    B, T, H, W = rgb.shape[:4]
+    ws = softgmm.SoftGMM(W, H, B, T, ckpt_every=ck)
+    ws.set_theta(theta)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rgb, depth, gt)]
+    loss = ws.forward(*d)
+    pg = torch.zeros((B, H * W, 4), dtype=torch.float32, device="cuda") if pixel else None
+    g = ws.backward(*d, pixel_grad=pg)
+    return loss, np.array(g), (pg.cpu().numpy().astype(np.float64) if pixel else None)
+
+
+@pytest.mark.parametrize("ck", [4, 8])
+def test_loss_and_gradient_match_oracle(ck):
+    from oracle import softgmm as osg
+    rgb, depth, gt = _data(2, 12, 9, 13, seed=40)
+    l_o, g_o = osg.loss_and_grad(rgb, depth, gt, THETA)
+    l_g, g_g, pg = _run_gpu(rgb, depth, gt, THETA, ck=ck)
+    assert l_g == pytest.approx(l_o, rel=1e-4)
+    # per-pixel contributions where every decision is clear of its threshold
+    margin = osg.decision_margins(rgb, depth, gt, THETA)
+    B, P = margin.shape
+    rng = np.random.default_rng(0)
+    cand = [(b, p) for b in range(B) for p in range(P) if margin[b, p] >= 1e-4]
+    assert len(cand) >= 0.8 * B * P
+    pick = [cand[i] for i in rng.choice(len(cand), size=min(40, len(cand)), replace=False)]
+    want = osg.pixel_grads(rgb, depth, gt, THETA, pick)
+    got = np.array([pg[b, p] for b, p in pick])
+    scale = np.abs(want).max(axis=0) + 1e-300
+    np.testing.assert_array_less(np.abs(got - want), 2e-3 * np.abs(want) + 1e-4 * scale)
+    # totals: the excluded near-tie pixels may differ, bounded by their share
+    np.testing.assert_allclose(g_g, g_o, rtol=5e-2, atol=1e-3 * np.abs(g_o).max())
+
+
+def test_checkpoint_interval_does_not_change_results():
+    rgb, depth, gt = _data(1, 16, 8, 17, seed=50)
+    a = _run_gpu(rgb, depth, gt, THETA, ck=1)
+    b = _run_gpu(rgb, depth, gt, THETA, ck=8)
+    c = _run_gpu(rgb, depth, gt, THETA, ck=16)
+    assert a[0] == b[0] == c[0]
+    np.testing.assert_array_equal(a[2], b[2])
+    np.testing.assert_array_equal(a[2], c[2])
+
+
+def test_deterministic_reduction():
+    rgb, depth, gt = _data(2, 20, 10, 9, seed=60)
+    r1 = _run_gpu(rgb, depth, gt, THETA, pixel=False)
+    r2 = _run_gpu(rgb, depth, gt, THETA, pixel=False)
+    assert r1[0] == r2[0]
+    np.testing.assert_array_equal(r1[1], r2[1])
+
+
+def test_autograd_function_and_descent():
+    import torch
+    from paper_2002_00250_gb300 import softgmm
+    rgb, depth, gt = _data(2, 16, 12, 10, seed=70)
+    B, T, H, W = rgb.shape[:4]
+    ws = softgmm.SoftGMM(W, H, B, T)
+    data = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rgb, depth, gt)]
+    theta = torch.tensor(THETA, dtype=torch.float64, requires_grad=True)
+    loss = softgmm.SoftGMMLoss.apply(theta, ws, *data)
+    loss.backward()
+    g_ref = np.array(ws.backward(*data))
+    np.testing.assert_array_equal(theta.grad.numpy(), g_ref)
+    # a small step in log-parameter space along minus the gradient lowers the loss
+    with torch.no_grad():
+        d = -theta.grad * theta
+        th1 = theta * torch.exp(1e-4 * d / d.abs().max())
+    l1 = softgmm.SoftGMMLoss.apply(th1, ws, *data)
+    assert float(l1.detach()) < float(loss.detach())
