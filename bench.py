@@ -438,6 +438,152 @@ def run_batch16(args):
     print(json.dumps(out), flush=True)
 
 
+def run_softgmm(args):
+    """Soft-GMM forward + adjoint: 8 sequences of 640x480, 64 frames, checkpoint
+    every 8 frames (a secondary workload).  Reports seconds per iteration and
+    Mpixel-frames/s of the forward+adjoint pass; with --check, also the
+    gradient against the FP64 oracle on a 24x24 crop of every sequence."""
+    import torch
+    from paper_2002_00250_gb300 import softgmm, synth
+
+    B, T, W, H = 8, args.frames if args.frames != NFRAMES else 64, 640, 480
+    dev = torch.device("cuda", 0)
+    rgb = torch.empty((B, T, H, W, 3), dtype=torch.uint8, device=dev)
+    depth = torch.empty((B, T, H, W), dtype=torch.uint16, device=dev)
+    gt = torch.empty((B, T, H, W), dtype=torch.uint8, device=dev)
+    for b in range(B):
+        sc = synth.RGBDScene(synth.SceneConfig(W, H, T, seed=0, stream_id=100 + b), device=dev)
+        rgb[b], depth[b], gt[b] = sc.sequence(0, T)
+    theta = (0.001, 6.25, 0.5, 36.0)
+    ws = softgmm.SoftGMM(W, H, B, T, ckpt_every=8)
+    ws.set_theta(theta)
+
+    def it():
+        loss = ws.forward(rgb, depth, gt)
+        return loss, ws.backward(rgb, depth, gt)
+
+    for _ in range(args.warmup):
+        it()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        loss, g = it()
+    dt = (time.perf_counter() - t0) / args.steps
+    out = {"metric": "soft-GMM forward+adjoint", "value": round(dt, 4), "unit": "s/iteration",
+           "mpx_frames_per_s": round(B * T * W * H / dt / 1e6, 1), "higher_is_better": False,
+           "steps": args.steps, "warmup": args.warmup, "dtype": "f32 (reductions f64)", "data": "synthetic",
+           "config": {"workload": f"soft-GMM {B}x{W}x{H}x{T}, checkpoint every 8", "theta": theta},
+           "loss": loss, "grad": g}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve32(args):
+    """Serving loop: 32 camera streams of mixed resolutions arriving at 30 fps
+    with +/-5 ms jitter (truncated Poisson offsets), staggered joins, some
+    streams leaving, admission by a device-memory budget of 75 % of the total
+    demand, 10,000 frames.  Reports p50/p99 latency (submit -> masks in host
+    memory) and throughput; a second pass submits as fast as possible."""
+    import threading
+    import torch
+    from paper_2002_00250_gb300 import fos, synth
+
+    rs = np.random.default_rng(5)
+    choices = [(424, 240), (640, 480), (848, 480), (1280, 720), (1920, 1080)]
+    sizes = [choices[i] for i in rs.integers(0, len(choices), size=32)]
+    pool_n = 8
+    dev = torch.device("cuda", 0)
+    pools = []
+    for s_id, (w, h) in enumerate(sizes):
+        sc = synth.RGBDScene(synth.config_stream(w, h, pool_n, seed=0, stream_id=s_id), device=dev)
+        r, d, _ = sc.sequence(0, pool_n)
+        pools.append((synth.to_numpy(r), synth.to_numpy(d)))
+    p = fos.default_params()
+    lib = fos.load()
+    need = [lib.fos_stream_device_bytes(w, h, p) + 14 * w * h for w, h in sizes]
+    budget = int(0.75 * sum(need))
+    total_frames = 10000
+    period = 1.0 / 30.0
+
+    def run(paced: bool):
+        srv = fos.Server(budget, 32)
+        sids = [None] * 32
+        outs = {}
+        lat, queue = [], []
+        done = [0]
+        stop = [False]
+
+        def poller():
+            while not stop[0] or done[0] < total_frames:
+                for r in srv.poll(1024):
+                    lat.append(r[3])
+                    queue.append(r[4])
+                    outs.pop(r[2], None)
+                    done[0] += 1
+                if stop[0] and done[0] >= total_frames:
+                    break
+                time.sleep(0.0005)
+
+        th = threading.Thread(target=poller, daemon=True)
+        th.start()
+        # arrival schedule: stream s joins at s * 40 ms; every 5th stream leaves
+        # after 120 frames; offsets of each frame from its 30 fps slot: Poisson
+        # (mean 5 ms) minus 5 ms, truncated to +/-5 ms
+        events = []
+        per = total_frames // 32 + 1
+        for s_id in range(32):
+            n = 120 if s_id % 5 == 4 else per + 40
+            j = np.clip(rs.poisson(5.0, size=n) - 5.0, -5.0, 5.0) * 1e-3
+            t = s_id * 0.040 + np.arange(n) * period + j
+            events += [(float(t[k]), s_id, k) for k in range(n)]
+        events.sort()
+        events = events[:total_frames]
+        last = {}
+        for _, s_id, k in events:
+            last[s_id] = k
+        t0 = time.perf_counter()
+        tag = 0
+        for (ta, s_id, k) in events:
+            if sids[s_id] is None:
+                sids[s_id] = srv.open_stream(*sizes[s_id], stream_id=s_id)
+            if paced:
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+            w, h = sizes[s_id]
+            mg = np.empty((h, w), np.uint8)
+            mp = np.empty((h, w), np.uint8)
+            outs[tag] = (mg, mp)
+            r, d = pools[s_id]
+            srv.submit(sids[s_id], r[k % pool_n], d[k % pool_n], mg, mp, tag)
+            tag += 1
+            if k == last[s_id] and s_id % 5 == 4:
+                srv.close_stream(sids[s_id])
+        stop[0] = True
+        th.join()
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        px = sum(sizes[s][0] * sizes[s][1] for _, s, _ in events)
+        return {"frames": len(events), "wall_s": round(wall, 3),
+                "mpx_frames_per_s": round(px / wall / 1e6, 1),
+                "latency_ms": {"p50": round(float(np.percentile(lat, 50)) / 1e3, 3),
+                               "p99": round(float(np.percentile(lat, 99)) / 1e3, 3),
+                               "max": round(float(np.max(lat)) / 1e3, 3)},
+                "queue_ms_p50": round(float(np.percentile(queue, 50)) / 1e3, 3),
+                "ticks": st["ticks"], "frames_per_tick": round(st["frames_done"] / max(1, st["ticks"]), 2),
+                "gpu_busy_s": round(st["busy_us"] / 1e6, 3)}
+
+    paced = run(True)
+    saturated = run(False)
+    out = {"metric": "serving p99 frame latency", "value": paced["latency_ms"]["p99"], "unit": "ms",
+           "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "32 streams 424x240..1920x1080 at 30 fps +/-5 ms, 10,000 frames, "
+                                  "HBM budget 75 % of demand", "budget_bytes": budget,
+                      "sizes": sizes},
+           "paced": paced, "saturated": saturated}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,13 +596,17 @@ def main():
                     help="frames per step (a shorter sequence for profiler captures)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run the device-resident steps only (for profiler captures)")
-    ap.add_argument("--workload", default="720p", choices=["720p", "batch16"],
+    ap.add_argument("--workload", default="720p", choices=["720p", "batch16", "softgmm", "serve32"],
                     help="720p: the headline single-stream sequence; batch16: 16 mixed streams")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch16":
         run_batch16(args)
+    elif args.workload == "softgmm":
+        run_softgmm(args)
+    elif args.workload == "serve32":
+        run_serve32(args)
     else:
         run_ours(args)
 

@@ -306,6 +306,58 @@ fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
                               void* stream, fos_batch_tuning* out);
 
 /* ---------------------------------------------------------------------------
+ * Serving loop with continuous batching.  No counterpart in the paper.
+ *
+ * A server owns a batch and a worker thread.  Streams (cameras) are admitted
+ * by a device-memory budget: each needs fos_stream_device_bytes plus two
+ * input and two mask buffers; a stream that does not fit, or finds no free
+ * slot, waits in FIFO order until others close.  fos_server_submit copies a
+ * frame into pinned host memory and returns at once.  Each worker tick takes
+ * the oldest pending frame of every admitted stream (frames of one stream run
+ * in order), runs them as one batched launch, and writes the masks into the
+ * caller's buffers given at submit time; two ticks are in flight, so frames
+ * that arrive while one runs join the next.  Results are identical to
+ * processing each stream alone.  All calls are thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct fos_server fos_server;
+
+typedef struct fos_server_result {
+    int32_t stream;      /* handle from fos_server_open_stream */
+    int32_t status;      /* fos_status of the frame */
+    int64_t tag;         /* caller's tag from fos_server_submit */
+    double latency_us;   /* submit -> masks written */
+    double queue_us;     /* submit -> its tick launched */
+} fos_server_result;
+
+typedef struct fos_server_stats_t {
+    int64_t ticks, frames_done;
+    size_t device_bytes_used;
+    int32_t streams_active, streams_waiting;
+    double busy_us;      /* sum over ticks of launch -> completion */
+} fos_server_stats_t;
+
+/* Server over one device-memory budget (bytes) and at most max_streams
+ * admitted streams.  NULL on error (fos_last_error(NULL)). */
+fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes, int32_t max_streams);
+/* Stops the worker (frames in flight complete; pending ones are dropped). */
+void fos_server_destroy(fos_server* s);
+const char* fos_server_last_error(const fos_server* s);
+/* Registers a camera; returns its handle (admitted now or when memory frees
+ * up), -1 if it can never fit the budget. */
+int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uint32_t stream_id);
+/* The stream leaves after its submitted frames complete; its memory is freed. */
+fos_status fos_server_close_stream(fos_server* s, int32_t stream);
+/* Queues one host frame of the stream (copied before returning).  The masks
+ * (either may be NULL) are written when the frame completes: keep those
+ * buffers valid until fos_server_poll reports the tag. */
+fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
+                             uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag);
+/* Up to max_results completed frames, oldest first; returns how many. */
+int32_t fos_server_poll(fos_server* s, fos_server_result* out, int32_t max_results);
+/* Counters; FOS_ERR_CUDA once the worker has stopped on an error. */
+fos_status fos_server_stats(fos_server* s, fos_server_stats_t* out);
+
+/* ---------------------------------------------------------------------------
  * Differentiable (soft) GMM: parameter tuning against ground-truth masks.
  * No counterpart in the paper, which runs the hard GMM of Sec. 3.1 with fixed
  * parameters.  The hard match test d_k < L is replaced by sigmoid((L - d_k)/tau)

@@ -1,0 +1,452 @@
+// server.cu -- serving loop with continuous batching over camera streams.
+//
+// No counterpart in the paper (one camera there).  Streams are admitted by
+// an HBM budget: a stream needs its device-resident models plus two input and
+// two mask buffers; a stream that does not fit waits (FIFO) until others
+// leave.  fos_server_submit copies a frame into pinned host memory and
+// returns at once.  A worker thread runs ticks: each tick takes the oldest
+// pending frame of every admitted stream (at most one per stream, so every
+// stream's frames run in order), copies them to the device, runs ONE batched
+// launch over all of them (fos_batch), and copies the masks back.  Two ticks
+// are in flight: frames that arrive while a tick runs are admitted into the
+// next one.  Completed frames are delivered into the caller's mask buffers
+// and reported by fos_server_poll with their latency.
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ctx.h"
+#include "fos.h"
+#include "fos_internal.h"
+
+using namespace fos;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_us()
+{
+    return std::chrono::duration<double, std::micro>(Clock::now().time_since_epoch()).count();
+}
+
+struct Frame {
+    int64_t tag;
+    uint8_t* host_in;    // pinned: rgb (P*3) then depth (P*2)
+    uint8_t* out_gmm;    // caller's buffers (nullable per method)
+    uint8_t* out_pbas;
+    double t_submit;
+};
+
+struct Stream {
+    int id;              // server handle
+    int32_t W, H;
+    uint32_t stream_id;
+    size_t bytes = 0;    // device bytes charged against the budget
+    int slot = -1;       // batch slot once admitted
+    bool closing = false;
+    std::deque<Frame> pending;
+    int inflight = 0;    // frames of this stream in ticks not yet completed
+    uint8_t* d_in[2] = {nullptr, nullptr};     // device rgb+depth, by frame parity
+    uint8_t* d_mg[2] = {nullptr, nullptr};
+    uint8_t* d_mp[2] = {nullptr, nullptr};
+    uint8_t* h_mg[2] = {nullptr, nullptr};     // pinned mask staging
+    uint8_t* h_mp[2] = {nullptr, nullptr};
+    int64_t nframes = 0;
+    std::vector<uint8_t*> free_in;               // reusable pinned input buffers
+};
+
+struct TickItem {
+    int stream;
+    int parity;
+    Frame f;
+};
+
+struct Tick {
+    std::vector<TickItem> items;
+    cudaEvent_t done = nullptr;
+    double t_launch = 0.0;
+};
+
+}  // namespace
+
+struct fos_server {
+    fos_params prm{};
+    size_t budget = 0, used = 0;
+    int max_streams = 0;
+    fos_batch* batch = nullptr;
+    cudaStream_t cs = nullptr;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<Stream*> streams;     // by handle (nullptr once gone)
+    std::deque<int> waiting;          // handles waiting for admission
+    std::deque<fos_server_result> results;
+    std::thread worker;
+    bool stop = false;
+    std::string err;
+    int64_t ticks = 0, frames_done = 0;
+    double busy_us = 0.0;
+};
+
+namespace {
+
+size_t stream_bytes(const fos_server* s, int32_t W, int32_t H)
+{
+    const size_t P = size_t(W) * size_t(H);
+    return fos_stream_device_bytes(W, H, &s->prm) + 2 * (P * 5 + 2 * P);
+}
+
+void free_stream_buffers(Stream* st)
+{
+    for (uint8_t* b : st->free_in) cudaFreeHost(b);
+    st->free_in.clear();
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(st->d_in[k]);
+        cudaFree(st->d_mg[k]);
+        cudaFree(st->d_mp[k]);
+        cudaFreeHost(st->h_mg[k]);
+        cudaFreeHost(st->h_mp[k]);
+        st->d_in[k] = st->d_mg[k] = st->d_mp[k] = st->h_mg[k] = st->h_mp[k] = nullptr;
+    }
+}
+
+// Admits waiting streams in FIFO order while they fit (worker thread, lock held).
+void admit(fos_server* s)
+{
+    while (!s->waiting.empty()) {
+        Stream* st = s->streams[s->waiting.front()];
+        if (!st) {
+            s->waiting.pop_front();
+            continue;
+        }
+        if (s->used + st->bytes > s->budget) break;
+        const int slot = fos_batch_add_stream(s->batch, st->W, st->H, st->stream_id);
+        if (slot < 0) break;  // no free slot yet
+        const size_t P = size_t(st->W) * size_t(st->H);
+        bool ok = true;
+        for (int k = 0; k < 2 && ok; ++k) {
+            ok = cudaMalloc(&st->d_in[k], P * 5 + 16) == cudaSuccess &&
+                 cudaMalloc(&st->d_mg[k], P + 16) == cudaSuccess &&
+                 cudaMalloc(&st->d_mp[k], P + 16) == cudaSuccess &&
+                 cudaMallocHost(&st->h_mg[k], P + 16) == cudaSuccess &&
+                 cudaMallocHost(&st->h_mp[k], P + 16) == cudaSuccess;
+        }
+        if (!ok) {
+            free_stream_buffers(st);
+            fos_batch_remove_stream(s->batch, slot);
+            s->err = "admission: device or pinned memory exhausted";
+            break;
+        }
+        st->slot = slot;
+        s->used += st->bytes;
+        s->waiting.pop_front();
+    }
+}
+
+void publish(fos_server* s, Tick& t)
+{
+    const double done = now_us();
+    for (TickItem& it : t.items) {
+        Stream* st = s->streams[it.stream];
+        const size_t P = size_t(st->W) * size_t(st->H);
+        if (it.f.out_gmm) std::memcpy(it.f.out_gmm, st->h_mg[it.parity], P);
+        if (it.f.out_pbas) std::memcpy(it.f.out_pbas, st->h_mp[it.parity], P);
+        st->free_in.push_back(it.f.host_in);
+        fos_server_result r{};
+        r.stream = it.stream;
+        r.tag = it.f.tag;
+        r.status = FOS_OK;
+        r.latency_us = done - it.f.t_submit;
+        r.queue_us = t.t_launch - it.f.t_submit;
+        s->results.push_back(r);
+        st->inflight -= 1;
+        s->frames_done += 1;
+    }
+    cudaEventDestroy(t.done);
+    t.done = nullptr;
+}
+
+// Streams that asked to close and have nothing left leave; their memory is freed.
+void retire(fos_server* s)
+{
+    for (size_t h = 0; h < s->streams.size(); ++h) {
+        Stream* st = s->streams[h];
+        if (!st || !st->closing || !st->pending.empty() || st->inflight > 0) continue;
+        if (st->slot >= 0) {
+            fos_batch_remove_stream(s->batch, st->slot);
+            s->used -= st->bytes;
+        }
+        free_stream_buffers(st);
+        delete st;
+        s->streams[h] = nullptr;
+    }
+}
+
+void worker_main(fos_server* s)
+{
+    cudaSetDevice(s->device);
+    std::deque<Tick> inflight;
+    std::vector<int32_t> slots;
+    std::vector<const uint8_t*> rgb;
+    std::vector<const uint16_t*> dep;
+    std::vector<uint8_t*> mg, mp;
+    for (;;) {
+        Tick t;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            retire(s);
+            admit(s);
+            auto ready = [&] {
+                if (s->stop) return true;
+                for (Stream* st : s->streams)
+                    if (st && st->slot >= 0 && !st->pending.empty()) return true;
+                return false;
+            };
+            // idle: sleep until a frame arrives (or re-check admission and
+            // closing streams every millisecond)
+            if (inflight.empty()) s->cv.wait_for(lk, std::chrono::milliseconds(1), ready);
+            if (s->stop && inflight.empty()) break;
+            if (!ready() && inflight.empty()) continue;
+            // continuous batching: the oldest frame of every admitted stream
+            // whose previous frame is not still using this parity's buffers
+            for (size_t h = 0; h < s->streams.size(); ++h) {
+                Stream* st = s->streams[h];
+                if (!st || st->slot < 0 || st->pending.empty() || st->inflight >= 2) continue;
+                TickItem it;
+                it.stream = int(h);
+                it.parity = int(st->nframes & 1);
+                it.f = st->pending.front();
+                st->pending.pop_front();
+                st->nframes += 1;
+                st->inflight += 1;
+                t.items.push_back(it);
+            }
+        }
+        if (!t.items.empty()) {
+            slots.clear(); rgb.clear(); dep.clear(); mg.clear(); mp.clear();
+            cudaError_t e = cudaSuccess;
+            for (TickItem& it : t.items) {
+                Stream* st = s->streams[it.stream];
+                const size_t P = size_t(st->W) * size_t(st->H);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(st->d_in[it.parity], it.f.host_in, P * 5, cudaMemcpyHostToDevice, s->cs);
+                slots.push_back(st->slot);
+                rgb.push_back(st->d_in[it.parity]);
+                dep.push_back(reinterpret_cast<const uint16_t*>(st->d_in[it.parity] + P * 3));
+                mg.push_back(st->d_mg[it.parity]);
+                mp.push_back(st->d_mp[it.parity]);
+            }
+            t.t_launch = now_us();
+            fos_status bst = FOS_OK;
+            if (e == cudaSuccess)
+                bst = fos_batch_process_device(s->batch, int32_t(slots.size()), slots.data(), rgb.data(),
+                                               dep.data(), mg.data(), mp.data(), s->cs);
+            for (TickItem& it : t.items) {
+                Stream* st = s->streams[it.stream];
+                const size_t P = size_t(st->W) * size_t(st->H);
+                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_GMM))
+                    e = cudaMemcpyAsync(st->h_mg[it.parity], st->d_mg[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
+                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_PBAS))
+                    e = cudaMemcpyAsync(st->h_mp[it.parity], st->d_mp[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
+            }
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(t.done, s->cs);
+            if (e != cudaSuccess || bst != FOS_OK) {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->err = e != cudaSuccess ? cudaGetErrorString(e) : fos_batch_last_error(s->batch);
+                s->stop = true;
+                for (TickItem& it : t.items) {
+                    fos_server_result r{};
+                    r.stream = it.stream;
+                    r.tag = it.f.tag;
+                    r.status = e != cudaSuccess ? FOS_ERR_CUDA : bst;
+                    s->results.push_back(r);
+                    s->streams[it.stream]->inflight -= 1;
+                    cudaFreeHost(it.f.host_in);
+                }
+                if (t.done) cudaEventDestroy(t.done);
+                break;
+            }
+            inflight.push_back(std::move(t));
+        }
+        // deliver finished ticks; keep at most two in flight
+        while (!inflight.empty()) {
+            Tick& old = inflight.front();
+            const bool full = inflight.size() >= 2;
+            const cudaError_t q = full ? cudaEventSynchronize(old.done) : cudaEventQuery(old.done);
+            if (q == cudaErrorNotReady) break;
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->busy_us += now_us() - old.t_launch;
+            s->ticks += 1;
+            publish(s, old);
+            inflight.pop_front();
+        }
+        if (!inflight.empty() && t.items.empty()) {
+            // nothing new to launch: wait for the oldest tick or a new frame
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait_for(lk, std::chrono::microseconds(200));
+        }
+    }
+    for (Tick& t : inflight) {
+        cudaEventSynchronize(t.done);
+        std::lock_guard<std::mutex> lk(s->mu);
+        publish(s, t);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes, int32_t max_streams)
+{
+    std::string why;
+    if (ctx_validate_params(params, why) != FOS_OK || max_streams < 1 || hbm_budget_bytes == 0) {
+        set_thread_error(why.empty() ? "fos_server_create: bad arguments" : why.c_str());
+        return nullptr;
+    }
+    fos_server* s = new fos_server();
+    s->prm = *params;
+    s->budget = hbm_budget_bytes;
+    s->max_streams = max_streams;
+    cudaGetDevice(&s->device);
+    s->batch = fos_batch_create(max_streams, params);
+    if (!s->batch || cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess) {
+        if (s->batch) fos_batch_destroy(s->batch);
+        delete s;
+        return nullptr;
+    }
+    s->worker = std::thread(worker_main, s);
+    return s;
+}
+
+void fos_server_destroy(fos_server* s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    for (Stream* st : s->streams) {
+        if (!st) continue;
+        for (Frame& f : st->pending) cudaFreeHost(f.host_in);
+        free_stream_buffers(st);
+        delete st;
+    }
+    fos_batch_destroy(s->batch);
+    cudaStreamDestroy(s->cs);
+    delete s;
+}
+
+const char* fos_server_last_error(const fos_server* s) { return s ? s->err.c_str() : ""; }
+
+int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uint32_t stream_id)
+{
+    if (!s || width < 1 || height < 1) return -1;
+    Stream* st = new Stream();
+    st->W = width;
+    st->H = height;
+    st->stream_id = stream_id;
+    st->bytes = stream_bytes(s, width, height);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (st->bytes > s->budget) {
+        s->err = "stream needs more device memory than the whole budget";
+        delete st;
+        return -1;
+    }
+    st->id = int(s->streams.size());
+    s->streams.push_back(st);
+    s->waiting.push_back(st->id);
+    s->cv.notify_all();
+    return st->id;
+}
+
+fos_status fos_server_close_stream(fos_server* s, int32_t stream)
+{
+    if (!s) return FOS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream]) return FOS_ERR_INVALID_ARG;
+    s->streams[stream]->closing = true;
+    s->cv.notify_all();
+    return FOS_OK;
+}
+
+fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
+                             uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag)
+{
+    if (!s || !rgb || !depth) return FOS_ERR_INVALID_ARG;
+    size_t P;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream] || s->streams[stream]->closing)
+            return FOS_ERR_INVALID_ARG;
+        if (s->stop) return FOS_ERR_STATE;
+        P = size_t(s->streams[stream]->W) * size_t(s->streams[stream]->H);
+    }
+    Frame f{};
+    f.tag = tag;
+    f.out_gmm = mask_gmm;
+    f.out_pbas = mask_pbas;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->streams[stream]) return FOS_ERR_INVALID_ARG;
+        std::vector<uint8_t*>& pool = s->streams[stream]->free_in;
+        if (!pool.empty()) {
+            f.host_in = pool.back();
+            pool.pop_back();
+        }
+    }
+    if (!f.host_in && cudaMallocHost(&f.host_in, P * 5) != cudaSuccess) return FOS_ERR_OOM;
+    std::memcpy(f.host_in, rgb, P * 3);
+    std::memcpy(f.host_in + P * 3, depth, P * 2);
+    f.t_submit = now_us();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->streams[stream] || s->streams[stream]->closing) {
+            cudaFreeHost(f.host_in);
+            return FOS_ERR_INVALID_ARG;
+        }
+        s->streams[stream]->pending.push_back(f);
+    }
+    s->cv.notify_all();
+    return FOS_OK;
+}
+
+int32_t fos_server_poll(fos_server* s, fos_server_result* out, int32_t max_results)
+{
+    if (!s || !out || max_results < 1) return 0;
+    std::lock_guard<std::mutex> lk(s->mu);
+    int32_t n = 0;
+    while (n < max_results && !s->results.empty()) {
+        out[n++] = s->results.front();
+        s->results.pop_front();
+    }
+    return n;
+}
+
+fos_status fos_server_stats(fos_server* s, fos_server_stats_t* out)
+{
+    if (!s || !out) return FOS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->ticks = s->ticks;
+    out->frames_done = s->frames_done;
+    out->device_bytes_used = s->used;
+    int32_t active = 0, waiting = 0;
+    for (Stream* st : s->streams)
+        if (st) (st->slot >= 0 ? active : waiting) += 1;
+    out->streams_active = active;
+    out->streams_waiting = waiting;
+    out->busy_us = s->busy_us;
+    return s->stop && !s->err.empty() ? FOS_ERR_CUDA : FOS_OK;
+}
+
+}  // extern "C"

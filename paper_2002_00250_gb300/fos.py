@@ -76,6 +76,17 @@ class SoftParams(ctypes.Structure):
                 ("depth_full_scale_mm", ctypes.c_uint32)]
 
 
+class ServerResult(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_int32), ("status", ctypes.c_int32), ("tag", ctypes.c_int64),
+                ("latency_us", ctypes.c_double), ("queue_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("ticks", ctypes.c_int64), ("frames_done", ctypes.c_int64),
+                ("device_bytes_used", ctypes.c_size_t), ("streams_active", ctypes.c_int32),
+                ("streams_waiting", ctypes.c_int32), ("busy_us", ctypes.c_double)]
+
+
 class KernelTiming(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -116,6 +127,14 @@ SIGNATURES = {
     "fos_batch_process_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fos_batch_set_shape": (_st, [_vp, _i32, _i32, _i32]),
     "fos_batch_autotune": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(BatchTuning)]),
+    "fos_server_create": (_vp, [ctypes.POINTER(Params), ctypes.c_size_t, _i32]),
+    "fos_server_destroy": (None, [_vp]),
+    "fos_server_last_error": (ctypes.c_char_p, [_vp]),
+    "fos_server_open_stream": (_i32, [_vp, _i32, _i32, _u32]),
+    "fos_server_close_stream": (_st, [_vp, _i32]),
+    "fos_server_submit": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _i64]),
+    "fos_server_poll": (_i32, [_vp, ctypes.POINTER(ServerResult), _i32]),
+    "fos_server_stats": (_st, [_vp, ctypes.POINTER(ServerStats)]),
     "fos_softgmm_default_params": (None, [ctypes.POINTER(SoftParams)]),
     "fos_softgmm_create": (_vp, [_i32, _i32, _i32, _i32, ctypes.POINTER(SoftParams)]),
     "fos_softgmm_destroy": (None, [_vp]),
@@ -413,3 +432,54 @@ class Batch:
         if st != 0:
             raise FosError(st, self.lib.fos_last_error(c).decode())
         return buf
+
+
+class Server:
+    """Serving loop: admission by device-memory budget, continuous batching."""
+
+    def __init__(self, hbm_budget_bytes: int, max_streams: int, params: Params | None = None, **overrides):
+        self.lib = load()
+        self.params = params if params is not None else default_params(**overrides)
+        h = self.lib.fos_server_create(ctypes.byref(self.params), hbm_budget_bytes, max_streams)
+        if not h:
+            raise FosError(1, self.lib.fos_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fos_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open_stream(self, width: int, height: int, stream_id: int) -> int:
+        sid = self.lib.fos_server_open_stream(self.h, width, height, stream_id)
+        if sid < 0:
+            raise FosError(5, self.lib.fos_server_last_error(self.h).decode())
+        return sid
+
+    def close_stream(self, sid: int) -> None:
+        st = self.lib.fos_server_close_stream(self.h, sid)
+        if st != 0:
+            raise FosError(st, "close_stream")
+
+    def submit(self, sid: int, rgb: np.ndarray, depth: np.ndarray, mask_gmm, mask_pbas, tag: int) -> None:
+        st = self.lib.fos_server_submit(self.h, sid, _ptr(rgb), _ptr(depth), _ptr(mask_gmm), _ptr(mask_pbas), tag)
+        if st != 0:
+            raise FosError(st, self.lib.fos_server_last_error(self.h).decode())
+
+    def poll(self, max_results: int = 256):
+        arr = (ServerResult * max_results)()
+        n = self.lib.fos_server_poll(self.h, arr, max_results)
+        return [(arr[i].stream, arr[i].status, arr[i].tag, arr[i].latency_us, arr[i].queue_us) for i in range(n)]
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        st = self.lib.fos_server_stats(self.h, ctypes.byref(s))
+        d = {f: getattr(s, f) for f, _ in ServerStats._fields_}
+        d["ok"] = st == 0
+        return d

@@ -1,0 +1,130 @@
+"""Serving loop: admission by device-memory budget, continuous batching, and
+every stream's masks identical to processing that stream alone."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from _helpers import scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(W, H, sid, rgb, depth):
+    from paper_2002_00250_gb300 import fos
+    seg = fos.Segmenter(W, H, stream_id=sid)
+    return seg.process_host(rgb, depth)
+
+
+def test_served_results_equal_alone_with_join_leave_and_waiting():
+    from paper_2002_00250_gb300 import fos
+    sizes = [(136, 40), (64, 48), (256, 24), (96, 32), (128, 64)]
+    n = 10
+    data = [scene(W, H, n, seed=80 + i) for i, (W, H) in enumerate(sizes)]
+    p = fos.default_params()
+    need = [fos.load().fos_stream_device_bytes(W, H, p) + 2 * 7 * W * H for W, H in sizes]
+    # room for the first three streams only: the fourth waits until the
+    # second closes, the fifth until the third closes
+    budget = max(need[0] + need[1] + need[2], need[0] + need[3] + need[4]) + 4096
+    assert need[0] + need[1] + need[2] + min(need[3], need[4]) > budget
+    srv = fos.Server(budget, 8)
+    out = {}
+    sids = {}
+    sent = {i: 0 for i in range(len(sizes))}
+
+    def submit(i, f):
+        W, H = sizes[i]
+        rgb, depth, _ = data[i]
+        mg = np.empty((H, W), np.uint8)
+        mp = np.empty((H, W), np.uint8)
+        out[(i, f)] = (mg, mp)
+        srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 1000 + f)
+        sent[i] += 1
+
+    rng = np.random.default_rng(1)
+    for i in range(3):
+        sids[i] = srv.open_stream(*sizes[i], stream_id=200 + i)
+    for i in (3, 4):
+        sids[i] = srv.open_stream(*sizes[i], stream_id=200 + i)   # these wait for memory
+    # interleaved submission; stream 1 stops after 6 frames, stream 2 after 8
+    for step in range(n):
+        for i in rng.permutation(len(sizes)):
+            limit = {1: 6, 2: 8}.get(int(i), n)
+            if step < limit:
+                submit(int(i), step)
+        if step == 5:
+            srv.close_stream(sids[1])
+        if step == 7:
+            srv.close_stream(sids[2])
+        time.sleep(0.002 * rng.random())
+    total = sum(sent.values())
+    done = []
+    t0 = time.time()
+    while len(done) < total and time.time() - t0 < 60:
+        done += srv.poll()
+        time.sleep(0.001)
+    assert len(done) == total, (len(done), total, srv.stats())
+    assert all(r[1] == 0 for r in done)
+    # every stream's frames come back in order
+    for i in range(len(sizes)):
+        tags = [r[2] for r in done if r[2] // 1000 == i]
+        assert tags == sorted(tags)
+    for i, (W, H) in enumerate(sizes):
+        rgb, depth, _ = data[i]
+        k = sent[i]
+        mg, mp = _alone(W, H, 200 + i, rgb[:k], depth[:k])
+        for f in range(k):
+            np.testing.assert_array_equal(out[(i, f)][0], mg[f], err_msg=f"gmm s{i} f{f}")
+            np.testing.assert_array_equal(out[(i, f)][1], mp[f], err_msg=f"pbas s{i} f{f}")
+    st = srv.stats()
+    assert st["ok"] and st["frames_done"] == total
+    assert st["ticks"] < total  # frames were batched together
+    srv.close()
+
+
+def test_stream_larger_than_budget_is_refused():
+    from paper_2002_00250_gb300 import fos
+    srv = fos.Server(1 << 20, 4)
+    with pytest.raises(fos.FosError):
+        srv.open_stream(640, 480, 0)
+    srv.close()
+
+
+def test_concurrent_submitters():
+    from paper_2002_00250_gb300 import fos
+    sizes = [(64, 32)] * 6
+    n = 8
+    data = [scene(W, H, n, seed=90 + i) for i, (W, H) in enumerate(sizes)]
+    srv = fos.Server(1 << 34, 8)
+    sids = [srv.open_stream(W, H, stream_id=300 + i) for i, (W, H) in enumerate(sizes)]
+    outs = {}
+
+    def cam(i):
+        W, H = sizes[i]
+        rgb, depth, _ = data[i]
+        for f in range(n):
+            mg = np.empty((H, W), np.uint8)
+            mp = np.empty((H, W), np.uint8)
+            outs[(i, f)] = (mg, mp)
+            srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 100 + f)
+            time.sleep(0.001)
+
+    th = [threading.Thread(target=cam, args=(i,)) for i in range(len(sizes))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    done = []
+    t0 = time.time()
+    while len(done) < n * len(sizes) and time.time() - t0 < 60:
+        done += srv.poll()
+        time.sleep(0.001)
+    assert len(done) == n * len(sizes)
+    for i, (W, H) in enumerate(sizes):
+        rgb, depth, _ = data[i]
+        mg, mp = _alone(W, H, 300 + i, rgb, depth)
+        for f in range(n):
+            np.testing.assert_array_equal(outs[(i, f)][1], mp[f])
+            np.testing.assert_array_equal(outs[(i, f)][0], mg[f])
+    srv.close()
