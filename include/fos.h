@@ -55,7 +55,8 @@ typedef enum fos_status {
     FOS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
     FOS_ERR_BUDGET = 5,      /* admission refused: memory budget exceeded */
     FOS_ERR_STATE = 6,       /* call not valid in the context's current state */
-    FOS_ERR_UNSUPPORTED = 7  /* parameter combination not compiled in */
+    FOS_ERR_UNSUPPORTED = 7, /* parameter combination not compiled in */
+    FOS_ERR_BUSY = 8         /* queue full: the call took nothing, retry later */
 } fos_status;
 
 /*
@@ -312,7 +313,8 @@ fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
  * by a device-memory budget: each needs fos_stream_device_bytes plus two
  * input and two mask buffers; a stream that does not fit, or finds no free
  * slot, waits in FIFO order until others close.  fos_server_submit copies a
- * frame into pinned host memory and returns at once.  Each worker tick takes
+ * frame into one of the stream's queue_depth pinned input slots (allocated at
+ * admission) and returns at once.  Each worker tick takes
  * the oldest pending frame of every admitted stream (frames of one stream run
  * in order), runs them as one batched launch, and writes the masks into the
  * caller's buffers given at submit time; two ticks are in flight, so frames
@@ -336,9 +338,11 @@ typedef struct fos_server_stats_t {
     double busy_us;      /* sum over ticks of launch -> completion */
 } fos_server_stats_t;
 
-/* Server over one device-memory budget (bytes) and at most max_streams
- * admitted streams.  NULL on error (fos_last_error(NULL)). */
-fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes, int32_t max_streams);
+/* Server over one device-memory budget (bytes), at most max_streams admitted
+ * streams, and queue_depth (1..1024) queued-or-running frames per stream.
+ * NULL on error (fos_last_error(NULL)). */
+fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes, int32_t max_streams,
+                              int32_t queue_depth);
 /* Stops the worker (frames in flight complete; pending ones are dropped). */
 void fos_server_destroy(fos_server* s);
 const char* fos_server_last_error(const fos_server* s);
@@ -349,7 +353,10 @@ int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uin
 fos_status fos_server_close_stream(fos_server* s, int32_t stream);
 /* Queues one host frame of the stream (copied before returning).  The masks
  * (either may be NULL) are written when the frame completes: keep those
- * buffers valid until fos_server_poll reports the tag. */
+ * buffers valid until fos_server_poll reports the tag.  The frame is not
+ * taken (drop it or retry) with FOS_ERR_BUDGET while the stream still waits
+ * for admission, and with FOS_ERR_BUSY while it has queue_depth frames queued
+ * or running. */
 fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
                              uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag);
 /* Up to max_results completed frames, oldest first; returns how many. */

@@ -3,8 +3,9 @@
 // No counterpart in the paper (one camera there).  Streams are admitted by
 // an HBM budget: a stream needs its device-resident models plus two input and
 // two mask buffers; a stream that does not fit waits (FIFO) until others
-// leave.  fos_server_submit copies a frame into pinned host memory and
-// returns at once.  A worker thread runs ticks: each tick takes the oldest
+// leave.  fos_server_submit copies a frame into one of the stream's pinned
+// input slots (allocated once, at admission) and returns at once; with no
+// free slot, or before admission, it refuses the frame (backpressure).  A worker thread runs ticks: each tick takes the oldest
 // pending frame of every admitted stream (at most one per stream, so every
 // stream's frames run in order), copies them to the device, runs ONE batched
 // launch over all of them (fos_batch), and copies the masks back.  Two ticks
@@ -59,7 +60,9 @@ struct Stream {
     uint8_t* h_mg[2] = {nullptr, nullptr};     // pinned mask staging
     uint8_t* h_mp[2] = {nullptr, nullptr};
     int64_t nframes = 0;
-    std::vector<uint8_t*> free_in;               // reusable pinned input buffers
+    uint8_t* arena = nullptr;                    // pinned input slots, allocated at admission
+    int copying = 0;                             // submits writing into a slot right now
+    std::vector<uint8_t*> free_in;               // free slots of the arena
 };
 
 struct TickItem {
@@ -80,6 +83,7 @@ struct fos_server {
     fos_params prm{};
     size_t budget = 0, used = 0;
     int max_streams = 0;
+    int queue_depth = 16;             // pinned input slots per stream
     fos_batch* batch = nullptr;
     cudaStream_t cs = nullptr;
     int device = 0;
@@ -105,7 +109,8 @@ size_t stream_bytes(const fos_server* s, int32_t W, int32_t H)
 
 void free_stream_buffers(Stream* st)
 {
-    for (uint8_t* b : st->free_in) cudaFreeHost(b);
+    cudaFreeHost(st->arena);
+    st->arena = nullptr;
     st->free_in.clear();
     for (int k = 0; k < 2; ++k) {
         cudaFree(st->d_in[k]);
@@ -131,6 +136,11 @@ void admit(fos_server* s)
         if (slot < 0) break;  // no free slot yet
         const size_t P = size_t(st->W) * size_t(st->H);
         bool ok = true;
+        ok = cudaMallocHost(&st->arena, size_t(s->queue_depth) * (P * 5 + 16)) == cudaSuccess;
+        if (ok) {
+            st->free_in.clear();
+            for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(st->arena + size_t(q) * (P * 5 + 16));
+        }
         for (int k = 0; k < 2 && ok; ++k) {
             ok = cudaMalloc(&st->d_in[k], P * 5 + 16) == cudaSuccess &&
                  cudaMalloc(&st->d_mg[k], P + 16) == cudaSuccess &&
@@ -178,7 +188,7 @@ void retire(fos_server* s)
 {
     for (size_t h = 0; h < s->streams.size(); ++h) {
         Stream* st = s->streams[h];
-        if (!st || !st->closing || !st->pending.empty() || st->inflight > 0) continue;
+        if (!st || !st->closing || !st->pending.empty() || st->inflight > 0 || st->copying > 0) continue;
         if (st->slot >= 0) {
             fos_batch_remove_stream(s->batch, st->slot);
             s->used -= st->bytes;
@@ -269,7 +279,7 @@ void worker_main(fos_server* s)
                     r.status = e != cudaSuccess ? FOS_ERR_CUDA : bst;
                     s->results.push_back(r);
                     s->streams[it.stream]->inflight -= 1;
-                    cudaFreeHost(it.f.host_in);
+                    s->streams[it.stream]->free_in.push_back(it.f.host_in);
                 }
                 if (t.done) cudaEventDestroy(t.done);
                 break;
@@ -291,7 +301,7 @@ void worker_main(fos_server* s)
         if (!inflight.empty() && t.items.empty()) {
             // nothing new to launch: wait for the oldest tick or a new frame
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait_for(lk, std::chrono::microseconds(200));
+            s->cv.wait_for(lk, std::chrono::microseconds(50));
         }
     }
     for (Tick& t : inflight) {
@@ -305,10 +315,12 @@ void worker_main(fos_server* s)
 
 extern "C" {
 
-fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes, int32_t max_streams)
+fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes, int32_t max_streams,
+                              int32_t queue_depth)
 {
     std::string why;
-    if (ctx_validate_params(params, why) != FOS_OK || max_streams < 1 || hbm_budget_bytes == 0) {
+    if (ctx_validate_params(params, why) != FOS_OK || max_streams < 1 || hbm_budget_bytes == 0 ||
+        queue_depth < 1 || queue_depth > 1024) {
         set_thread_error(why.empty() ? "fos_server_create: bad arguments" : why.c_str());
         return nullptr;
     }
@@ -316,6 +328,7 @@ fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes,
     s->prm = *params;
     s->budget = hbm_budget_bytes;
     s->max_streams = max_streams;
+    s->queue_depth = queue_depth;
     cudaGetDevice(&s->device);
     s->batch = fos_batch_create(max_streams, params);
     if (!s->batch || cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess) {
@@ -338,7 +351,6 @@ void fos_server_destroy(fos_server* s)
     if (s->worker.joinable()) s->worker.join();
     for (Stream* st : s->streams) {
         if (!st) continue;
-        for (Frame& f : st->pending) cudaFreeHost(f.host_in);
         free_stream_buffers(st);
         delete st;
     }
@@ -384,38 +396,32 @@ fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, 
                              uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag)
 {
     if (!s || !rgb || !depth) return FOS_ERR_INVALID_ARG;
+    Frame f{};
+    f.tag = tag;
+    f.out_gmm = mask_gmm;
+    f.out_pbas = mask_pbas;
     size_t P;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream] || s->streams[stream]->closing)
             return FOS_ERR_INVALID_ARG;
         if (s->stop) return FOS_ERR_STATE;
-        P = size_t(s->streams[stream]->W) * size_t(s->streams[stream]->H);
+        Stream* st = s->streams[stream];
+        if (st->slot < 0) return FOS_ERR_BUDGET;        // still waiting for admission
+        if (st->free_in.empty()) return FOS_ERR_BUSY;    // queue full
+        f.host_in = st->free_in.back();
+        st->free_in.pop_back();
+        st->copying += 1;
+        P = size_t(st->W) * size_t(st->H);
     }
-    Frame f{};
-    f.tag = tag;
-    f.out_gmm = mask_gmm;
-    f.out_pbas = mask_pbas;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        if (!s->streams[stream]) return FOS_ERR_INVALID_ARG;
-        std::vector<uint8_t*>& pool = s->streams[stream]->free_in;
-        if (!pool.empty()) {
-            f.host_in = pool.back();
-            pool.pop_back();
-        }
-    }
-    if (!f.host_in && cudaMallocHost(&f.host_in, P * 5) != cudaSuccess) return FOS_ERR_OOM;
+    // the slot belongs to this call until it is queued
     std::memcpy(f.host_in, rgb, P * 3);
     std::memcpy(f.host_in + P * 3, depth, P * 2);
     f.t_submit = now_us();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (!s->streams[stream] || s->streams[stream]->closing) {
-            cudaFreeHost(f.host_in);
-            return FOS_ERR_INVALID_ARG;
-        }
         s->streams[stream]->pending.push_back(f);
+        s->streams[stream]->copying -= 1;
     }
     s->cv.notify_all();
     return FOS_OK;

@@ -8,6 +8,7 @@ raises.  Device tensors are torch CUDA tensors; streams are torch streams.
 from __future__ import annotations
 
 import ctypes
+import time
 import os
 from dataclasses import dataclass
 
@@ -21,7 +22,8 @@ METHOD_PBAS = 2
 KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_FLUSH, KERNEL_INIT, KERNEL_FUSED = 0, 1, 2, 3, 4
 KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_flush", "init", "fused_classify")
 STATUS = {0: "FOS_OK", 1: "FOS_ERR_INVALID_ARG", 2: "FOS_ERR_CUDA", 3: "FOS_ERR_OOM",
-          4: "FOS_ERR_TIMEOUT", 5: "FOS_ERR_BUDGET", 6: "FOS_ERR_STATE", 7: "FOS_ERR_UNSUPPORTED"}
+          4: "FOS_ERR_TIMEOUT", 5: "FOS_ERR_BUDGET", 6: "FOS_ERR_STATE", 7: "FOS_ERR_UNSUPPORTED",
+          8: "FOS_ERR_BUSY"}
 
 
 class FosError(RuntimeError):
@@ -127,7 +129,7 @@ SIGNATURES = {
     "fos_batch_process_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "fos_batch_set_shape": (_st, [_vp, _i32, _i32, _i32]),
     "fos_batch_autotune": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(BatchTuning)]),
-    "fos_server_create": (_vp, [ctypes.POINTER(Params), ctypes.c_size_t, _i32]),
+    "fos_server_create": (_vp, [ctypes.POINTER(Params), ctypes.c_size_t, _i32, _i32]),
     "fos_server_destroy": (None, [_vp]),
     "fos_server_last_error": (ctypes.c_char_p, [_vp]),
     "fos_server_open_stream": (_i32, [_vp, _i32, _i32, _u32]),
@@ -437,10 +439,11 @@ class Batch:
 class Server:
     """Serving loop: admission by device-memory budget, continuous batching."""
 
-    def __init__(self, hbm_budget_bytes: int, max_streams: int, params: Params | None = None, **overrides):
+    def __init__(self, hbm_budget_bytes: int, max_streams: int, queue_depth: int = 16,
+                 params: Params | None = None, **overrides):
         self.lib = load()
         self.params = params if params is not None else default_params(**overrides)
-        h = self.lib.fos_server_create(ctypes.byref(self.params), hbm_budget_bytes, max_streams)
+        h = self.lib.fos_server_create(ctypes.byref(self.params), hbm_budget_bytes, max_streams, queue_depth)
         if not h:
             raise FosError(1, self.lib.fos_last_error(None).decode())
         self.h = h
@@ -467,10 +470,24 @@ class Server:
         if st != 0:
             raise FosError(st, "close_stream")
 
-    def submit(self, sid: int, rgb: np.ndarray, depth: np.ndarray, mask_gmm, mask_pbas, tag: int) -> None:
-        st = self.lib.fos_server_submit(self.h, sid, _ptr(rgb), _ptr(depth), _ptr(mask_gmm), _ptr(mask_pbas), tag)
-        if st != 0:
-            raise FosError(st, self.lib.fos_server_last_error(self.h).decode())
+    def submit(self, sid: int, rgb: np.ndarray, depth: np.ndarray, mask_gmm, mask_pbas, tag: int,
+               wait: float = 0.0) -> bool:
+        """True if queued.  False if refused for longer than ``wait`` seconds;
+        ``self.refusal`` then says why: "waiting" (stream not admitted yet) or
+        "full" (its queue is full)."""
+        deadline = time.monotonic() + wait
+        while True:
+            st = self.lib.fos_server_submit(self.h, sid, _ptr(rgb), _ptr(depth), _ptr(mask_gmm),
+                                            _ptr(mask_pbas), tag)
+            if st == 0:
+                self.refusal = None
+                return True
+            if st not in (5, 8):
+                raise FosError(st, self.lib.fos_server_last_error(self.h).decode())
+            self.refusal = "waiting" if st == 5 else "full"
+            if time.monotonic() >= deadline:
+                return False
+            time.sleep(0.0002)
 
     def poll(self, max_results: int = 256):
         arr = (ServerResult * max_results)()

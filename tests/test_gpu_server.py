@@ -32,15 +32,25 @@ def test_served_results_equal_alone_with_join_leave_and_waiting():
     out = {}
     sids = {}
     sent = {i: 0 for i in range(len(sizes))}
+    backlog = {i: [] for i in range(len(sizes))}   # frames the server refused so far
 
-    def submit(i, f):
+    def drain(i):
+        # in order; a refused frame (stream still waiting for memory) stays queued here
         W, H = sizes[i]
         rgb, depth, _ = data[i]
-        mg = np.empty((H, W), np.uint8)
-        mp = np.empty((H, W), np.uint8)
-        out[(i, f)] = (mg, mp)
-        srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 1000 + f)
-        sent[i] += 1
+        while backlog[i]:
+            f = backlog[i][0]
+            mg = np.empty((H, W), np.uint8)
+            mp = np.empty((H, W), np.uint8)
+            if not srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 1000 + f):
+                return
+            out[(i, f)] = (mg, mp)
+            backlog[i].pop(0)
+            sent[i] += 1
+
+    def submit(i, f):
+        backlog[i].append(f)
+        drain(i)
 
     rng = np.random.default_rng(1)
     for i in range(3):
@@ -58,10 +68,12 @@ def test_served_results_equal_alone_with_join_leave_and_waiting():
         if step == 7:
             srv.close_stream(sids[2])
         time.sleep(0.002 * rng.random())
-    total = sum(sent.values())
+    total = sum(sent.values()) + sum(len(b) for b in backlog.values())
     done = []
     t0 = time.time()
     while len(done) < total and time.time() - t0 < 60:
+        for i in backlog:
+            drain(i)
         done += srv.poll()
         time.sleep(0.001)
     assert len(done) == total, (len(done), total, srv.stats())
@@ -80,6 +92,63 @@ def test_served_results_equal_alone_with_join_leave_and_waiting():
     st = srv.stats()
     assert st["ok"] and st["frames_done"] == total
     assert st["ticks"] < total  # frames were batched together
+    srv.close()
+
+
+def test_full_queue_refuses_frames():
+    from paper_2002_00250_gb300 import fos
+    W, H, n = 64, 32, 12
+    rgb, depth, _ = scene(W, H, n, seed=95)
+    srv = fos.Server(1 << 34, 2, queue_depth=3)
+    sid = srv.open_stream(W, H, stream_id=400)
+    outs = [(np.empty((H, W), np.uint8), np.empty((H, W), np.uint8)) for _ in range(n)]
+    taken, refused = [], 0
+    for f in range(n):
+        # waits only for admission (first frame), never for a free slot
+        if srv.submit(sid, rgb[f], depth[f], *outs[f], tag=f, wait=30.0 if f == 0 else 0.0):
+            taken.append(f)
+        else:
+            refused += 1
+    done = []
+    t0 = time.time()
+    while len(done) < len(taken) and time.time() - t0 < 60:
+        done += srv.poll()
+        time.sleep(0.001)
+    assert [r[2] for r in done] == taken
+    assert len(taken) >= 3
+    # with every slot free again, a frame is taken at once
+    mg, mp = np.empty((H, W), np.uint8), np.empty((H, W), np.uint8)
+    assert srv.submit(sid, rgb[0], depth[0], mg, mp, tag=99)
+    srv.close()
+    # the refusals are the only difference from a lone stream fed the taken frames
+    ref_g, ref_p = _alone(W, H, 400, rgb[taken], depth[taken])
+    for k, f in enumerate(taken):
+        np.testing.assert_array_equal(outs[f][1], ref_p[k])
+        np.testing.assert_array_equal(outs[f][0], ref_g[k])
+    assert refused + len(taken) == n
+
+
+def test_waiting_stream_refuses_frames_until_admitted():
+    from paper_2002_00250_gb300 import fos
+    W, H = 64, 32
+    rgb, depth, _ = scene(W, H, 2, seed=96)
+    need = fos.load().fos_stream_device_bytes(W, H, fos.default_params()) + 2 * 7 * W * H
+    srv = fos.Server(need + need // 2, 4, queue_depth=2)   # room for one stream
+    a = srv.open_stream(W, H, stream_id=1)
+    b = srv.open_stream(W, H, stream_id=2)
+    m = [np.empty((H, W), np.uint8) for _ in range(4)]
+    assert srv.submit(a, rgb[0], depth[0], m[0], m[1], tag=0, wait=30.0)
+    assert not srv.submit(b, rgb[0], depth[0], m[2], m[3], tag=1)
+    assert srv.stats()["streams_waiting"] == 1
+    srv.close_stream(a)
+    assert srv.submit(b, rgb[0], depth[0], m[2], m[3], tag=1, wait=30.0)
+    done = []
+    t0 = time.time()
+    while len(done) < 2 and time.time() - t0 < 60:
+        done += srv.poll()
+        time.sleep(0.001)
+    assert sorted(r[2] for r in done) == [0, 1]
+    np.testing.assert_array_equal(m[0], m[2])   # same data, same first-frame result
     srv.close()
 
 
@@ -107,7 +176,7 @@ def test_concurrent_submitters():
             mg = np.empty((H, W), np.uint8)
             mp = np.empty((H, W), np.uint8)
             outs[(i, f)] = (mg, mp)
-            srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 100 + f)
+            assert srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 100 + f, wait=30.0)
             time.sleep(0.001)
 
     th = [threading.Thread(target=cam, args=(i,)) for i in range(len(sizes))]
