@@ -289,6 +289,29 @@ __device__ __forceinline__ void gmm_tile_part(const GmmArgs& g, const PbasArgs& 
     }
 }
 
+// L1 prefetch of the 128-byte line holding p (a hint: no result, no fault
+// semantics are relied on; every address passed is inside its buffer).
+__device__ __forceinline__ void prefetch_l1(const void* p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Prefetch of what channel c of this thread's pixels reads first: its N
+// sample slots and R, T, S.  Issued one channel ahead, so the loads of the
+// next channel find their lines in L1 (the kernel is latency-bound; deeper
+// prefetch evicts lines before use).
+template <int NT>
+__device__ __forceinline__ void prefetch_channel(const PbasArgs& a, int N, int c, int x, int y, int64_t q0)
+{
+    const uint16_t* sb = a.samp + sidx(a, N, c, 0, x, y);
+#pragma unroll(NT > 0 ? NT : 4)
+    for (int k = 0; k < N; ++k) prefetch_l1(sb + int64_t(k) * kSeg);
+    const int64_t pc = int64_t(c) * a.plane + q0;
+    prefetch_l1(a.R + pc);
+    prefetch_l1(a.T + pc);
+    prefetch_l1(a.S + pc);
+}
+
 // Shared memory of one classify tile.
 template <int PX, int TY>
 struct ClassifySmem {
@@ -311,6 +334,10 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
     uint32_t* sreq = S.sreq;
     const int N = NT > 0 ? NT : a.N;
     const int tid = threadIdx.y * 32 + threadIdx.x;
+    {
+        const int px = x0 + int(threadIdx.x) * PX, py = y0 + int(threadIdx.y);
+        if (py < a.H && px < a.W) prefetch_channel<NT>(a, N, 0, px, py, int64_t(py) * a.Wp + px);
+    }
     stage_input<PX, TY>(a, x0, y0, sm);
     if (a.apply) stage_requests<PX, TY>(a, x0, y0, sreq);
     if (build_table && tid < 4) {
@@ -422,6 +449,7 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
                 Sv[i] = inb[i] ? a.S[pc + i] : 0u;
             }
         }
+        if (c < 3 && inb[0]) prefetch_channel<NT>(a, N, c + 1, x, y, q0);
 
         // distances to the N samples: count within R, minimum.
         // dist = fl(fl(wg * |dg|) + |dv|): the product comes from the table.
