@@ -289,6 +289,7 @@ fos_status fos_batch_process_device(fos_batch* b, int32_t n, const int32_t* slot
     hdr[0] = n;
     hdr[1] = ptiles;
     hdr[2] = gblocks;
+    hdr[3] = 0;  // tile counter of the PBAS kernel (copied in with the arguments)
     FOS_BTRY(b, cudaGraphLaunch(b->graph[k], s));
     FOS_BTRY(b, cudaEventRecord(b->done[k], s));
     b->used[k] = true;

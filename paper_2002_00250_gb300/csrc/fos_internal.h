@@ -111,9 +111,10 @@ struct PbasBatchEntry {
     int init;      // 1: frame 0 of this stream
     int pad;
 };
-// Persistent batched PBAS launch over hdr[0] entries and hdr[1] tiles; with
+// Persistent batched PBAS launch over hdr[0] entries and hdr[1] tiles; hdr[3]
+// is the tile counter the blocks claim from (must be zero at launch).  With
 // G non-NULL (3+3-component GMM) each tile also runs the GMM of its pixels.
-LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr,
+LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, int* hdr,
                                int blocks, int N, int px, int ty, cudaStream_t s);
 int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused);
 

@@ -682,26 +682,29 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
 
 // Many streams in one persistent launch.  Entry i of the batch holds stream
 // i's arguments, whether it is at frame 0, its tile offset in the launch
-// (prefix sum) and its tiles per row; blocks walk the launch's tiles with a
-// grid stride.  The count of entries and tiles is read from device memory, so
-// one captured graph serves any batch composition.
+// (prefix sum) and its tiles per row.  Blocks claim tiles one at a time from
+// a counter (hdr[3], zero at launch) in launch order, so the hardware keeps
+// every block busy whatever the mix of stream sizes and tile costs.  The
+// count of entries and tiles is read from device memory, so one captured
+// graph serves any batch composition.
 template <int NT, int PX, int TY, int KR>
 __global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
 pbas_batch_kernel(const PbasBatchEntry* __restrict__ E, const GmmBatchEntry* __restrict__ GE,
-                  const int* __restrict__ hdr)
+                  int* __restrict__ hdr)
 {
     constexpr int KD = KR;
     __shared__ ClassifySmem<PX, TY> S;
     __shared__ __align__(16) PbasArgs sa;
     __shared__ __align__(16) GmmArgs sg;
+    __shared__ int s_it;
     const int n = hdr[0], total = hdr[1];
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    // each block takes a contiguous run of tiles, so consecutive tiles mostly
-    // belong to the same stream (arguments and weight table are reused)
-    const int chunk = (total + int(gridDim.x) - 1) / int(gridDim.x);
-    const int it0 = int(blockIdx.x) * chunk, it1 = min(total, it0 + chunk);
-    int cur = -1;
-    for (int it = it0; it < it1; ++it) {
+    int cur = -1;  // entry whose arguments (and weight table) are loaded
+    for (;;) {
+        if (tid == 0) s_it = atomicAdd(&hdr[3], 1);
+        __syncthreads();
+        const int it = s_it;
+        if (it >= total) break;
         int lo = 0, hi = n - 1;  // entry whose tile range holds `it`
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -800,7 +803,7 @@ LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStre
 }
 
 template <int NT, int KR>
-bool batch_shape(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr, int blocks, int px,
+bool batch_shape(const PbasBatchEntry* E, const GmmBatchEntry* G, int* hdr, int blocks, int px,
                  int ty, cudaStream_t s)
 {
     if (px == 2 && ty == 8) pbas_batch_kernel<NT, 2, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
@@ -812,7 +815,7 @@ bool batch_shape(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr
     return true;
 }
 
-LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, const int* hdr,
+LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, int* hdr,
                                int blocks, int N, int px, int ty, cudaStream_t s)
 {
     bool ok;
