@@ -482,6 +482,89 @@ def run_softgmm(args):
     print(json.dumps(out), flush=True)
 
 
+def run_table(args):
+    """Per-method rows (GMM alone, PBAS alone) at 640x480x50 and 1280x720x300:
+    device throughput with the method's own kernel timed by CUDA events, its
+    roofline fraction, host-path latency (fos_process_frame, pinned host
+    buffers) and the oracle of that method on 1 host core and on all cores.
+    Not the headline (that is the default workload, both methods fused)."""
+    import torch
+    import oracle
+    from paper_2002_00250_gb300 import fos, synth
+    peak, peak_src = _peaks()
+    dev = torch.device("cuda", 0)
+    oracle.build()
+    rows = []
+    for (w, h, n) in ((640, 480, 50), (1280, 720, 300)):
+        cfg = synth.SceneConfig(w, h, n, seed=0, n_camouflage=2 if w >= 1280 else 0,
+                                illumination_ramp=w >= 1280, shadows=w >= 1280)
+        sc = synth.RGBDScene(cfg, device=dev)
+        rgb, depth, _ = sc.sequence(0, n)
+        host = [(synth.to_numpy(rgb[t]), synth.to_numpy(depth[t])) for t in range(min(n, 9))]
+        for name, methods, kern in (("GMM", fos.METHOD_GMM, "gmm_step"),
+                                    ("PBAS", fos.METHOD_PBAS, "pbas_classify")):
+            seg = fos.Segmenter(w, h, methods=methods)
+            mg = torch.empty((n, h, w), dtype=torch.uint8, device=dev) if name == "GMM" else None
+            mp = torch.empty((n, h, w), dtype=torch.uint8, device=dev) if name == "PBAS" else None
+            for _ in range(args.warmup):
+                seg.reset()
+                seg.process_device(rgb, depth, mg, mp)
+            torch.cuda.synchronize()
+            seg.get_timing()
+            seg.get_counters()
+            seg.set_timing(1 << (fos.KERNEL_GMM if name == "GMM" else fos.KERNEL_PBAS_CLASSIFY))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                seg.reset()
+                seg.process_device(rgb, depth, mg, mp)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            tm = seg.get_timing()[kern]
+            cnt = seg.get_counters()
+            seg.set_timing(0)
+            avg_us = tm[1] / max(1, tm[0]) * 1e3
+            algo = ALGO_BYTES[kern] * w * h
+            if name == "PBAS":
+                fr = max(1, cnt["frames"])
+                algo += (SPARSE_OWN * cnt["own_updates"] + SPARSE_NEIGH * cnt["neighbour_writes"]) / fr
+            gbs = algo / (avg_us * 1e-6) / 1e9
+            # host path latency: one frame at a time from pinned host memory
+            seg.reset()
+            r0 = torch.from_numpy(host[0][0]).pin_memory().numpy()
+            d0 = torch.from_numpy(host[0][1]).pin_memory().numpy()
+            out = torch.empty((h, w), dtype=torch.uint8).pin_memory().numpy()
+            lat = []
+            for t in range(60):
+                t0 = time.perf_counter()
+                seg.process_frame(r0 if t % 2 == 0 else host[1][0], d0 if t % 2 == 0 else host[1][1], out)
+                lat.append((time.perf_counter() - t0) * 1e3)
+            seg.close()
+            # oracle of this method on 1 core and on all cores (bootstrap + 8 frames)
+            cpu = {}
+            for threads in (1, os.cpu_count()):
+                o = oracle.GMM(w, h, nthreads=threads) if name == "GMM" else oracle.PBAS(w, h, nthreads=threads)
+                o.step(*host[0])
+                nf = len(host) - 1 if threads > 1 else 2
+                t0 = time.perf_counter()
+                for t in range(1, nf + 1):
+                    o.step(*host[t])
+                cpu[str(threads)] = round(nf * w * h / (time.perf_counter() - t0) / 1e6, 3)
+            rows.append({"config": f"{w}x{h}x{n}", "method": name,
+                         "mpx_frames_per_s": round(w * h * n / (ms * 1e-3) / 1e6, 1),
+                         "kernel": kern, "kernel_avg_us": round(avg_us, 2),
+                         "roofline": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                                      "frac": round(gbs / peak, 3), "peak_source": peak_src,
+                                      "algo_bytes_per_launch": round(algo)},
+                         "latency_ms": {"p50": round(float(np.percentile(lat[10:], 50)), 3),
+                                        "p99": round(float(np.percentile(lat[10:], 99)), 3),
+                                        "path": "fos_process_frame, host buffers"},
+                         "cpu_oracle_mpx_frames_per_s": {"cores_" + k: v for k, v in cpu.items()}})
+    print(json.dumps({"metric": "per-method table", "unit": "Mpixel-frames/s", "steps": args.steps,
+                      "warmup": args.warmup, "data": "synthetic", "rows": rows}), flush=True)
+
+
 def run_serve32(args):
     """Serving loop: 32 camera streams of mixed resolutions arriving at 30 fps
     with +/-5 ms jitter (truncated Poisson offsets), staggered joins, some
@@ -489,7 +572,8 @@ def run_serve32(args):
     demand (late joiners wait until others leave), 10,000 frames.  A camera
     whose stream is not admitted yet drops its frame (counted).  Reports
     p50/p99 latency (submit -> masks in host memory) and throughput; a second
-    pass submits as fast as the queues take frames (backpressure)."""
+    pass submits as fast as the queues take frames (backpressure), zero-copy
+    from pinned camera buffers."""
     import threading
     import torch
     from paper_2002_00250_gb300 import fos, synth
@@ -499,11 +583,14 @@ def run_serve32(args):
     sizes = [choices[i] for i in rs.integers(0, len(choices), size=32)]
     pool_n = 8
     dev = torch.device("cuda", 0)
-    pools = []
+    pools, pinned = [], []
     for s_id, (w, h) in enumerate(sizes):
         sc = synth.RGBDScene(synth.config_stream(w, h, pool_n, seed=0, stream_id=s_id), device=dev)
         r, d, _ = sc.sequence(0, pool_n)
         pools.append((synth.to_numpy(r), synth.to_numpy(d)))
+        # camera buffers in pinned memory for the zero-copy pass
+        pr, pd = r.cpu().pin_memory(), d.cpu().pin_memory()
+        pinned.append((pr, pd, pr.numpy(), pd.numpy()))
     p = fos.default_params()
     lib = fos.load()
     need = [lib.fos_stream_device_bytes(w, h, p) + 14 * w * h for w, h in sizes]
@@ -570,10 +657,15 @@ def run_serve32(args):
             mg = np.empty((h, w), np.uint8)
             mp = np.empty((h, w), np.uint8)
             outs[tag] = (mg, mp)
-            r, d = pools[s_id]
-            ok = srv.submit(sids[s_id], r[k % pool_n], d[k % pool_n], mg, mp, tag)
-            if not ok and not paced and srv.refusal == "full":
-                ok = srv.submit(sids[s_id], r[k % pool_n], d[k % pool_n], mg, mp, tag, wait=30.0)
+            if paced:  # a camera callback: copy the frame and return
+                r, d = pools[s_id]
+                ok = srv.submit(sids[s_id], r[k % pool_n], d[k % pool_n], mg, mp, tag)
+            else:      # frames already in pinned buffers: zero-copy, wait while the queue is full
+                r, d = pinned[s_id][2], pinned[s_id][3]
+                ok = srv.submit(sids[s_id], r[k % pool_n], d[k % pool_n], mg, mp, tag, copy=False)
+                if not ok and srv.refusal == "full":
+                    ok = srv.submit(sids[s_id], r[k % pool_n], d[k % pool_n], mg, mp, tag, wait=30.0,
+                                    copy=False)
             if ok:
                 taken_px += w * h
             else:
@@ -624,7 +716,7 @@ def main():
                     help="frames per step (a shorter sequence for profiler captures)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run the device-resident steps only (for profiler captures)")
-    ap.add_argument("--workload", default="720p", choices=["720p", "batch16", "softgmm", "serve32"],
+    ap.add_argument("--workload", default="720p", choices=["720p", "batch16", "softgmm", "serve32", "table"],
                     help="720p: the headline single-stream sequence; batch16: 16 mixed streams")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -635,6 +727,8 @@ def main():
         run_softgmm(args)
     elif args.workload == "serve32":
         run_serve32(args)
+    elif args.workload == "table":
+        run_table(args)
     else:
         run_ours(args)
 

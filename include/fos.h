@@ -359,6 +359,16 @@ fos_status fos_server_close_stream(fos_server* s, int32_t stream);
  * or running. */
 fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
                              uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag);
+
+/* Zero-copy variant of fos_server_submit: the frame is not copied; the
+ * server reads rgb (H*W*3) and depth (H*W) straight from the caller's buffers
+ * when the frame's tick runs, so they must stay valid and unchanged until
+ * fos_server_poll reports the tag.  Pinned buffers (cudaHostAlloc /
+ * cudaHostRegister) are copied by DMA; pageable ones work but are staged by
+ * the driver.  Same refusals (FOS_ERR_BUDGET, FOS_ERR_BUSY) as
+ * fos_server_submit; frames of both kinds share the stream's queue_depth. */
+fos_status fos_server_submit_nocopy(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
+                                    uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag);
 /* Up to max_results completed frames, oldest first; returns how many. */
 int32_t fos_server_poll(fos_server* s, fos_server_result* out, int32_t max_results);
 /* Counters; FOS_ERR_CUDA once the worker has stopped on an error. */

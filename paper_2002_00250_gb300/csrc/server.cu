@@ -39,11 +39,18 @@ double now_us()
 
 struct Frame {
     int64_t tag;
-    uint8_t* host_in;    // pinned: rgb (P*3) then depth (P*2)
+    uint8_t* host_in;    // pinned slot: rgb (P*3), depth (P*2) at depth_offset(P); or NULL
+    const uint8_t* ext_rgb;     // caller's buffers (zero-copy submit) when host_in is NULL
+    const uint16_t* ext_depth;
     uint8_t* out_gmm;    // caller's buffers (nullable per method)
     uint8_t* out_pbas;
     double t_submit;
 };
+
+// Byte offset of the depth plane in an input buffer (host slot or device):
+// 16-byte aligned whatever the pixel count.
+size_t depth_offset(size_t P) { return (P * 3 + 15) / 16 * 16; }
+size_t input_bytes(size_t P) { return depth_offset(P) + P * 2; }
 
 struct Stream {
     int id;              // server handle
@@ -104,7 +111,7 @@ namespace {
 size_t stream_bytes(const fos_server* s, int32_t W, int32_t H)
 {
     const size_t P = size_t(W) * size_t(H);
-    return fos_stream_device_bytes(W, H, &s->prm) + 2 * (P * 5 + 2 * P);
+    return fos_stream_device_bytes(W, H, &s->prm) + 2 * (input_bytes(P) + 2 * P);
 }
 
 void free_stream_buffers(Stream* st)
@@ -136,13 +143,14 @@ void admit(fos_server* s)
         if (slot < 0) break;  // no free slot yet
         const size_t P = size_t(st->W) * size_t(st->H);
         bool ok = true;
-        ok = cudaMallocHost(&st->arena, size_t(s->queue_depth) * (P * 5 + 16)) == cudaSuccess;
+        const size_t slot_bytes = (input_bytes(P) + 15) / 16 * 16;
+        ok = cudaMallocHost(&st->arena, size_t(s->queue_depth) * slot_bytes) == cudaSuccess;
         if (ok) {
             st->free_in.clear();
-            for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(st->arena + size_t(q) * (P * 5 + 16));
+            for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(st->arena + size_t(q) * slot_bytes);
         }
         for (int k = 0; k < 2 && ok; ++k) {
-            ok = cudaMalloc(&st->d_in[k], P * 5 + 16) == cudaSuccess &&
+            ok = cudaMalloc(&st->d_in[k], input_bytes(P)) == cudaSuccess &&
                  cudaMalloc(&st->d_mg[k], P + 16) == cudaSuccess &&
                  cudaMalloc(&st->d_mp[k], P + 16) == cudaSuccess &&
                  cudaMallocHost(&st->h_mg[k], P + 16) == cudaSuccess &&
@@ -168,7 +176,7 @@ void publish(fos_server* s, Tick& t)
         const size_t P = size_t(st->W) * size_t(st->H);
         if (it.f.out_gmm) std::memcpy(it.f.out_gmm, st->h_mg[it.parity], P);
         if (it.f.out_pbas) std::memcpy(it.f.out_pbas, st->h_mp[it.parity], P);
-        st->free_in.push_back(it.f.host_in);
+        if (it.f.host_in) st->free_in.push_back(it.f.host_in);
         fos_server_result r{};
         r.stream = it.stream;
         r.tag = it.f.tag;
@@ -245,11 +253,19 @@ void worker_main(fos_server* s)
             for (TickItem& it : t.items) {
                 Stream* st = s->streams[it.stream];
                 const size_t P = size_t(st->W) * size_t(st->H);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(st->d_in[it.parity], it.f.host_in, P * 5, cudaMemcpyHostToDevice, s->cs);
+                const size_t od = depth_offset(P);
+                if (it.f.host_in) {  // one copy of the packed slot
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.host_in, od + P * 2, cudaMemcpyHostToDevice, s->cs);
+                } else {             // zero-copy submit: straight from the caller's buffers
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.ext_rgb, P * 3, cudaMemcpyHostToDevice, s->cs);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(st->d_in[it.parity] + od, it.f.ext_depth, P * 2, cudaMemcpyHostToDevice, s->cs);
+                }
                 slots.push_back(st->slot);
                 rgb.push_back(st->d_in[it.parity]);
-                dep.push_back(reinterpret_cast<const uint16_t*>(st->d_in[it.parity] + P * 3));
+                dep.push_back(reinterpret_cast<const uint16_t*>(st->d_in[it.parity] + od));
                 mg.push_back(st->d_mg[it.parity]);
                 mp.push_back(st->d_mp[it.parity]);
             }
@@ -279,7 +295,7 @@ void worker_main(fos_server* s)
                     r.status = e != cudaSuccess ? FOS_ERR_CUDA : bst;
                     s->results.push_back(r);
                     s->streams[it.stream]->inflight -= 1;
-                    s->streams[it.stream]->free_in.push_back(it.f.host_in);
+                    if (it.f.host_in) s->streams[it.stream]->free_in.push_back(it.f.host_in);
                 }
                 if (t.done) cudaEventDestroy(t.done);
                 break;
@@ -408,7 +424,8 @@ fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, 
         if (s->stop) return FOS_ERR_STATE;
         Stream* st = s->streams[stream];
         if (st->slot < 0) return FOS_ERR_BUDGET;        // still waiting for admission
-        if (st->free_in.empty()) return FOS_ERR_BUSY;    // queue full
+        if (int(st->pending.size()) + st->inflight + st->copying >= s->queue_depth || st->free_in.empty())
+            return FOS_ERR_BUSY;  // queue full
         f.host_in = st->free_in.back();
         st->free_in.pop_back();
         st->copying += 1;
@@ -416,12 +433,37 @@ fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, 
     }
     // the slot belongs to this call until it is queued
     std::memcpy(f.host_in, rgb, P * 3);
-    std::memcpy(f.host_in + P * 3, depth, P * 2);
+    std::memcpy(f.host_in + depth_offset(P), depth, P * 2);
     f.t_submit = now_us();
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->streams[stream]->pending.push_back(f);
         s->streams[stream]->copying -= 1;
+    }
+    s->cv.notify_all();
+    return FOS_OK;
+}
+
+fos_status fos_server_submit_nocopy(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
+                                    uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag)
+{
+    if (!s || !rgb || !depth) return FOS_ERR_INVALID_ARG;
+    Frame f{};
+    f.tag = tag;
+    f.ext_rgb = rgb;
+    f.ext_depth = depth;
+    f.out_gmm = mask_gmm;
+    f.out_pbas = mask_pbas;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream] || s->streams[stream]->closing)
+            return FOS_ERR_INVALID_ARG;
+        if (s->stop) return FOS_ERR_STATE;
+        Stream* st = s->streams[stream];
+        if (st->slot < 0) return FOS_ERR_BUDGET;  // still waiting for admission
+        if (int(st->pending.size()) + st->inflight + st->copying >= s->queue_depth) return FOS_ERR_BUSY;
+        f.t_submit = now_us();
+        st->pending.push_back(f);
     }
     s->cv.notify_all();
     return FOS_OK;

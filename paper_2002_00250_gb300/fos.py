@@ -135,6 +135,7 @@ SIGNATURES = {
     "fos_server_open_stream": (_i32, [_vp, _i32, _i32, _u32]),
     "fos_server_close_stream": (_st, [_vp, _i32]),
     "fos_server_submit": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _i64]),
+    "fos_server_submit_nocopy": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _i64]),
     "fos_server_poll": (_i32, [_vp, ctypes.POINTER(ServerResult), _i32]),
     "fos_server_stats": (_st, [_vp, ctypes.POINTER(ServerStats)]),
     "fos_softgmm_default_params": (None, [ctypes.POINTER(SoftParams)]),
@@ -471,14 +472,15 @@ class Server:
             raise FosError(st, "close_stream")
 
     def submit(self, sid: int, rgb: np.ndarray, depth: np.ndarray, mask_gmm, mask_pbas, tag: int,
-               wait: float = 0.0) -> bool:
+               wait: float = 0.0, copy: bool = True) -> bool:
         """True if queued.  False if refused for longer than ``wait`` seconds;
         ``self.refusal`` then says why: "waiting" (stream not admitted yet) or
-        "full" (its queue is full)."""
+        "full" (its queue is full).  copy=False: zero-copy submit, the arrays
+        must stay unchanged until poll() reports the tag (pinned for DMA)."""
+        fn = self.lib.fos_server_submit if copy else self.lib.fos_server_submit_nocopy
         deadline = time.monotonic() + wait
         while True:
-            st = self.lib.fos_server_submit(self.h, sid, _ptr(rgb), _ptr(depth), _ptr(mask_gmm),
-                                            _ptr(mask_pbas), tag)
+            st = fn(self.h, sid, _ptr(rgb), _ptr(depth), _ptr(mask_gmm), _ptr(mask_pbas), tag)
             if st == 0:
                 self.refusal = None
                 return True

@@ -197,3 +197,45 @@ def test_concurrent_submitters():
             np.testing.assert_array_equal(outs[(i, f)][1], mp[f])
             np.testing.assert_array_equal(outs[(i, f)][0], mg[f])
     srv.close()
+
+
+def test_zero_copy_submit_and_odd_sizes():
+    """Frames read straight from pinned caller buffers, and odd pixel counts
+    (the depth plane of a packed input must stay aligned): same masks as
+    each stream processed alone."""
+    import torch
+    from paper_2002_00250_gb300 import fos
+    sizes = [(67, 45), (33, 17), (64, 32)]
+    n = 6
+    data = [scene(W, H, n, seed=120 + i) for i, (W, H) in enumerate(sizes)]
+    pinned = [(torch.from_numpy(rgb).pin_memory(), torch.from_numpy(depth).pin_memory())
+              for rgb, depth, _ in data]
+    srv = fos.Server(1 << 34, 4)
+    sids = [srv.open_stream(W, H, stream_id=500 + i) for i, (W, H) in enumerate(sizes)]
+    outs = {}
+    for f in range(n):
+        for i, (W, H) in enumerate(sizes):
+            mg, mp = np.empty((H, W), np.uint8), np.empty((H, W), np.uint8)
+            outs[(i, f)] = (mg, mp)
+            if i == 2:  # one stream through the copying path
+                rgb, depth, _ = data[i]
+                ok = srv.submit(sids[i], rgb[f], depth[f], mg, mp, tag=i * 100 + f, wait=30.0)
+            else:
+                r, d = pinned[i]
+                ok = srv.submit(sids[i], r[f].numpy(), d[f].numpy(), mg, mp, tag=i * 100 + f,
+                                wait=30.0, copy=False)
+            assert ok
+    done = []
+    t0 = time.time()
+    while len(done) < n * len(sizes) and time.time() - t0 < 60:
+        done += srv.poll()
+        time.sleep(0.001)
+    assert len(done) == n * len(sizes)
+    assert all(r[1] == 0 for r in done)
+    srv.close()
+    for i, (W, H) in enumerate(sizes):
+        rgb, depth, _ = data[i]
+        mg, mp = _alone(W, H, 500 + i, rgb, depth)
+        for f in range(n):
+            np.testing.assert_array_equal(outs[(i, f)][0], mg[f], err_msg=f"gmm s{i} f{f}")
+            np.testing.assert_array_equal(outs[(i, f)][1], mp[f], err_msg=f"pbas s{i} f{f}")
