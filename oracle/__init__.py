@@ -90,12 +90,13 @@ def lib():
             L.or_philox_many.argtypes = [i64, vp, vp, vp]
             L.or_depth_to_u8.argtypes = [i64, vp, u32, vp]
             L.or_sobel_grad_u8.argtypes = [i32, i32, vp, vp]
+            L.or_depth_resample.argtypes = [i32, i32, vp, i32, i32, vp]
             L.or_gmm_frame.argtypes = [ctypes.POINTER(_GmmParams), i32, i32, i64, vp, vp,
                                        vp, vp, vp, vp, vp, vp, vp, vp, i32]
             L.or_pbas_frame.argtypes = [ctypes.POINTER(_PbasParams), i32, i32, i64, vp, vp,
                                         vp, vp, vp, vp, vp, vp, vp, vp, i32]
             L.or_quality.argtypes = [i64, vp, vp, vp]
-            for f in ("or_philox4x32_10", "or_philox_many", "or_depth_to_u8", "or_sobel_grad_u8",
+            for f in ("or_philox4x32_10", "or_philox_many", "or_depth_to_u8", "or_depth_resample", "or_sobel_grad_u8",
                       "or_gmm_frame", "or_pbas_frame", "or_quality"):
                 getattr(L, f).restype = None
             _lib = L
@@ -129,6 +130,16 @@ def depth_to_u8(depth, full_scale_mm: int = 10000) -> np.ndarray:
     d = np.ascontiguousarray(depth, dtype=np.uint16)
     out = np.empty(d.shape, dtype=np.uint8)
     lib().or_depth_to_u8(d.size, _p(d), full_scale_mm, _p(out))
+    return out
+
+
+def depth_resample(depth, width: int, height: int) -> np.ndarray:
+    """Depth frame (h, w) u16 resampled onto a (height, width) colour grid,
+    nearest neighbour with floor mapping (Sec. 4.3)."""
+    d = np.ascontiguousarray(depth, dtype=np.uint16)
+    sh, sw = d.shape
+    out = np.empty((height, width), dtype=np.uint16)
+    lib().or_depth_resample(sw, sh, _p(d), width, height, _p(out))
     return out
 
 

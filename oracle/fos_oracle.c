@@ -92,6 +92,17 @@ static int or_px(const uint8_t* img, int W, int H, int x, int y)
     return img[(int64_t)or_clampi(y, 0, H - 1) * W + or_clampi(x, 0, W - 1)];
 }
 
+void or_depth_resample(int sw, int sh, const uint16_t* src, int dw, int dh, uint16_t* out)
+{
+    for (int y = 0; y < dh; ++y) {
+        const int ys = (int)(((int64_t)y * sh) / dh);
+        for (int x = 0; x < dw; ++x) {
+            const int xs = (int)(((int64_t)x * sw) / dw);
+            out[(int64_t)y * dw + x] = src[(int64_t)ys * sw + xs];
+        }
+    }
+}
+
 void or_sobel_grad_u8(int W, int H, const uint8_t* img, uint8_t* g)
 {
     for (int y = 0; y < H; ++y)

@@ -9,6 +9,7 @@
  * What it computes (paper: Janus, Kryjak, Gorgon, "Foreground object
  * segmentation in RGB-D data implemented on GPU"):
  *   - depth u16 -> u8 rescale                        Sec. 4.2
+ *   - depth resampled to the colour resolution       Sec. 4.3
  *   - GMM with two separate models (RGB, depth)       Sec. 3.1, Eq. 1
  *   - PBAS with samples holding RGB and depth         Sec. 3.2
  *   - quality indicators PWC, FNR, FPR, Si            Sec. 5
@@ -37,6 +38,12 @@ void or_philox_many(int64_t n, const uint32_t* ctr, const uint32_t* key, uint32_
 
 /* ---- Sec. 4.2: depth u16 (mm, 0 = invalid) -> u8 (0 = invalid, 1..255). ---- */
 void or_depth_to_u8(int64_t n, const uint16_t* depth, uint32_t full_scale_mm, uint8_t* out);
+
+/* Depth frame of sw x sh resampled onto the colour grid dw x dh (Sec. 4.3:
+ * depth is brought to the colour resolution when the two differ; the paper
+ * does not say how).  Nearest neighbour: out(x, y) = src(floor(x*sw/dw),
+ * floor(y*sh/dh)), so the invalid value 0 is never blended into a valid depth. */
+void or_depth_resample(int sw, int sh, const uint16_t* src, int dw, int dh, uint16_t* out);
 
 /* ---- gradient magnitude feature used by PBAS: 3x3 Sobel, L1, >>3, clamp. ---- */
 void or_sobel_grad_u8(int W, int H, const uint8_t* img, uint8_t* g);

@@ -88,3 +88,35 @@ def test_quality_hand_counts(orc):
     assert q["FNR"] == pytest.approx(2 / 4)
     assert q["FPR"] == pytest.approx(1 / 4)
     assert q["Si"] == pytest.approx(2 / 5)
+
+
+# ---- depth resampled to the colour grid (Sec. 4.3; nearest, floor mapping) ----
+
+def test_depth_resample_identity(orc):
+    d = np.random.default_rng(0).integers(0, 65536, (7, 11)).astype(np.uint16)
+    np.testing.assert_array_equal(orc.depth_resample(d, 11, 7), d)
+
+
+def test_depth_resample_integer_factor_replicates(orc):
+    d = np.random.default_rng(1).integers(0, 65536, (5, 6)).astype(np.uint16)
+    up = orc.depth_resample(d, 12, 15)   # x2 across, x3 down
+    np.testing.assert_array_equal(up, np.repeat(np.repeat(d, 3, axis=0), 2, axis=1))
+
+
+def test_depth_resample_three_halves_by_hand(orc):
+    # 2x2 depth onto a 3x3 colour grid (the 1280x720 -> 1920x1080 ratio):
+    # source index = floor(dst * 2 / 3): 0 -> 0, 1 -> 0, 2 -> 1
+    d = np.array([[10, 20], [30, 0]], np.uint16)
+    want = np.array([[10, 10, 20], [10, 10, 20], [30, 30, 0]], np.uint16)
+    np.testing.assert_array_equal(orc.depth_resample(d, 3, 3), want)
+
+
+def test_depth_resample_keeps_values_and_holes(orc):
+    rng = np.random.default_rng(2)
+    d = rng.integers(1, 65536, (72, 128)).astype(np.uint16)
+    d[rng.random(d.shape) < 0.1] = 0
+    up = orc.depth_resample(d, 192, 108)
+    assert set(np.unique(up)) <= set(np.unique(d))       # no new values
+    assert (up == 0).mean() == pytest.approx((d == 0).mean(), abs=0.02)
+    down = orc.depth_resample(d, 64, 36)                  # downscale picks even rows/cols
+    np.testing.assert_array_equal(down, d[::2, ::2])
