@@ -499,7 +499,8 @@ def run_table(args):
         cfg = synth.SceneConfig(w, h, n, seed=0, n_camouflage=2 if w >= 1280 else 0,
                                 illumination_ramp=w >= 1280, shadows=w >= 1280)
         sc = synth.RGBDScene(cfg, device=dev)
-        rgb, depth, _ = sc.sequence(0, n)
+        rgb, depth, gt = sc.sequence(0, n)
+        gt = gt.contiguous()
         host = [(synth.to_numpy(rgb[t]), synth.to_numpy(depth[t])) for t in range(min(n, 9))]
         for name, methods, kern in (("GMM", fos.METHOD_GMM, "gmm_step"),
                                     ("PBAS", fos.METHOD_PBAS, "pbas_classify")):
@@ -525,6 +526,22 @@ def run_table(args):
             cnt = seg.get_counters()
             seg.set_timing(0)
             avg_us = tm[1] / max(1, tm[0]) * 1e3
+            # quality indicators (Sec. 5) of this run's masks, frames 1..n-1,
+            # on the device; the counting kernel timed on its own
+            masks = (mg if name == "GMM" else mp)[1:].contiguous()
+            truth = gt[1:]
+            counts = fos.quality_counts(masks, truth)
+            torch.cuda.synchronize()
+            q = fos.quality(counts.cpu().tolist())
+            reps = 20
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record()
+            for _ in range(reps):
+                fos.quality_counts(masks, truth, counts)
+            q1.record()
+            torch.cuda.synchronize()
+            q_us = q0.elapsed_time(q1) / reps * 1e3
+            q_gbs = 2.0 * masks.numel() / (q_us * 1e-6) / 1e9
             algo = ALGO_BYTES[kern] * w * h
             if name == "PBAS":
                 fr = max(1, cnt["frames"])
@@ -560,7 +577,36 @@ def run_table(args):
                          "latency_ms": {"p50": round(float(np.percentile(lat[10:], 50)), 3),
                                         "p99": round(float(np.percentile(lat[10:], 99)), 3),
                                         "path": "fos_process_frame, host buffers"},
-                         "cpu_oracle_mpx_frames_per_s": {"cores_" + k: v for k, v in cpu.items()}})
+                         "cpu_oracle_mpx_frames_per_s": {"cores_" + k: v for k, v in cpu.items()},
+                         "quality": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in q.items()},
+                         "quality_kernel": {"us": round(q_us, 2), "GBps": round(q_gbs, 1),
+                                            "frac": round(q_gbs / peak, 3), "bytes": 2 * masks.numel()}})
+    # the paper's mixed-resolution sensor configuration: 1920x1080 colour with
+    # 1280x720 depth resampled onto it every frame, both methods, against the
+    # same sequence with full-resolution depth
+    w, h, n, wd, hd = 1920, 1080, 100, 1280, 720
+    sc = synth.RGBDScene(synth.SceneConfig(w, h, n, seed=0), device=dev)
+    rgb, depth_full, _ = sc.sequence(0, n)
+    depth_lo = synth.RGBDScene(synth.SceneConfig(wd, hd, n, seed=0), device=dev).sequence(0, n)[1]
+    mixed = {}
+    for label, dsz, dep in (("depth 1280x720 resampled", (wd, hd), depth_lo), ("depth 1920x1080", None, depth_full)):
+        seg = fos.Segmenter(w, h, depth_size=dsz)
+        mg = torch.empty((n, h, w), dtype=torch.uint8, device=dev)
+        mp = torch.empty_like(mg)
+        for _ in range(args.warmup):
+            seg.reset()
+            seg.process_device(rgb, dep, mg, mp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            seg.reset()
+            seg.process_device(rgb, dep, mg, mp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        mixed[label] = round(w * h * n / (ms * 1e-3) / 1e6, 1)
+        seg.close()
+    rows.append({"config": f"{w}x{h}x{n} colour", "method": "GMM+PBAS", "mpx_frames_per_s": mixed})
     print(json.dumps({"metric": "per-method table", "unit": "Mpixel-frames/s", "steps": args.steps,
                       "warmup": args.warmup, "data": "synthetic", "rows": rows}), flush=True)
 

@@ -105,6 +105,32 @@ int32_t fos_abi_version(void);
  */
 fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params);
 
+/*
+ * Like fos_create, for a sensor whose depth frames are depth_width x
+ * depth_height (1..16384 each) while colour frames are width x height
+ * (Sec. 4.3: processing runs at the colour resolution).  Every depth frame
+ * passed to this context has the depth size (a frame batch is
+ * n * depth_width * depth_height values); each is resampled onto the colour
+ * grid as fos_depth_resample_device does before it is used.  With equal
+ * sizes this is fos_create.  The batch and serving APIs take equal sizes only.
+ */
+fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int32_t depth_height,
+                         const fos_params* params);
+
+/*
+ * Depth frame d_src (src_width x src_height uint16, device) resampled onto
+ * d_dst (dst_width x dst_height uint16, device), nearest neighbour:
+ * dst(x, y) = src(floor(x * src_width / dst_width),
+ * floor(y * src_height / dst_height)); every output is an input value, so
+ * the invalid reading 0 is never blended into a valid depth (Sec. 4.3 brings
+ * depth to the colour resolution without saying how).  Sizes 1..16384.
+ * Asynchronous on `stream` (cudaStream_t; NULL = legacy default stream).
+ * FOS_ERR_INVALID_ARG on NULL pointers or sizes out of range, FOS_ERR_CUDA if
+ * the launch fails (text in fos_last_error(NULL)).  Allocates nothing.
+ */
+fos_status fos_depth_resample_device(const uint16_t* d_src, int32_t src_width, int32_t src_height,
+                                     uint16_t* d_dst, int32_t dst_width, int32_t dst_height, void* stream);
+
 /* Frees the context and its device memory.  NULL-safe. */
 void fos_destroy(fos_ctx* ctx);
 
@@ -240,6 +266,27 @@ int32_t fos_get_option(const fos_ctx* ctx, int32_t option);
  * out[2] neighbour requests issued, out[3] frames.
  */
 fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4]);
+
+/* ---------------------------------------------------------------------------
+ * Quality indicators (Sec. 5): confusion counts of foreground masks against
+ * ground truth, and the percentage of wrong classifications (PWC), the false
+ * negative rate (FNR), the false positive rate (FPR) and the similarity (Si)
+ * derived from them.  A byte is foreground when it is non-zero.
+ *
+ * fos_quality_counts_device: d_mask, d_gt are device arrays of n_pixels bytes
+ * (any number of frames laid end to end); the counts TP, TN, FP, FN are ADDED
+ * to d_counts[0..3] (device uint64; zero them to start a new total).
+ * Asynchronous on `stream` (cudaStream_t; NULL = legacy default stream).
+ * FOS_ERR_INVALID_ARG for NULL pointers or n_pixels < 0; FOS_ERR_CUDA if the
+ * launch fails (text in fos_last_error(NULL)).  Allocates nothing.
+ *
+ * fos_quality_metrics: out = {PWC = 100 (FN+FP)/(TP+FN+FP+TN),
+ * FNR = FN/(TP+FN), FPR = FP/(FP+TN), Si = TP/(TP+FP+FN)} from host counts
+ * (a ratio with a zero denominator is NaN).
+ * ------------------------------------------------------------------------- */
+fos_status fos_quality_counts_device(const uint8_t* d_mask, const uint8_t* d_gt, int64_t n_pixels,
+                                     uint64_t* d_counts, void* stream);
+void fos_quality_metrics(const uint64_t counts[4], double out[4]);
 
 /* ---------------------------------------------------------------------------
  * Batched multi-stream processing.  No counterpart in the paper (one stream

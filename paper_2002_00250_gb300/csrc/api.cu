@@ -196,6 +196,11 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     if (!rgb || !depth) return fail(c, FOS_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     if (gmm_on(c) && !mg) return fail(c, FOS_ERR_INVALID_ARG, "GMM enabled: mask_gmm must be non-NULL");
     if (pbas_on(c) && !mp) return fail(c, FOS_ERR_INVALID_ARG, "PBAS enabled: mask_pbas must be non-NULL");
+    if (c->dup) {  // depth of another resolution: onto the colour grid first
+        if (launch_depth_resample(depth, c->Wd, c->Hd, c->dup, c->W, c->H, s) != kLaunchOk)
+            return fail(c, FOS_ERR_CUDA, std::string("depth resample: ") + cudaGetErrorString(cudaGetLastError()));
+        depth = c->dup;
+    }
     const bool first = c->t == 0;
     if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
     if (!first && ctx_fused(c)) {
@@ -240,7 +245,7 @@ fos_status ensure_staging(fos_ctx* c)
     if (c->h_rgb[0]) return FOS_OK;
     for (int b = 0; b < 2; ++b) {
         FOS_TRY(c, cudaMalloc(&c->h_rgb[b], size_t(c->P) * 3 + 16));
-        FOS_TRY(c, cudaMalloc(&c->h_depth[b], size_t(c->P) * 2 + 16));
+        FOS_TRY(c, cudaMalloc(&c->h_depth[b], size_t(c->Pd) * 2 + 16));
         FOS_TRY(c, cudaMalloc(&c->h_mg[b], size_t(c->P) + 16));
         FOS_TRY(c, cudaMalloc(&c->h_mp[b], size_t(c->P) + 16));
         FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
@@ -264,7 +269,7 @@ size_t pbas_bytes(const fos_ctx* c)
 void free_all(fos_ctx* c)
 {
     cudaFree(c->gmm); cudaFree(c->samp); cudaFree(c->Dq); cudaFree(c->R); cudaFree(c->T);
-    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux);
+    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux); cudaFree(c->dup);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
@@ -355,9 +360,16 @@ int32_t fos_abi_version(void) { return FOS_ABI_VERSION; }
 
 fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
 {
+    return fos_create_rgbd(width, height, width, height, params);
+}
+
+fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int32_t depth_height,
+                         const fos_params* params)
+{
     g_create_error.clear();
-    if (width < 1 || height < 1 || width > 16384 || height > 16384) {
-        fail(nullptr, FOS_ERR_INVALID_ARG, "width and height must be in 1..16384");
+    if (width < 1 || height < 1 || width > 16384 || height > 16384 || depth_width < 1 || depth_height < 1 ||
+        depth_width > 16384 || depth_height > 16384) {
+        fail(nullptr, FOS_ERR_INVALID_ARG, "width, height, depth_width, depth_height must be in 1..16384");
         return nullptr;
     }
     std::string why;
@@ -368,6 +380,8 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
     fos_ctx* c = new fos_ctx();
     c->W = width; c->H = height;
     c->P = int64_t(width) * height;
+    c->Wd = depth_width; c->Hd = depth_height;
+    c->Pd = int64_t(depth_width) * depth_height;
     c->plane = round_up(c->P, 128);
     c->spr = (width + kSeg - 1) / kSeg;
     c->Wp = c->spr * kSeg;
@@ -400,6 +414,9 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params)
         if ((e = cudaMalloc(&c->prev, pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
     if ((e = cudaMalloc(&c->aux, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
+    if ((depth_width != width || depth_height != height) &&
+        (e = cudaMalloc(&c->dup, size_t(c->P) * 2 + 16)) != cudaSuccess)
+        return bail("cudaMalloc(resampled depth)", e);
     if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
     return c;
 }
@@ -441,9 +458,9 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
 {
     if (!ctx) return FOS_ERR_INVALID_ARG;
     if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
-    const int64_t P = ctx->P;
+    const int64_t P = ctx->P, Pd = ctx->Pd;
     for (int32_t f = 0; f < n_frames; ++f) {
-        fos_status st = process_device(ctx, d_rgb + f * P * 3, d_depth + f * P,
+        fos_status st = process_device(ctx, d_rgb + f * P * 3, d_depth + f * Pd,
                                        d_mask_gmm ? d_mask_gmm + f * P : nullptr,
                                        d_mask_pbas ? d_mask_pbas + f * P : nullptr,
                                        static_cast<cudaStream_t>(stream));
@@ -462,12 +479,12 @@ fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t
     if (pbas_on(ctx) && !mask_pbas && n_frames > 0) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_pbas must be non-NULL");
     fos_status st = ensure_staging(ctx);
     if (st != FOS_OK) return st;
-    const size_t P = size_t(ctx->P);
+    const size_t P = size_t(ctx->P), Pd = size_t(ctx->Pd);
     for (int32_t f = 0; f < n_frames; ++f) {
         const int b = f & 1;
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[b], 0));
         FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_rgb[b], rgb + f * P * 3, P * 3, cudaMemcpyHostToDevice, ctx->copy_stream));
-        FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_depth[b], depth + f * P, P * 2, cudaMemcpyHostToDevice, ctx->copy_stream));
+        FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_depth[b], depth + f * Pd, Pd * 2, cudaMemcpyHostToDevice, ctx->copy_stream));
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_in[b], ctx->copy_stream));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[b], 0));
         st = process_device(ctx, ctx->h_rgb[b], ctx->h_depth[b], ctx->h_mg[b], ctx->h_mp[b], ctx->stream);

@@ -118,6 +118,10 @@ LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, 
                                int blocks, int N, int px, int ty, cudaStream_t s);
 int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused);
 
+// Depth frame sw x sh resampled onto dw x dh (nearest, floor mapping).
+LaunchResult launch_depth_resample(const uint16_t* src, int sw, int sh, uint16_t* dst, int dw, int dh,
+                                   cudaStream_t s);
+
 // Sets the text fos_last_error(NULL) returns on the calling thread.
 void set_thread_error(const char* msg);
 

@@ -101,6 +101,8 @@ SIGNATURES = {
     "fos_default_params": (None, [ctypes.POINTER(Params)]),
     "fos_abi_version": (_i32, []),
     "fos_create": (_vp, [_i32, _i32, ctypes.POINTER(Params)]),
+    "fos_create_rgbd": (_vp, [_i32, _i32, _i32, _i32, ctypes.POINTER(Params)]),
+    "fos_depth_resample_device": (_st, [_vp, _i32, _i32, _vp, _i32, _i32, _vp]),
     "fos_destroy": (None, [_vp]),
     "fos_last_error": (ctypes.c_char_p, [_vp]),
     "fos_reset": (_st, [_vp]),
@@ -118,6 +120,8 @@ SIGNATURES = {
     "fos_get_counters": (_st, [_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "fos_set_option": (_st, [_vp, _i32, _i32]),
     "fos_get_option": (_i32, [_vp, _i32]),
+    "fos_quality_counts_device": (_st, [_vp, _vp, _i64, _vp, _vp]),
+    "fos_quality_metrics": (None, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
     "fos_pbas_step_noalloc": (_st, [_i32, _i32, ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp]),
     "fos_stream_device_bytes": (ctypes.c_size_t, [_i32, _i32, ctypes.POINTER(Params)]),
     "fos_batch_create": (_vp, [_i32, ctypes.POINTER(Params)]),
@@ -208,14 +212,19 @@ class StateView:
 class Segmenter:
     """One camera stream: owns a fos_ctx (device-resident GMM and/or PBAS model)."""
 
-    def __init__(self, width: int, height: int, params: Params | None = None, **overrides):
+    def __init__(self, width: int, height: int, params: Params | None = None, depth_size=None,
+                 **overrides):
+        """depth_size=(depth_width, depth_height): depth frames of another
+        resolution, resampled onto the colour grid (fos_create_rgbd)."""
         self.lib = load()
         self.params = params if params is not None else default_params(**overrides)
         if params is not None and overrides:
             for k, v in overrides.items():
                 setattr(self.params, "lambda_" if k == "lambda" else k, v)
         self.W, self.H, self.P = width, height, width * height
-        h = self.lib.fos_create(width, height, ctypes.byref(self.params))
+        self.Wd, self.Hd = depth_size if depth_size is not None else (width, height)
+        self.Pd = self.Wd * self.Hd
+        h = self.lib.fos_create_rgbd(width, height, self.Wd, self.Hd, ctypes.byref(self.params))
         if not h:
             raise FosError(1, self.lib.fos_last_error(None).decode())
         self.h = h
@@ -266,7 +275,7 @@ class Segmenter:
         depth = np.ascontiguousarray(depth, dtype=np.uint16)
         n = 1 if single else rgb.shape[0]
         shape = (self.H, self.W) if single else (n, self.H, self.W)
-        assert rgb.size == n * self.P * 3 and depth.size == n * self.P
+        assert rgb.size == n * self.P * 3 and depth.size == n * self.Pd
         mg = np.empty(shape, np.uint8) if self.gmm else None
         mp = np.empty(shape, np.uint8) if self.pbas else None
         self._check(self.lib.fos_process_frames_host(self.h, n, _ptr(rgb), _ptr(depth),
@@ -280,9 +289,9 @@ class Segmenter:
     # -- device frames -------------------------------------------------------
     def process_device(self, rgb, depth, mask_gmm=None, mask_pbas=None, stream=None):
         """Frames already on the device (torch CUDA tensors), asynchronous.
-        rgb (n,H,W,3) or (H,W,3) u8; depth u16 of matching shape; masks u8."""
+        rgb (n,H,W,3) or (H,W,3) u8; depth u16 (n,Hd,Wd) or (Hd,Wd); masks u8."""
         n = 1 if rgb.dim() == 3 else rgb.shape[0]
-        assert rgb.numel() == n * self.P * 3 and depth.numel() == n * self.P
+        assert rgb.numel() == n * self.P * 3 and depth.numel() == n * self.Pd
         self._check(self.lib.fos_process_frames_device(
             self.h, n, _ptr(rgb), _ptr(depth), _ptr(mask_gmm), _ptr(mask_pbas),
             _stream_handle(stream)))
@@ -502,3 +511,47 @@ class Server:
         d = {f: getattr(s, f) for f, _ in ServerStats._fields_}
         d["ok"] = st == 0
         return d
+
+
+QUALITY_NAMES = ("TP", "TN", "FP", "FN", "PWC", "FNR", "FPR", "Si")
+
+
+def quality_counts(mask, gt, counts=None, stream=None):
+    """Adds TP, TN, FP, FN of device masks against device ground truth (torch
+    uint8 CUDA tensors of the same number of bytes) to `counts` (an int64
+    CUDA tensor of 4, created zeroed if None); returns counts (asynchronous)."""
+    import torch
+    lib = load()
+    if counts is None:
+        counts = torch.zeros(4, dtype=torch.int64, device=mask.device)  # same bits as uint64 here
+    n = mask.numel()
+    if gt.numel() != n:
+        raise ValueError("mask and ground truth differ in size")
+    st = lib.fos_quality_counts_device(_ptr(mask), _ptr(gt), n, _ptr(counts), _stream_handle(stream))
+    if st != 0:
+        raise FosError(st, lib.fos_last_error(None).decode())
+    return counts
+
+
+def quality(counts) -> dict:
+    """TP, TN, FP, FN and PWC, FNR, FPR, Si from four counts (host values)."""
+    lib = load()
+    c = (ctypes.c_uint64 * 4)(*[int(v) for v in counts])
+    out = (ctypes.c_double * 4)()
+    lib.fos_quality_metrics(c, out)
+    return dict(zip(QUALITY_NAMES, [int(v) for v in counts] + list(out)))
+
+
+def depth_resample(src, width: int, height: int, out=None, stream=None):
+    """Device depth frame (torch uint16 CUDA tensor (h, w)) resampled onto a
+    (height, width) grid by fos_depth_resample_device (asynchronous)."""
+    import torch
+    lib = load()
+    sh, sw = src.shape[-2], src.shape[-1]
+    if out is None:
+        out = torch.empty((height, width), dtype=src.dtype, device=src.device)
+    st = lib.fos_depth_resample_device(_ptr(src), sw, sh, _ptr(out), width, height, _stream_handle(stream))
+    if st != 0:
+        raise FosError(st, lib.fos_last_error(None).decode())
+    return out
+
