@@ -64,6 +64,10 @@ class _GmmParams(ctypes.Structure):
                 ("depth_full_scale_mm", ctypes.c_uint32)]
 
 
+class _GmmLiteralParams(ctypes.Structure):
+    _fields_ = [("base", _GmmParams), ("s", ctypes.c_double), ("theta", ctypes.c_double)]
+
+
 class _PbasParams(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("n_min", ctypes.c_int),
                 ("R_lower_rgb", ctypes.c_float), ("R_lower_d", ctypes.c_float),
@@ -96,8 +100,10 @@ def lib():
             L.or_pbas_frame.argtypes = [ctypes.POINTER(_PbasParams), i32, i32, i64, vp, vp,
                                         vp, vp, vp, vp, vp, vp, vp, vp, i32]
             L.or_quality.argtypes = [i64, vp, vp, vp]
+            L.or_gmm_literal_frame.argtypes = [ctypes.POINTER(_GmmLiteralParams), i32, i32, i64, vp, vp,
+                                               vp, vp, vp, vp, vp, vp, vp, vp, i32]
             for f in ("or_philox4x32_10", "or_philox_many", "or_depth_to_u8", "or_depth_resample", "or_sobel_grad_u8",
-                      "or_gmm_frame", "or_pbas_frame", "or_quality"):
+                      "or_gmm_frame", "or_gmm_literal_frame", "or_pbas_frame", "or_quality"):
                 getattr(L, f).restype = None
             _lib = L
     return _lib
@@ -197,6 +203,50 @@ class GMM:
                            _p(self.w_rgb), _p(self.mu_rgb), _p(self.v_rgb),
                            _p(self.w_d), _p(self.mu_d), _p(self.v_d), _p(mask),
                            _p(margin) if margin is not None else None, self.nthreads)
+        self.t += 1
+        return (mask, margin) if want_margin else mask
+
+
+GMM_LITERAL_DEFAULTS = dict(GMM_DEFAULTS, K_rgb=7, K_d=3, s=10000.0, theta=1.0)
+
+
+class GMMLiteral:
+    """Sec. 3.1 as printed: K = 7 / 3, FP64, one variance per colour channel,
+    decision on the product of the two models' s-scaled Eq. 1 densities
+    (full definition with or_gmm_literal_frame in fos_oracle.h).
+
+    State arrays: ``w_rgb (P,Kr)``, ``mu_rgb (P,Kr,3)``, ``v_rgb (P,Kr,3)``,
+    ``w_d (P,Kd)``, ``mu_d (P,Kd)``, ``v_d (P,Kd)``.
+    """
+
+    def __init__(self, width: int, height: int, nthreads: int = 0, **params):
+        pr = dict(GMM_LITERAL_DEFAULTS)
+        pr.update(params)
+        self.params = pr
+        base = {k: v for k, v in pr.items() if k not in ("s", "theta")}
+        self._c = _GmmLiteralParams(_GmmParams(**base), pr["s"], pr["theta"])
+        self.W, self.H = width, height
+        P = width * height
+        Kr, Kd = pr["K_rgb"], pr["K_d"]
+        self.w_rgb = np.zeros((P, Kr))
+        self.mu_rgb = np.zeros((P, Kr, 3))
+        self.v_rgb = np.zeros((P, Kr, 3))
+        self.w_d = np.zeros((P, Kd))
+        self.mu_d = np.zeros((P, Kd))
+        self.v_d = np.zeros((P, Kd))
+        self.t = 0
+        self.nthreads = nthreads
+
+    def step(self, rgb, depth, want_margin: bool = False):
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        assert rgb.shape == (self.H, self.W, 3) and depth.shape == (self.H, self.W)
+        mask = np.empty((self.H, self.W), dtype=np.uint8)
+        margin = np.empty((self.H, self.W), dtype=np.float64) if want_margin else None
+        lib().or_gmm_literal_frame(ctypes.byref(self._c), self.W, self.H, self.t, _p(rgb), _p(depth),
+                                   _p(self.w_rgb), _p(self.mu_rgb), _p(self.v_rgb),
+                                   _p(self.w_d), _p(self.mu_d), _p(self.v_d), _p(mask),
+                                   _p(margin) if margin is not None else None, self.nthreads)
         self.t += 1
         return (mask, margin) if want_margin else mask
 

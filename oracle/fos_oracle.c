@@ -299,6 +299,160 @@ void or_gmm_frame(const or_gmm_params* p, int W, int H, int64_t t,
     }
 }
 
+/* ---- the paper-literal GMM variant (declaration comment in the header) ---- */
+typedef struct {
+    double w, mu[3], v[3];
+} or_dcomp;
+
+/* One model, one pixel, one frame t >= 1: returns the model's density factor
+ * F = s * (background-set mixture density of x) before this frame's update. */
+static double or_gmm_literal_model_step(int K, int C, const or_gmm_literal_params* lp, double v_init,
+                                        double v_min, const double* x, or_dcomp* c, double* margin)
+{
+    const or_gmm_params* p = &lp->base;
+    const double lam2 = p->lambda * p->lambda, alpha = p->alpha;
+    const double two_pi = 6.283185307179586476925286766559;
+    double D[8], diff[8][3];
+    for (int k = 0; k < K; ++k) {
+        D[k] = 0.0;
+        for (int ch = 0; ch < C; ++ch) {
+            diff[k][ch] = x[ch] - c[k].mu[ch];
+            D[k] += diff[k][ch] * diff[k][ch] / c[k].v[ch];
+        }
+    }
+    /* background set and its normalised mixture density (old parameters) */
+    double cum = 0.0, num = 0.0, den = 0.0;
+    for (int k = 0; k < K; ++k) {
+        double g = 1.0;
+        for (int ch = 0; ch < C; ++ch) g *= c[k].v[ch];
+        g = pow(g, 1.0 / (double)C);
+        num += c[k].w * exp(-0.5 * D[k]) / (two_pi * g);
+        den += c[k].w;
+        cum += c[k].w;
+        or_margin_min(margin, cum, p->T_bg);
+        if (cum > p->T_bg) break;
+    }
+    const double F = lp->s * num / den;
+    /* match on the per-channel Mahalanobis distance, averaged over channels */
+    int match = -1;
+    for (int k = 0; k < K; ++k) {
+        const double dm = D[k] / (double)C;
+        or_margin_min(margin, dm, lam2);
+        if (dm < lam2) {
+            match = k;
+            break;
+        }
+    }
+    for (int k = 0; k < K; ++k) c[k].w = (1.0 - alpha) * c[k].w + (k == match ? alpha : 0.0);
+    if (match >= 0) {
+        or_dcomp* m = &c[match];
+        const double rho = alpha / m->w;
+        for (int ch = 0; ch < C; ++ch) {
+            m->mu[ch] = m->mu[ch] + rho * diff[match][ch];
+            const double v = m->v[ch] + rho * (diff[match][ch] * diff[match][ch] - m->v[ch]);
+            m->v[ch] = v > v_min ? v : v_min;
+        }
+    } else {
+        or_dcomp* m = &c[K - 1];
+        m->w = alpha;
+        for (int ch = 0; ch < 3; ++ch) {
+            m->mu[ch] = ch < C ? x[ch] : 0.0;
+            m->v[ch] = ch < C ? v_init : 0.0;
+        }
+    }
+    double sum = 0.0;
+    for (int k = 0; k < K; ++k) sum += c[k].w;
+    for (int k = 0; k < K; ++k) c[k].w = c[k].w / sum;
+    double key[8];
+    for (int k = 0; k < K; ++k) {
+        double vb = 0.0;
+        for (int ch = 0; ch < C; ++ch) vb += c[k].v[ch];
+        key[k] = c[k].w / sqrt(vb / (double)C);
+    }
+    for (int a = 0; a < K; ++a)
+        for (int b = a + 1; b < K; ++b) {
+            if (key[a] == 0.0 && key[b] == 0.0) continue;
+            const double mx = fabs(key[a]) > fabs(key[b]) ? fabs(key[a]) : fabs(key[b]);
+            const double r = fabs(key[a] - key[b]) / mx;
+            if (r < *margin) *margin = r;
+        }
+    for (int i = 1; i < K; ++i) {
+        int j = i;
+        while (j > 0 && key[j] > key[j - 1]) {
+            or_dcomp tc = c[j]; c[j] = c[j - 1]; c[j - 1] = tc;
+            double tk = key[j]; key[j] = key[j - 1]; key[j - 1] = tk;
+            --j;
+        }
+    }
+    return F;
+}
+
+void or_gmm_literal_frame(const or_gmm_literal_params* lp, int W, int H, int64_t t,
+                          const uint8_t* rgb, const uint16_t* depth,
+                          double* w_rgb, double* mu_rgb, double* v_rgb,
+                          double* w_d, double* mu_d, double* v_d,
+                          uint8_t* mask, double* margin, int nthreads)
+{
+    const or_gmm_params* p = &lp->base;
+    const int64_t P = (int64_t)W * H;
+    const int Kr = p->K_rgb, Kd = p->K_d;
+    (void)nthreads;
+#pragma omp parallel for schedule(static) num_threads(OR_THREADS(nthreads))
+    for (int64_t i = 0; i < P; ++i) {
+        const double xr[3] = {rgb[3 * i + 0], rgb[3 * i + 1], rgb[3 * i + 2]};
+        const int valid = depth[i] != 0;
+        const double xd[1] = {(double)or_depth_u8_one(depth[i], p->depth_full_scale_mm)};
+        or_dcomp cr[8], cd[8];
+        double mg = INFINITY;
+        if (t == 0) {
+            for (int k = 0; k < Kr; ++k) {
+                cr[k].w = k == 0 ? 1.0 : 0.0;
+                for (int ch = 0; ch < 3; ++ch) {
+                    cr[k].mu[ch] = k == 0 ? xr[ch] : 0.0;
+                    cr[k].v[ch] = p->v_init_rgb;
+                }
+            }
+            for (int k = 0; k < Kd; ++k) {
+                cd[k].w = k == 0 ? 1.0 : 0.0;
+                cd[k].mu[0] = k == 0 ? xd[0] : 0.0;
+                cd[k].v[0] = p->v_init_d;
+            }
+            mask[i] = 0;
+        } else {
+            for (int k = 0; k < Kr; ++k) {
+                cr[k].w = w_rgb[i * Kr + k];
+                for (int ch = 0; ch < 3; ++ch) {
+                    cr[k].mu[ch] = mu_rgb[(i * Kr + k) * 3 + ch];
+                    cr[k].v[ch] = v_rgb[(i * Kr + k) * 3 + ch];
+                }
+            }
+            for (int k = 0; k < Kd; ++k) {
+                cd[k].w = w_d[i * Kd + k];
+                cd[k].mu[0] = mu_d[i * Kd + k];
+                cd[k].v[0] = v_d[i * Kd + k];
+            }
+            double F = or_gmm_literal_model_step(Kr, 3, lp, p->v_init_rgb, p->v_min_rgb, xr, cr, &mg);
+            if (valid) F *= or_gmm_literal_model_step(Kd, 1, lp, p->v_init_d, p->v_min_d, xd, cd, &mg);
+            const double r = fabs(log(F / lp->theta));
+            if (r < mg) mg = r;
+            mask[i] = F >= lp->theta ? 0 : 255;
+        }
+        for (int k = 0; k < Kr; ++k) {
+            w_rgb[i * Kr + k] = cr[k].w;
+            for (int ch = 0; ch < 3; ++ch) {
+                mu_rgb[(i * Kr + k) * 3 + ch] = cr[k].mu[ch];
+                v_rgb[(i * Kr + k) * 3 + ch] = cr[k].v[ch];
+            }
+        }
+        for (int k = 0; k < Kd; ++k) {
+            w_d[i * Kd + k] = cd[k].w;
+            mu_d[i * Kd + k] = cd[k].mu[0];
+            v_d[i * Kd + k] = cd[k].v[0];
+        }
+        if (margin) margin[i] = mg;
+    }
+}
+
 /* ======================================================================== */
 /* Sec. 3.2: PBAS (Hofmann et al.) with a sample holding R, G, B and D,     */
 /* each channel processed separately with its own decision threshold R,     */

@@ -78,6 +78,36 @@ void or_gmm_frame(const or_gmm_params* p, int W, int H, int64_t t,
                   double* w_d, double* mu_d, double* v_d,
                   uint8_t* mask, double* margin, int nthreads);
 
+/* ---- Sec. 3.1 as printed: the paper-literal GMM variant (FP64). ----
+ * K_rgb = 7 / K_d = 3 in the paper; one variance per colour channel
+ * ("a single value is used for each colour component"); the decision uses
+ * the Eq. 1 density scaled by s: per model the factor
+ *   F = s * sum_{k in B} w_k eta_k(x) / sum_{k in B} w_k,
+ *   eta_k = exp(-D_k / 2) / (2 pi g_k),  D_k = sum_c (x_c - mu_kc)^2 / v_kc,
+ *   g_k = (prod_c v_kc)^(1/C)
+ * over the background set B of the model before this frame's update (for one
+ * channel this is Eq. 1 with sigma read as the variance); the two factors are
+ * multiplied (depth only where valid) and the pixel is foreground when the
+ * product is below theta.  The update is the default one per channel: match =
+ * first ranked k with D_k / C < lambda^2; matched: rho = alpha / w_k,
+ * mu_kc += rho (x_c - mu_kc), v_kc <- max(v_min, v_kc + rho ((x_c - mu_kc)^2
+ * - v_kc)); no match: last-ranked <- (alpha, x, v_init in every channel);
+ * normalise; stable re-rank by w / sqrt(mean_c v_kc).
+ * State (pixel-major, then component, ranked): w_rgb[P*Kr], mu_rgb[P*Kr*3],
+ * v_rgb[P*Kr*3], w_d[P*Kd], mu_d[P*Kd], v_d[P*Kd].  margin as or_gmm_frame
+ * (the final decision's margin is |log(F / theta)|). */
+typedef struct {
+    or_gmm_params base;
+    double s;       /* density scale, 10000 in the paper */
+    double theta;   /* background iff the product of the factors >= theta */
+} or_gmm_literal_params;
+
+void or_gmm_literal_frame(const or_gmm_literal_params* p, int W, int H, int64_t t,
+                          const uint8_t* rgb, const uint16_t* depth,
+                          double* w_rgb, double* mu_rgb, double* v_rgb,
+                          double* w_d, double* mu_d, double* v_d,
+                          uint8_t* mask, double* margin, int nthreads);
+
 /* ---- Sec. 3.2: PBAS with samples holding (R, G, B, D), FP32 + integers. ---- */
 typedef struct {
     int N;                      /* samples per pixel, 1..32 */
