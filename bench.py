@@ -581,6 +581,42 @@ def run_table(args):
                          "quality": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in q.items()},
                          "quality_kernel": {"us": round(q_us, 2), "GBps": round(q_gbs, 1),
                                             "frac": round(q_gbs / peak, 3), "bytes": 2 * masks.numel()}})
+    # the paper-literal GMM (K = 7 + 3, FP64, per-channel variances, density
+    # product decision) on the 1280x720 sequence: throughput, its kernel
+    # against HBM (934 B per pixel-frame: 58 doubles read and written, 5 B
+    # input, 1 B mask) and the quality of its masks
+    w, h, n = 1280, 720, 60
+    sc = synth.RGBDScene(synth.config_720p(seed=0), device=dev)
+    rgb, depth, gt = sc.sequence(0, n)
+    seg = fos.Segmenter(w, h, methods=fos.METHOD_GMM, gmm_literal=1, K_rgb=7, K_d=3)
+    mg = torch.empty((n, h, w), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        seg.reset()
+        seg.process_device(rgb, depth, mg, None)
+    torch.cuda.synchronize()
+    seg.get_timing()
+    seg.set_timing(1 << fos.KERNEL_GMM)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        seg.reset()
+        seg.process_device(rgb, depth, mg, None)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tm = seg.get_timing()["gmm_step"]
+    seg.close()
+    avg_us = tm[1] / max(1, tm[0]) * 1e3
+    gbs = 934.0 * w * h / (avg_us * 1e-6) / 1e9
+    q = fos.quality(fos.quality_counts(mg[1:].contiguous(), gt[1:].contiguous()).cpu().tolist())
+    rows.append({"config": f"{w}x{h}x{n}", "method": "GMM literal (K 7+3, FP64, density product)",
+                 "mpx_frames_per_s": round(w * h * n / (ms * 1e-3) / 1e6, 1),
+                 "kernel": "gmm_literal", "kernel_avg_us": round(avg_us, 2),
+                 "roofline": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(gbs / peak, 3), "peak_source": peak_src,
+                              "note": "FP64 exp/pow per component: arithmetic-bound"},
+                 "quality": {k: (round(v, 5) if isinstance(v, float) else v) for k, v in q.items()}})
+
     # the paper's mixed-resolution sensor configuration: 1920x1080 colour with
     # 1280x720 depth resampled onto it every frame, both methods, against the
     # same sequence with full-resolution depth

@@ -88,6 +88,12 @@ typedef struct fos_params {
     int32_t forced_rng;        /* 0: Philox; 1: deterministic test draws */
     /* ---- input conversion (Sec. 4.2) ---- */
     uint32_t depth_full_scale_mm; /* depth mapped onto 1..255, 0 = invalid */
+    /* ---- GMM as the paper prints it (Sec. 3.1, Eq. 1) ---- */
+    int32_t gmm_literal;       /* 1: FP64 state, one variance per colour channel, decision on the
+                                  product of the s-scaled Eq. 1 densities (K = 7+3 or 3+3);
+                                  0: the FP32 isotropic model with the distance score */
+    float density_scale;       /* s (paper: 10000) */
+    float density_threshold;   /* background iff the product of the factors >= this */
 } fos_params;
 
 typedef struct fos_ctx fos_ctx;
@@ -193,6 +199,9 @@ fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t
  *        w[k], mu_r[k], mu_g[k], mu_b[k], v[k] (in that order, each k = 0..K-1),
  *        then for the depth model with K = K_d: w[k], mu[k], v[k].
  *        Components are stored in ranked order (k = 0 ranks highest).
+ *        With gmm_literal = 1 the section is float64 with one variance per
+ *        colour channel: w[k], mu_r[k], mu_g[k], mu_b[k], v_r[k], v_g[k],
+ *        v_b[k], then depth w[k], mu[k], v[k] (gmm_bytes tells them apart).
  *   PBAS: samples  uint16 planes [c][k] (c = R,G,B,D; k = 0..N-1), value in the
  *                  low byte, gradient magnitude in the high byte;
  *         D        uint16 planes [c][k]: minimal distance x16 (rounded);

@@ -66,8 +66,19 @@ fos_status validate_params(const fos_params* p, std::string& why)
     if (p->methods == 0 || (p->methods & ~(FOS_METHOD_GMM | FOS_METHOD_PBAS))) {
         why = "methods must be a non-empty subset of GMM|PBAS"; return FOS_ERR_INVALID_ARG;
     }
+    if (p->gmm_literal != 0 && p->gmm_literal != 1) {
+        why = "gmm_literal must be 0 or 1"; return FOS_ERR_INVALID_ARG;
+    }
+    if ((p->methods & FOS_METHOD_GMM) && p->gmm_literal) {
+        if (!gmm_literal_supported(p->K_rgb, p->K_d)) {
+            why = "the literal GMM takes (K_rgb, K_d) = (7, 3) or (3, 3)"; return FOS_ERR_UNSUPPORTED;
+        }
+        if (!(p->density_scale > 0.f) || !(p->density_threshold > 0.f)) {
+            why = "density_scale and density_threshold must be > 0"; return FOS_ERR_INVALID_ARG;
+        }
+    }
     if (p->methods & FOS_METHOD_GMM) {
-        if (!k_supported(p->K_rgb, p->K_d)) {
+        if (!p->gmm_literal && !k_supported(p->K_rgb, p->K_d)) {
             why = "unsupported (K_rgb, K_d); K_rgb in {1,2,3,5,7}, K_d in {1,2,3}";
             return FOS_ERR_UNSUPPORTED;
         }
@@ -187,7 +198,8 @@ GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t*
 // GMM and PBAS of a frame in one launch: both methods, the 3+3 model, option on.
 bool ctx_fused(const fos_ctx* c)
 {
-    return gmm_on(c) && pbas_on(c) && c->prm.K_rgb == 3 && c->prm.K_d == 3 && c->opt[FOS_OPT_FUSE] != 0;
+    return gmm_on(c) && pbas_on(c) && !c->prm.gmm_literal && c->prm.K_rgb == 3 && c->prm.K_d == 3 &&
+           c->opt[FOS_OPT_FUSE] != 0;
 }
 
 fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mg,
@@ -215,10 +227,22 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
         return FOS_OK;
     }
     if (gmm_on(c)) {
-        const GmmArgs a = gmm_args(c, rgb, depth, mg);
         const fos_params& p = c->prm;
         TimedScope ts(c, first ? FOS_KERNEL_INIT : FOS_KERNEL_GMM, s);
-        fos_status st = launch_result(c, launch_gmm(a, p.K_rgb, p.K_d, s), "gmm");
+        fos_status st;
+        if (p.gmm_literal) {
+            GmmLiteralArgs a{};
+            a.P = c->P; a.plane = c->plane; a.state = reinterpret_cast<double*>(c->gmm);
+            a.rgb = rgb; a.depth = depth; a.mask = mg;
+            a.alpha = p.alpha; a.lam2 = double(p.lambda) * double(p.lambda); a.T_bg = p.T_bg;
+            a.v_init_rgb = p.v_init_rgb; a.v_init_d = p.v_init_d; a.v_min_rgb = p.v_min_rgb; a.v_min_d = p.v_min_d;
+            a.s = p.density_scale; a.theta = p.density_threshold;
+            a.depth_fs = p.depth_full_scale_mm; a.init = first ? 1 : 0;
+            st = launch_result(c, launch_gmm_literal(a, p.K_rgb, p.K_d, s), "gmm_literal");
+        } else {
+            const GmmArgs a = gmm_args(c, rgb, depth, mg);
+            st = launch_result(c, launch_gmm(a, p.K_rgb, p.K_d, s), "gmm");
+        }
         if (st != FOS_OK) return st;
     }
     if (pbas_on(c)) {
@@ -254,9 +278,18 @@ fos_status ensure_staging(fos_ctx* c)
     return FOS_OK;
 }
 
+// GMM state planes and bytes per element: FP32 isotropic, or the FP64
+// literal model with per-channel variances.
+size_t gmm_nplanes(const fos_ctx* c)
+{
+    return size_t(c->prm.gmm_literal ? gmm_literal_planes(c->prm.K_rgb, c->prm.K_d)
+                                     : gmm_planes(c->prm.K_rgb, c->prm.K_d));
+}
+size_t gmm_elem(const fos_ctx* c) { return c->prm.gmm_literal ? 8 : 4; }
+
 size_t gmm_bytes(const fos_ctx* c)
 {
-    return gmm_on(c) ? size_t(gmm_planes(c->prm.K_rgb, c->prm.K_d)) * c->P * 4 : 0;
+    return gmm_on(c) ? gmm_nplanes(c) * size_t(c->P) * gmm_elem(c) : 0;
 }
 
 size_t pbas_bytes(const fos_ctx* c)
@@ -354,6 +387,7 @@ void fos_default_params(fos_params* p)
     p->alpha_g = 10.f; p->eps_d = 1.f / 16.f;
     p->seed = 0; p->stream_id = 0; p->forced_rng = 0;
     p->depth_full_scale_mm = 10000;
+    p->gmm_literal = 0; p->density_scale = 10000.f; p->density_threshold = 1.f;
 }
 
 int32_t fos_abi_version(void) { return FOS_ABI_VERSION; }
@@ -400,7 +434,7 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
     if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
     const size_t pl = size_t(c->plane);
     if (gmm_on(c)) {
-        const size_t n = size_t(gmm_planes(params->K_rgb, params->K_d)) * pl * sizeof(float);
+        const size_t n = gmm_nplanes(c) * pl * gmm_elem(c);
         if ((e = cudaMalloc(&c->gmm, n)) != cudaSuccess) return bail("cudaMalloc(gmm)", e);
     }
     if (pbas_on(c)) {
@@ -554,9 +588,9 @@ fos_status fos_get_state(fos_ctx* ctx, void* host_buf, size_t bytes)
     out += sizeof h;
     const size_t P = size_t(ctx->P), pl = size_t(ctx->plane);
     if (gmm_on(ctx)) {
-        const size_t np = size_t(gmm_planes(ctx->prm.K_rgb, ctx->prm.K_d));
-        FOS_TRY(ctx, cudaMemcpy2D(out, P * 4, ctx->gmm, pl * 4, P * 4, np, cudaMemcpyDeviceToHost));
-        out += np * P * 4;
+        const size_t np = gmm_nplanes(ctx), el = gmm_elem(ctx);
+        FOS_TRY(ctx, cudaMemcpy2D(out, P * el, ctx->gmm, pl * el, P * el, np, cudaMemcpyDeviceToHost));
+        out += np * P * el;
     }
     if (pbas_on(ctx)) {
         const size_t N4 = 4 * size_t(ctx->prm.N);
@@ -597,9 +631,9 @@ fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes)
     FOS_TRY(ctx, cudaDeviceSynchronize());
     const size_t P = size_t(ctx->P), pl = size_t(ctx->plane);
     if (gmm_on(ctx)) {
-        const size_t np = size_t(gmm_planes(ctx->prm.K_rgb, ctx->prm.K_d));
-        FOS_TRY(ctx, cudaMemcpy2D(ctx->gmm, pl * 4, in, P * 4, P * 4, np, cudaMemcpyHostToDevice));
-        in += np * P * 4;
+        const size_t np = gmm_nplanes(ctx), el = gmm_elem(ctx);
+        FOS_TRY(ctx, cudaMemcpy2D(ctx->gmm, pl * el, in, P * el, P * el, np, cudaMemcpyHostToDevice));
+        in += np * P * el;
     }
     if (pbas_on(ctx)) {
         const size_t N4 = 4 * size_t(ctx->prm.N);

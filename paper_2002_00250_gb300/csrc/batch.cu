@@ -155,6 +155,10 @@ fos_batch* fos_batch_create(int32_t max_streams, const fos_params* params)
         bfail(nullptr, FOS_ERR_INVALID_ARG, why);
         return nullptr;
     }
+    if ((params->methods & FOS_METHOD_GMM) && params->gmm_literal) {
+        bfail(nullptr, FOS_ERR_UNSUPPORTED, "batched launches take the FP32 GMM only (gmm_literal = 0)");
+        return nullptr;
+    }
     fos_batch* b = new fos_batch();
     b->prm = *params;
     b->max_streams = max_streams;

@@ -33,6 +33,22 @@ struct GmmArgs {
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
 
+// The paper-literal GMM (FP64, per-channel variances, density-product
+// decision); plane layout with the kernel in gmm_literal.cu.
+struct GmmLiteralArgs {
+    int64_t P, plane;
+    double* state;          // gmm_literal_planes(Kr, Kd) * plane doubles
+    const uint8_t* rgb;
+    const uint16_t* depth;
+    uint8_t* mask;
+    double alpha, lam2, T_bg, v_init_rgb, v_init_d, v_min_rgb, v_min_d, s, theta;
+    uint32_t depth_fs;
+    int init;
+};
+int gmm_literal_planes(int Kr, int Kd);
+bool gmm_literal_supported(int Kr, int Kd);
+LaunchResult launch_gmm_literal(const GmmLiteralArgs& a, int Kr, int Kd, cudaStream_t s);
+
 // One stream of a batched GMM launch (device memory).
 struct GmmBatchEntry {
     GmmArgs a;

@@ -47,7 +47,9 @@ class Params(ctypes.Structure):
                 ("T_inc", ctypes.c_float), ("T_dec", ctypes.c_float),
                 ("alpha_g", ctypes.c_float), ("eps_d", ctypes.c_float),
                 ("seed", ctypes.c_uint32), ("stream_id", ctypes.c_uint32),
-                ("forced_rng", ctypes.c_int32), ("depth_full_scale_mm", ctypes.c_uint32)]
+                ("forced_rng", ctypes.c_int32), ("depth_full_scale_mm", ctypes.c_uint32),
+                ("gmm_literal", ctypes.c_int32), ("density_scale", ctypes.c_float),
+                ("density_threshold", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -341,7 +343,17 @@ def decode_state(blob: np.ndarray) -> StateView:
     off = ctypes.sizeof(StateHeader)
     P = hdr.width * hdr.height
     gmm = pbas = None
-    if hdr.methods & METHOD_GMM:
+    if hdr.methods & METHOD_GMM and hdr.gmm_bytes == (7 * hdr.K_rgb + 3 * hdr.K_d) * P * 8:
+        # the paper-literal model: doubles, one variance per colour channel
+        Kr, Kd = hdr.K_rgb, hdr.K_d
+        planes = blob[off:off + hdr.gmm_bytes].view(np.float64).reshape(7 * Kr + 3 * Kd, P)
+        off += hdr.gmm_bytes
+        gmm = dict(w_rgb=planes[0:Kr].T,
+                   mu_rgb=np.stack([planes[(1 + c) * Kr:(2 + c) * Kr].T for c in range(3)], axis=2),
+                   v_rgb=np.stack([planes[(4 + c) * Kr:(5 + c) * Kr].T for c in range(3)], axis=2),
+                   w_d=planes[7 * Kr:7 * Kr + Kd].T, mu_d=planes[7 * Kr + Kd:7 * Kr + 2 * Kd].T,
+                   v_d=planes[7 * Kr + 2 * Kd:].T)
+    elif hdr.methods & METHOD_GMM:
         Kr, Kd = hdr.K_rgb, hdr.K_d
         planes = blob[off:off + hdr.gmm_bytes].view(np.float32).reshape(5 * Kr + 3 * Kd, P)
         off += hdr.gmm_bytes
