@@ -261,7 +261,11 @@ fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
 #define FOS_OPT_PBAS_TY 4  /* PBAS tile rows: 2, 4, 8 (2 only with 4 px/thread) */
 #define FOS_OPT_FUSE 5     /* 1 (default): with both methods and K = 3+3, frames >= 1
                               run GMM and PBAS in one fused launch; 0: two launches */
-#define FOS_OPT_COUNT 6
+#define FOS_OPT_TEMPORAL 6 /* 1 (default): fos_process_frames_device with GMM alone (FP32, K = 3+3
+                              or 7+3, equal colour/depth size) runs all its frames in one launch,
+                              each pixel's mixtures kept in registers; 0: one launch per frame.
+                              Same bits either way. */
+#define FOS_OPT_COUNT 7
 
 /* Sets a kernel-shape option; FOS_ERR_INVALID_ARG for unknown options or
  * values, FOS_ERR_UNSUPPORTED for shapes not compiled in. */

@@ -493,6 +493,22 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
     if (!ctx) return FOS_ERR_INVALID_ARG;
     if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
     const int64_t P = ctx->P, Pd = ctx->Pd;
+    const fos_params& p = ctx->prm;
+    if (n_frames > 1 && gmm_on(ctx) && !pbas_on(ctx) && !p.gmm_literal && !ctx->dup &&
+        ctx->opt[FOS_OPT_TEMPORAL] && gmm_frames_supported(p.K_rgb, p.K_d)) {
+        // GMM alone over frames already on the device: one launch for all of them
+        if (!d_rgb || !d_depth || !d_mask_gmm)
+            return fail(ctx, FOS_ERR_INVALID_ARG, "rgb, depth and mask_gmm must be non-NULL");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (ctx->t == 0) FOS_TRY(ctx, cudaMemsetAsync(ctx->aux, 0, 12 * sizeof(unsigned long long), s));
+        GmmArgs a = gmm_args(ctx, d_rgb, d_depth, d_mask_gmm);
+        TimedScope ts(ctx, FOS_KERNEL_GMM, s);
+        fos_status st = launch_result(ctx, launch_gmm_frames(a, n_frames, p.K_rgb, p.K_d, s), "gmm_frames");
+        if (st != FOS_OK) return st;
+        ctx->t += n_frames;
+        ctx->frames_since_counters += uint64_t(n_frames);
+        return FOS_OK;
+    }
     for (int32_t f = 0; f < n_frames; ++f) {
         fos_status st = process_device(ctx, d_rgb + f * P * 3, d_depth + f * Pd,
                                        d_mask_gmm ? d_mask_gmm + f * P : nullptr,
@@ -693,6 +709,7 @@ fos_status fos_set_option(fos_ctx* ctx, int32_t option, int32_t value)
     case FOS_OPT_PBAS_PX: ok = value == 1 || value == 2 || value == 4; break;
     case FOS_OPT_PBAS_TY: ok = value == 2 || value == 4 || value == 8; break;
     case FOS_OPT_FUSE: ok = value == 0 || value == 1; break;
+    case FOS_OPT_TEMPORAL: ok = value == 0 || value == 1; break;
     default: return fail(ctx, FOS_ERR_INVALID_ARG, "unknown option");
     }
     if (!ok) return fail(ctx, FOS_ERR_INVALID_ARG, "option value not supported");

@@ -36,7 +36,7 @@ struct fos_ctx {
     uint32_t* req = nullptr;            // [2][pplane] requests of even / odd frames
     uint64_t* prev = nullptr;           // [pplane]
     bool pending = false;               // requests of the last frame not yet applied
-    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1};  // kernel shapes (fos_set_option)
+    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1, 1};  // kernel shapes (fos_set_option)
     unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
     uint8_t* h_rgb[2] = {nullptr, nullptr};  // device staging for host frames
     uint16_t* h_depth[2] = {nullptr, nullptr};

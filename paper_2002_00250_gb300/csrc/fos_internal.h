@@ -32,6 +32,10 @@ struct GmmArgs {
 };
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
+// n consecutive frames (rgb, depth, mask of frame f at f * P) in one launch,
+// the mixtures held in registers across the frames; same bits as n launches.
+bool gmm_frames_supported(int Kr, int Kd);
+LaunchResult launch_gmm_frames(const GmmArgs& a, int n, int Kr, int Kd, cudaStream_t s);
 
 // The paper-literal GMM (FP64, per-channel variances, density-product
 // decision); plane layout with the kernel in gmm_literal.cu.

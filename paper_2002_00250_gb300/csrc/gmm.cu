@@ -182,4 +182,52 @@ int gmm_batch_blocks_per_sm(int Kr, int Kd, int px)
 
 #undef FOS_GMM_BATCH_CASES
 
+namespace {
+
+// Many frames of one stream in one launch (the frames already in device
+// memory): every pixel's mixtures stay in registers across the frames, so
+// the state is read and written once per launch instead of once per frame
+// and each frame costs only its 5 input bytes and 1 mask byte per pixel.
+// The per-pixel arithmetic is gmm_pixel's, so the results are the bits of
+// frame-by-frame processing.  The next frame's inputs are loaded while the
+// current one is processed.
+constexpr int kFramesThreads = 128;
+
+template <int KR, int KD>
+__global__ void __launch_bounds__(kFramesThreads) gmm_frames_kernel(const GmmArgs a, int n)
+{
+    const int64_t p = int64_t(blockIdx.x) * kFramesThreads + threadIdx.x;
+    if (p >= a.P) return;
+    Mix<KR, 3> mr[1];
+    Mix<KD, 1> md[1];
+    if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md);
+    GmmArgs b = a;
+    uint32_t r = a.rgb[3 * p], g = a.rgb[3 * p + 1], bl = a.rgb[3 * p + 2], d = a.depth[p];
+    for (int f = 0; f < n; ++f) {
+        uint32_t r1 = 0, g1 = 0, b1 = 0, d1 = 0;
+        if (f + 1 < n) {
+            const int64_t q = int64_t(f + 1) * a.P + p;
+            r1 = a.rgb[3 * q]; g1 = a.rgb[3 * q + 1]; b1 = a.rgb[3 * q + 2]; d1 = a.depth[q];
+        }
+        b.init = (f == 0) ? a.init : 0;
+        a.mask[int64_t(f) * a.P + p] = gmm_pixel<KR, KD>(mr[0], md[0], r, g, bl, d, b);
+        r = r1; g = g1; bl = b1; d = d1;
+    }
+    move_state<KR, KD, 1, true>(a.state, a.plane, p, mr, md);
+}
+
+}  // namespace
+
+bool gmm_frames_supported(int Kr, int Kd) { return (Kr == 3 && Kd == 3) || (Kr == 7 && Kd == 3); }
+
+LaunchResult launch_gmm_frames(const GmmArgs& a, int n, int Kr, int Kd, cudaStream_t s)
+{
+    if (a.P == 0 || n <= 0) return kLaunchOk;
+    const unsigned blocks = unsigned((a.P + kFramesThreads - 1) / kFramesThreads);
+    if (Kr == 3 && Kd == 3) gmm_frames_kernel<3, 3><<<blocks, kFramesThreads, 0, s>>>(a, n);
+    else if (Kr == 7 && Kd == 3) gmm_frames_kernel<7, 3><<<blocks, kFramesThreads, 0, s>>>(a, n);
+    else return kLaunchUnsupported;
+    return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+}
+
 }  // namespace fos

@@ -140,3 +140,28 @@ def test_kernel_shapes_give_identical_bits(px, tpb):
     ms, _ = seg.process_host(rgb, depth)
     np.testing.assert_array_equal(ms, mr)
     np.testing.assert_array_equal(seg.get_state(), ref.get_state())
+
+
+@pytest.mark.parametrize("Kr,Kd", [(3, 3), (7, 3)])
+def test_temporal_blocking_same_bits(Kr, Kd):
+    """GMM alone over device frames: all frames in one launch (mixtures kept in
+    registers) gives the bits of one launch per frame, from frame 0 and from
+    the middle of a sequence."""
+    import torch
+    from paper_2002_00250_gb300 import fos
+    W, H, n = 131, 37, 16
+    rgb, depth, _ = scene(W, H, n, seed=44)
+    d_rgb, d_dep = torch.from_numpy(rgb).cuda(), torch.from_numpy(depth).cuda()
+    outs, states = [], []
+    for temporal in (1, 0):
+        seg = fos.Segmenter(W, H, methods=fos.METHOD_GMM, K_rgb=Kr, K_d=Kd)
+        seg.set_option(fos.OPT_TEMPORAL, temporal)
+        m = torch.empty((n, H, W), dtype=torch.uint8, device="cuda")
+        seg.process_device(d_rgb[:5], d_dep[:5], m[:5])          # frames 0..4
+        seg.process_device(d_rgb[5], d_dep[5], m[5])              # one frame
+        seg.process_device(d_rgb[6:], d_dep[6:], m[6:])          # frames 6..15
+        torch.cuda.synchronize()
+        outs.append(m.cpu().numpy())
+        states.append(seg.get_state())
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(states[0], states[1])
