@@ -145,6 +145,12 @@ void fos_destroy(fos_ctx* ctx);
  * on the same context / thread. */
 const char* fos_last_error(const fos_ctx* ctx);
 
+/* Status of the context's last failed call (FOS_OK if none); ctx == NULL
+ * gives the status of the calling thread's last failed fos_create /
+ * fos_create_rgbd (for example FOS_ERR_OOM when device memory ran out, which
+ * the NULL return alone does not tell). */
+fos_status fos_last_status(const fos_ctx* ctx);
+
 /* Restarts the sequence: the next processed frame is frame 0 again. */
 fos_status fos_reset(fos_ctx* ctx);
 

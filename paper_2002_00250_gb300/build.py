@@ -78,7 +78,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if (not os.path.exists(SO) or force or
             any(os.path.getmtime(o) > os.path.getmtime(SO) for o in objs)):
-        cmd = [nvcc(), "-shared", "-o", SO + ".tmp"] + ARCH + objs + ["-Xcompiler", "-fPIC"]
+        # -ldl: the NVTX ranges look their collector up with dlopen
+        cmd = [nvcc(), "-shared", "-o", SO + ".tmp"] + ARCH + objs + ["-Xcompiler", "-fPIC", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

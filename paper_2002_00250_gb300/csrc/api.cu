@@ -10,6 +10,8 @@
 // with the next frame's copy overlapping the current frame's kernels).
 #include <cstdio>
 #include <cstring>
+#include <atomic>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -22,6 +24,7 @@ using namespace fos;
 namespace {
 
 thread_local std::string g_create_error;
+thread_local fos_status g_create_status = FOS_OK;
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
@@ -32,8 +35,13 @@ namespace {
 
 fos_status fail(fos_ctx* c, fos_status st, const std::string& msg)
 {
-    if (c) c->err = msg;
-    else g_create_error = msg;
+    if (c) {
+        c->err = msg;
+        c->last_status = st;
+    } else {
+        g_create_error = msg;
+        g_create_status = st;
+    }
     return st;
 }
 
@@ -268,10 +276,10 @@ fos_status ensure_staging(fos_ctx* c)
 {
     if (c->h_rgb[0]) return FOS_OK;
     for (int b = 0; b < 2; ++b) {
-        FOS_TRY(c, cudaMalloc(&c->h_rgb[b], size_t(c->P) * 3 + 16));
-        FOS_TRY(c, cudaMalloc(&c->h_depth[b], size_t(c->Pd) * 2 + 16));
-        FOS_TRY(c, cudaMalloc(&c->h_mg[b], size_t(c->P) + 16));
-        FOS_TRY(c, cudaMalloc(&c->h_mp[b], size_t(c->P) + 16));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_rgb[b]), size_t(c->P) * 3 + 16));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_depth[b]), size_t(c->Pd) * 2 + 16));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mg[b]), size_t(c->P) + 16));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mp[b]), size_t(c->P) + 16));
         FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
         FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
     }
@@ -346,6 +354,20 @@ void block_samples(const fos_ctx* c, const uint16_t* planes, uint16_t* blocked)
 
 void fos::set_thread_error(const char* msg) { g_create_error = msg; }
 
+cudaError_t fos::dev_alloc(void** p, size_t bytes)
+{
+    static const long long fail_after = [] {
+        const char* v = std::getenv("FOS_FAIL_ALLOC_AFTER");
+        return v ? std::atoll(v) : -1LL;
+    }();
+    static std::atomic<long long> count{0};
+    if (fail_after >= 0 && count.fetch_add(1) >= fail_after) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 GmmArgs fos::ctx_gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mask)
 {
     return gmm_args(c, rgb, depth, mask);
@@ -401,6 +423,7 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
                          const fos_params* params)
 {
     g_create_error.clear();
+    g_create_status = FOS_OK;
     if (width < 1 || height < 1 || width > 16384 || height > 16384 || depth_width < 1 || depth_height < 1 ||
         depth_width > 16384 || depth_height > 16384) {
         fail(nullptr, FOS_ERR_INVALID_ARG, "width, height, depth_width, depth_height must be in 1..16384");
@@ -435,21 +458,21 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
     const size_t pl = size_t(c->plane);
     if (gmm_on(c)) {
         const size_t n = gmm_nplanes(c) * pl * gmm_elem(c);
-        if ((e = cudaMalloc(&c->gmm, n)) != cudaSuccess) return bail("cudaMalloc(gmm)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->gmm), n)) != cudaSuccess) return bail("cudaMalloc(gmm)", e);
     }
     if (pbas_on(c)) {
         const size_t N = size_t(params->N), ns = size_t(c->nseg) * kSeg, pp = size_t(c->pplane);
-        if ((e = cudaMalloc(&c->samp, 4 * N * ns * 2)) != cudaSuccess) return bail("cudaMalloc(samples)", e);
-        if ((e = cudaMalloc(&c->Dq, 4 * N * ns * 2)) != cudaSuccess) return bail("cudaMalloc(D)", e);
-        if ((e = cudaMalloc(&c->R, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(R)", e);
-        if ((e = cudaMalloc(&c->T, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
-        if ((e = cudaMalloc(&c->S, 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
-        if ((e = cudaMalloc(&c->req, 2 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
-        if ((e = cudaMalloc(&c->prev, pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->samp), 4 * N * ns * 2)) != cudaSuccess) return bail("cudaMalloc(samples)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->Dq), 4 * N * ns * 2)) != cudaSuccess) return bail("cudaMalloc(D)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->R), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(R)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->T), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->S), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->req), 2 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
-    if ((e = cudaMalloc(&c->aux, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
+    if ((e = dev_alloc(reinterpret_cast<void**>(&c->aux), 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
     if ((depth_width != width || depth_height != height) &&
-        (e = cudaMalloc(&c->dup, size_t(c->P) * 2 + 16)) != cudaSuccess)
+        (e = dev_alloc(reinterpret_cast<void**>(&c->dup), size_t(c->P) * 2 + 16)) != cudaSuccess)
         return bail("cudaMalloc(resampled depth)", e);
     if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
     return c;
@@ -469,6 +492,11 @@ const char* fos_last_error(const fos_ctx* ctx)
     return ctx ? ctx->err.c_str() : g_create_error.c_str();
 }
 
+fos_status fos_last_status(const fos_ctx* ctx)
+{
+    return ctx ? ctx->last_status : g_create_status;
+}
+
 fos_status fos_reset(fos_ctx* ctx)
 {
     if (!ctx) return FOS_ERR_INVALID_ARG;
@@ -482,6 +510,7 @@ int64_t fos_frame_index(const fos_ctx* ctx) { return ctx ? ctx->t : -1; }
 fos_status fos_process_frame_device(fos_ctx* ctx, const uint8_t* d_rgb, const uint16_t* d_depth,
                                     uint8_t* d_mask_gmm, uint8_t* d_mask_pbas, void* stream)
 {
+    NvtxRange nvtx("fos_process_frame_device");
     if (!ctx) return FOS_ERR_INVALID_ARG;
     return process_device(ctx, d_rgb, d_depth, d_mask_gmm, d_mask_pbas, static_cast<cudaStream_t>(stream));
 }
@@ -490,6 +519,7 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
                                      const uint16_t* d_depth, uint8_t* d_mask_gmm,
                                      uint8_t* d_mask_pbas, void* stream)
 {
+    NvtxRange nvtx("fos_process_frames_device");
     if (!ctx) return FOS_ERR_INVALID_ARG;
     if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
     const int64_t P = ctx->P, Pd = ctx->Pd;
@@ -522,6 +552,7 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
 fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t* rgb,
                                    const uint16_t* depth, uint8_t* mask_gmm, uint8_t* mask_pbas)
 {
+    NvtxRange nvtx("fos_process_frames_host");
     if (!ctx) return FOS_ERR_INVALID_ARG;
     if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
     if (n_frames > 0 && (!rgb || !depth)) return fail(ctx, FOS_ERR_INVALID_ARG, "rgb and depth must be non-NULL");

@@ -245,6 +245,7 @@ fos_status fos_batch_process_device(fos_batch* b, int32_t n, const int32_t* slot
                                     uint8_t* const* d_mask_gmm, uint8_t* const* d_mask_pbas,
                                     void* stream)
 {
+    NvtxRange nvtx("fos_batch_process_device");
     if (!b) return FOS_ERR_INVALID_ARG;
     if (n < 0 || n > b->max_streams) return bfail(b, FOS_ERR_INVALID_ARG, "n out of range");
     if (n == 0) return FOS_OK;

@@ -49,6 +49,7 @@ struct fos_ctx {
     size_t ev_used = 0;
     uint64_t frames_since_counters = 0;
     std::string err;
+    fos_status last_status = FOS_OK;    // status of the last failed call (fos_last_status)
 };
 
 namespace fos {

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace fos {
 
@@ -141,6 +142,22 @@ int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused);
 // Depth frame sw x sh resampled onto dw x dh (nearest, floor mapping).
 LaunchResult launch_depth_resample(const uint16_t* src, int sw, int sh, uint16_t* dst, int dw, int dh,
                                    cudaStream_t s);
+
+// NVTX range over a host call (frame steps, batch ticks, server ticks, the
+// soft-GMM passes), visible on the timeline of a profiler that collects
+// NVTX; costs nothing without one.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Device allocation of the library's long-lived buffers.  The environment
+// variable FOS_FAIL_ALLOC_AFTER=n makes every allocation after the first n
+// of the process fail with cudaErrorMemoryAllocation (host-side fault
+// injection for the error-path tests; unset, it is cudaMalloc).
+cudaError_t dev_alloc(void** p, size_t bytes);
 
 // Sets the text fos_last_error(NULL) returns on the calling thread.
 void set_thread_error(const char* msg);

@@ -107,6 +107,7 @@ SIGNATURES = {
     "fos_depth_resample_device": (_st, [_vp, _i32, _i32, _vp, _i32, _i32, _vp]),
     "fos_destroy": (None, [_vp]),
     "fos_last_error": (ctypes.c_char_p, [_vp]),
+    "fos_last_status": (_st, [_vp]),
     "fos_reset": (_st, [_vp]),
     "fos_frame_index": (_i64, [_vp]),
     "fos_process_frame": (_st, [_vp, _vp, _vp, _vp]),
@@ -172,6 +173,34 @@ def load(path: str = LIB_PATH):
     return _lib
 
 
+def params_from_dict(d: dict) -> Params:
+    """Defaults overridden by the fields present in `d` (field names of
+    fos_params; "lambda" is accepted for lambda_); unknown keys raise."""
+    names = {f for f, _ in Params._fields_}
+    over = {}
+    for k, v in d.items():
+        k2 = "lambda_" if k == "lambda" else k
+        if k2 not in names:
+            raise KeyError(f"unknown parameter {k!r}")
+        over[k2] = v
+    return default_params(**over)
+
+
+def params_from_json(path_or_text: str) -> Params:
+    """Parameters from a JSON object (a file path or the JSON text itself)."""
+    import json
+    text = path_or_text
+    if not path_or_text.lstrip().startswith("{"):
+        with open(path_or_text) as f:
+            text = f.read()
+    return params_from_dict(json.loads(text))
+
+
+def params_to_json(p: Params) -> str:
+    import json
+    return json.dumps(p.as_dict(), sort_keys=True)
+
+
 def default_params(**overrides) -> Params:
     p = Params()
     load().fos_default_params(ctypes.byref(p))
@@ -228,7 +257,7 @@ class Segmenter:
         self.Pd = self.Wd * self.Hd
         h = self.lib.fos_create_rgbd(width, height, self.Wd, self.Hd, ctypes.byref(self.params))
         if not h:
-            raise FosError(1, self.lib.fos_last_error(None).decode())
+            raise FosError(self.lib.fos_last_status(None) or 1, self.lib.fos_last_error(None).decode())
         self.h = h
 
     # -- lifecycle ---------------------------------------------------------

@@ -89,3 +89,17 @@ def test_create_fails_loudly_without_a_device(fos):
         pytest.skip("a GPU is present")
     with pytest.raises(fos.FosError):
         fos.Segmenter(32, 16)
+
+
+def test_params_json_round_trip(tmp_path):
+    from paper_2002_00250_gb300 import fos
+    p = fos.params_from_dict({"alpha": 0.01, "lambda": 3.0, "N": 16, "methods": 2})
+    assert p.N == 16 and p.methods == 2 and abs(p.lambda_ - 3.0) < 1e-7
+    text = fos.params_to_json(p)
+    q = fos.params_from_json(text)
+    assert q.as_dict() == p.as_dict()
+    f = tmp_path / "p.json"
+    f.write_text(text)
+    assert fos.params_from_json(str(f)).as_dict() == p.as_dict()
+    with pytest.raises(KeyError):
+        fos.params_from_dict({"no_such_field": 1})
