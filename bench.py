@@ -103,6 +103,24 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def reduce_max(x: float, ws: int, device) -> float:
+    """Largest x over the ranks (the slowest replica sets the job's time);
+    x itself with one rank."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(work_per_rank: float, ws: int, seconds_max: float) -> float:
+    """Whole-job throughput of independent replicas (weak scaling): every
+    rank's work over the slowest rank's time."""
+    return ws * work_per_rank / seconds_max
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -241,12 +259,9 @@ def run_ours(args):
     counters = seg.get_counters()
     seg.set_timing(0)
 
-    t_max = torch.tensor([ms], device=dev)
-    if ws > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = reduce_max(ms, ws, dev)
     px_frames = ws * args.steps * NFRAMES * P
-    value = px_frames / (ms_max / 1e3) / 1e6
+    value = replica_value(args.steps * NFRAMES * P, ws, ms_max / 1e3) / 1e6
 
     # per-kernel roofline: algorithmic bytes per launch / mean launch time
     peak, peak_src = _peaks()
@@ -304,10 +319,7 @@ def run_ours(args):
     for _ in range(args.steps):
         e2e_step()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([e2e_s], device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = px_frames / float(t.item()) / 1e6
+    e2e_value = replica_value(args.steps * NFRAMES * P, ws, reduce_max(e2e_s, ws, dev)) / 1e6
 
     # per-frame latency: one synchronous host call per frame (pinned buffers)
     lat = []
