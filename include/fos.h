@@ -116,9 +116,11 @@ fos_ctx* fos_create(int32_t width, int32_t height, const fos_params* params);
  * depth_height (1..16384 each) while colour frames are width x height
  * (Sec. 4.3: processing runs at the colour resolution).  Every depth frame
  * passed to this context has the depth size (a frame batch is
- * n * depth_width * depth_height values); each is resampled onto the colour
- * grid as fos_depth_resample_device does before it is used.  With equal
- * sizes this is fos_create.  The batch and serving APIs take equal sizes only.
+ * n * depth_width * depth_height values); the kernels read each colour
+ * pixel's depth through the nearest-neighbour map of fos_depth_resample_device
+ * while they stage their input (no separate pass, no extra buffer).  With
+ * equal sizes this is fos_create.  The batch and serving APIs take equal
+ * sizes only.
  */
 fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int32_t depth_height,
                          const fos_params* params);

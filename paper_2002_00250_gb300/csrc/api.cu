@@ -163,6 +163,7 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     PbasArgs a{};
     const fos_params& p = c->prm;
     a.W = c->W; a.H = c->H; a.P = c->P;
+    a.Wd = c->Wd; a.Hd = c->Hd;
     a.Wp = c->Wp; a.spr = c->spr; a.nseg = c->nseg; a.plane = c->pplane;
     a.rgb = rgb; a.depth = depth; a.mask = mask;
     a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S; a.prev = c->prev;
@@ -197,7 +198,9 @@ GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t*
     a.v_min_rgb = p.v_min_rgb; a.v_min_d = p.v_min_d;
     a.depth_fs = p.depth_full_scale_mm;
     a.init = c->t == 0 ? 1 : 0;
-    a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4);
+    a.W = c->W; a.H = c->H; a.Wd = c->Wd; a.Hd = c->Hd;
+    // the vector path reads depth as it lies in memory: equal sizes only
+    a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4) && c->Wd == c->W && c->Hd == c->H;
     a.px = c->opt[FOS_OPT_GMM_PX];
     a.tpb = c->opt[FOS_OPT_GMM_TPB];
     return a;
@@ -216,11 +219,6 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     if (!rgb || !depth) return fail(c, FOS_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     if (gmm_on(c) && !mg) return fail(c, FOS_ERR_INVALID_ARG, "GMM enabled: mask_gmm must be non-NULL");
     if (pbas_on(c) && !mp) return fail(c, FOS_ERR_INVALID_ARG, "PBAS enabled: mask_pbas must be non-NULL");
-    if (c->dup) {  // depth of another resolution: onto the colour grid first
-        if (launch_depth_resample(depth, c->Wd, c->Hd, c->dup, c->W, c->H, s) != kLaunchOk)
-            return fail(c, FOS_ERR_CUDA, std::string("depth resample: ") + cudaGetErrorString(cudaGetLastError()));
-        depth = c->dup;
-    }
     const bool first = c->t == 0;
     if (first) FOS_TRY(c, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
     if (!first && ctx_fused(c)) {
@@ -246,6 +244,7 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
             a.v_init_rgb = p.v_init_rgb; a.v_init_d = p.v_init_d; a.v_min_rgb = p.v_min_rgb; a.v_min_d = p.v_min_d;
             a.s = p.density_scale; a.theta = p.density_threshold;
             a.depth_fs = p.depth_full_scale_mm; a.init = first ? 1 : 0;
+            a.W = c->W; a.H = c->H; a.Wd = c->Wd; a.Hd = c->Hd;
             st = launch_result(c, launch_gmm_literal(a, p.K_rgb, p.K_d, s), "gmm_literal");
         } else {
             const GmmArgs a = gmm_args(c, rgb, depth, mg);
@@ -310,7 +309,7 @@ size_t pbas_bytes(const fos_ctx* c)
 void free_all(fos_ctx* c)
 {
     cudaFree(c->gmm); cudaFree(c->samp); cudaFree(c->Dq); cudaFree(c->R); cudaFree(c->T);
-    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux); cudaFree(c->dup);
+    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
@@ -471,9 +470,6 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
     if ((e = dev_alloc(reinterpret_cast<void**>(&c->aux), 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
-    if ((depth_width != width || depth_height != height) &&
-        (e = dev_alloc(reinterpret_cast<void**>(&c->dup), size_t(c->P) * 2 + 16)) != cudaSuccess)
-        return bail("cudaMalloc(resampled depth)", e);
     if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
     return c;
 }
@@ -524,7 +520,7 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
     if (n_frames < 0) return fail(ctx, FOS_ERR_INVALID_ARG, "n_frames < 0");
     const int64_t P = ctx->P, Pd = ctx->Pd;
     const fos_params& p = ctx->prm;
-    if (n_frames > 1 && gmm_on(ctx) && !pbas_on(ctx) && !p.gmm_literal && !ctx->dup &&
+    if (n_frames > 1 && gmm_on(ctx) && !pbas_on(ctx) && !p.gmm_literal &&
         ctx->opt[FOS_OPT_TEMPORAL] && gmm_frames_supported(p.K_rgb, p.K_d)) {
         // GMM alone over frames already on the device: one launch for all of them
         if (!d_rgb || !d_depth || !d_mask_gmm)

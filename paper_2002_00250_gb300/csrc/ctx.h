@@ -18,9 +18,8 @@ struct fos_ctx {
     int W = 0, H = 0;
     int64_t P = 0, plane = 0;       // GMM planes: P padded to 128
     int Wp = 0, spr = 0;            // PBAS: row pitch, 128-pixel segments per row
-    int Wd = 0, Hd = 0;             // depth frames (resampled onto W x H when they differ)
+    int Wd = 0, Hd = 0;             // depth frames (read through the resampling map when they differ)
     int64_t Pd = 0;
-    uint16_t* dup = nullptr;        // resampled depth of the current frame (W x H), or NULL
     int64_t nseg = 0, pplane = 0;   // PBAS: segments, plane stride (Wp * H)
     fos_params prm{};
     int64_t t = 0;

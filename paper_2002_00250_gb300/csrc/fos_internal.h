@@ -11,6 +11,16 @@ namespace fos {
 // Launch status of an internal launcher.
 enum LaunchResult { kLaunchOk = 0, kLaunchUnsupported = 1, kLaunchCudaError = 2 };
 
+// Index of the depth reading used for colour pixel (x, y) of a W x H frame
+// when depth frames are Wd x Hd: the same pixel at equal sizes, else the
+// nearest-neighbour source with floor mapping (Sec. 4.3; the resampling that
+// fos_depth_resample_device performs as a separate pass).
+__host__ __device__ inline int64_t depth_index(int x, int y, int W, int H, int Wd, int Hd)
+{
+    if (Wd == W && Hd == H) return int64_t(y) * W + x;
+    return ((int64_t(y) * Hd) / H) * Wd + (int64_t(x) * Wd) / W;
+}
+
 // Plane layout of the GMM state (float32, one plane of `plane` elements each):
 // colour model  w[k]=k, mu_r[k]=Kr+k, mu_g[k]=2Kr+k, mu_b[k]=3Kr+k, v[k]=4Kr+k;
 // depth model   w[k]=5Kr+k, mu[k]=5Kr+Kd+k, v[k]=5Kr+2Kd+k.
@@ -30,6 +40,7 @@ struct GmmArgs {
     int vec_ok;         // 1: pointers aligned for the vectorised path
     int px;             // pixels per thread: 1, 2 or 4
     int tpb;            // threads per block: 64, 128 or 256
+    int W, H, Wd, Hd;   // colour frame; depth frame (resampled on read when it differs)
 };
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
@@ -49,6 +60,7 @@ struct GmmLiteralArgs {
     double alpha, lam2, T_bg, v_init_rgb, v_init_d, v_min_rgb, v_min_d, s, theta;
     uint32_t depth_fs;
     int init;
+    int W, H, Wd, Hd;       // colour frame; depth frame (resampled on read when it differs)
 };
 int gmm_literal_planes(int Kr, int Kd);
 bool gmm_literal_supported(int Kr, int Kd);
@@ -115,6 +127,7 @@ struct PbasArgs {
     int apply;     // 1: requests of frame t-1 are pending
     int px, ty;    // tile shape: pixels per thread (used when W % px == 0), rows
     int mask_vec;  // mask pointer aligned for PX-wide stores
+    int Wd, Hd;    // depth frame size (resampled on staging when it differs from W x H)
 };
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);

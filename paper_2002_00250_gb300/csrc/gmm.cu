@@ -16,6 +16,16 @@ namespace fos {
 namespace {
 using namespace gmmdev;
 
+// Depth reading of colour pixel p (through the resampling map when the depth
+// frame has another size; frame f of a multi-frame call at f * Wd * Hd).
+__device__ __forceinline__ uint32_t depth_at(const GmmArgs& a, int64_t p, int f = 0)
+{
+    const uint16_t* d = a.depth + int64_t(f) * a.Wd * a.Hd;
+    if (a.Wd == a.W && a.Hd == a.H) return d[p];
+    const int y = int(p / a.W), x = int(p - int64_t(y) * a.W);
+    return d[depth_index(x, y, a.W, a.H, a.Wd, a.Hd)];
+}
+
 // PX consecutive pixels per thread starting at pixel p0 of one stream.
 template <int KR, int KD, int PX>
 __device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
@@ -41,7 +51,7 @@ __device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
 #pragma unroll
             for (int j = 0; j < 3 * PX; ++j) rgbb[j] = a.rgb[3 * p0 + j];
 #pragma unroll
-            for (int i = 0; i < PX; ++i) dv[i] = a.depth[p0 + i];
+            for (int i = 0; i < PX; ++i) dv[i] = uint16_t(depth_at(a, p0 + i));
         }
         uint8_t m[PX];
 #pragma unroll
@@ -64,7 +74,7 @@ __device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
         Mix<KD, 1> md[1];
         if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md);
         const uint8_t m = gmm_pixel<KR, KD>(mr[0], md[0], a.rgb[3 * p], a.rgb[3 * p + 1],
-                                            a.rgb[3 * p + 2], a.depth[p], a);
+                                            a.rgb[3 * p + 2], depth_at(a, p), a);
         move_state<KR, KD, 1, true>(a.state, a.plane, p, mr, md);
         a.mask[p] = m;
     }
@@ -202,12 +212,12 @@ __global__ void __launch_bounds__(kFramesThreads) gmm_frames_kernel(const GmmArg
     Mix<KD, 1> md[1];
     if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md);
     GmmArgs b = a;
-    uint32_t r = a.rgb[3 * p], g = a.rgb[3 * p + 1], bl = a.rgb[3 * p + 2], d = a.depth[p];
+    uint32_t r = a.rgb[3 * p], g = a.rgb[3 * p + 1], bl = a.rgb[3 * p + 2], d = depth_at(a, p);
     for (int f = 0; f < n; ++f) {
         uint32_t r1 = 0, g1 = 0, b1 = 0, d1 = 0;
         if (f + 1 < n) {
             const int64_t q = int64_t(f + 1) * a.P + p;
-            r1 = a.rgb[3 * q]; g1 = a.rgb[3 * q + 1]; b1 = a.rgb[3 * q + 2]; d1 = a.depth[q];
+            r1 = a.rgb[3 * q]; g1 = a.rgb[3 * q + 1]; b1 = a.rgb[3 * q + 2]; d1 = depth_at(a, p, f + 1);
         }
         b.init = (f == 0) ? a.init : 0;
         a.mask[int64_t(f) * a.P + p] = gmm_pixel<KR, KD>(mr[0], md[0], r, g, bl, d, b);

@@ -159,7 +159,8 @@ __global__ void __launch_bounds__(kLitThreads) gmm_literal_kernel(const GmmLiter
     const int64_t p = int64_t(blockIdx.x) * kLitThreads + threadIdx.x;
     if (p >= a.P) return;
     const double xr[3] = {double(a.rgb[3 * p]), double(a.rgb[3 * p + 1]), double(a.rgb[3 * p + 2])};
-    const uint32_t d8 = lit_depth_u8(a.depth[p], a.depth_fs);
+    const int y = int(p / a.W), x = int(p - int64_t(y) * a.W);
+    const uint32_t d8 = lit_depth_u8(a.depth[depth_index(x, y, a.W, a.H, a.Wd, a.Hd)], a.depth_fs);
     const double xd[1] = {double(d8)};
     double F;
     {

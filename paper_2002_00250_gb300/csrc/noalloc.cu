@@ -107,6 +107,7 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
     uint8_t* m = static_cast<uint8_t*>(d_model);
     PbasArgs a{};
     a.W = width; a.H = height; a.P = int64_t(width) * height;
+    a.Wd = width; a.Hd = height;
     a.Wp = spr * kSeg; a.spr = spr; a.nseg = int64_t(spr) * height; a.plane = padded;
     a.rgb = d_rgb; a.depth = d_depth; a.mask = d_mask;
     a.samp = reinterpret_cast<uint16_t*>(m);

@@ -65,7 +65,8 @@ __device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, u
         sm[o] = a.rgb[3 * p];
         sm[G::CH + o] = a.rgb[3 * p + 1];
         sm[2 * G::CH + o] = a.rgb[3 * p + 2];
-        sm[3 * G::CH + o] = uint8_t(depth_to_u8(a.depth[p], a.depth_fs));
+        const int64_t pd = depth_index(gx, gy, a.W, a.H, a.Wd, a.Hd);
+        sm[3 * G::CH + o] = uint8_t(depth_to_u8(a.depth[pd], a.depth_fs));
     }
 }
 

@@ -26,30 +26,41 @@ def test_resample_exact(orc, src, dst):
 
 
 @pytest.mark.parametrize("W,H,Wd,Hd", [(96, 54, 64, 36), (67, 45, 50, 30)])
-def test_mixed_resolution_context_equals_resampled_input(orc, W, H, Wd, Hd):
+@pytest.mark.parametrize("kind", ["both", "gmm", "pbas", "gmm_literal"])
+def test_mixed_resolution_context_equals_resampled_input(orc, W, H, Wd, Hd, kind):
+    """Every kernel path (fused, GMM alone including the all-frames launch,
+    PBAS alone, the literal GMM) reads the lower-resolution depth through the
+    resampling map: same bits as a same-size context fed resampled depth."""
     import torch
     from paper_2002_00250_gb300 import fos
+    kw = {"both": {}, "gmm": dict(methods=fos.METHOD_GMM), "pbas": dict(methods=fos.METHOD_PBAS),
+          "gmm_literal": dict(methods=fos.METHOD_GMM, gmm_literal=1)}[kind]
     n = 8
-    rgb, depth_full, _ = scene(W, H, n, seed=11)
-    # a lower-resolution depth sensor: take the depth of a Wd x Hd scene
-    _, depth, _ = scene(Wd, Hd, n, seed=12)
+    rgb, _, _ = scene(W, H, n, seed=11)
+    _, depth, _ = scene(Wd, Hd, n, seed=12)   # a lower-resolution depth sensor
     up = np.stack([orc.depth_resample(depth[t], W, H) for t in range(n)])
-    a = fos.Segmenter(W, H, depth_size=(Wd, Hd), stream_id=3)
-    b = fos.Segmenter(W, H, stream_id=3)
-    ga, pa = a.process_host(rgb, depth)
-    gb, pb = b.process_host(rgb, up)
-    np.testing.assert_array_equal(ga, gb)
-    np.testing.assert_array_equal(pa, pb)
+    a = fos.Segmenter(W, H, depth_size=(Wd, Hd), stream_id=3, **kw)
+    b = fos.Segmenter(W, H, stream_id=3, **kw)
+    ra = a.process_host(rgb, depth)
+    rb = b.process_host(rgb, up)
+    for x, y in zip(ra, rb):
+        if x is not None:
+            np.testing.assert_array_equal(x, y)
     np.testing.assert_array_equal(a.get_state(), b.get_state())
-    # device entry point, continuing the same models
+    # device entry point (several frames per call), continuing the same models
     d_rgb = torch.from_numpy(rgb).cuda()
     d_dep = torch.from_numpy(depth).cuda()
     d_up = torch.from_numpy(up).cuda()
-    mg = [torch.empty((n, H, W), dtype=torch.uint8, device="cuda") for _ in range(4)]
-    a.process_device(d_rgb, d_dep, mg[0], mg[1])
-    b.process_device(d_rgb, d_up, mg[2], mg[3])
+    m = [torch.empty((n, H, W), dtype=torch.uint8, device="cuda") for _ in range(4)]
+    mg_a, mp_a = (m[0] if a.gmm else None), (m[1] if a.pbas else None)
+    mg_b, mp_b = (m[2] if b.gmm else None), (m[3] if b.pbas else None)
+    a.process_device(d_rgb, d_dep, mg_a, mp_a)
+    b.process_device(d_rgb, d_up, mg_b, mp_b)
     torch.cuda.synchronize()
-    assert torch.equal(mg[0], mg[2]) and torch.equal(mg[1], mg[3])
+    if a.gmm:
+        assert torch.equal(m[0], m[2])
+    if a.pbas:
+        assert torch.equal(m[1], m[3])
     np.testing.assert_array_equal(a.get_state(), b.get_state())
 
 
