@@ -18,7 +18,8 @@ enum LaunchResult { kLaunchOk = 0, kLaunchUnsupported = 1, kLaunchCudaError = 2 
 __host__ __device__ inline int64_t depth_index(int x, int y, int W, int H, int Wd, int Hd)
 {
     if (Wd == W && Hd == H) return int64_t(y) * W + x;
-    return ((int64_t(y) * Hd) / H) * Wd + (int64_t(x) * Wd) / W;
+    // sizes up to 16384: the products stay below 2^28, 32-bit arithmetic
+    return int64_t(uint32_t(y * Hd) / uint32_t(H)) * Wd + int64_t(uint32_t(x * Wd) / uint32_t(W));
 }
 
 // Plane layout of the GMM state (float32, one plane of `plane` elements each):

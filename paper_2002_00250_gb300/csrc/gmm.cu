@@ -17,12 +17,12 @@ namespace {
 using namespace gmmdev;
 
 // Depth reading of colour pixel p (through the resampling map when the depth
-// frame has another size; frame f of a multi-frame call at f * Wd * Hd).
-__device__ __forceinline__ uint32_t depth_at(const GmmArgs& a, int64_t p, int f = 0)
+// frame has another size).
+__device__ __forceinline__ uint32_t depth_at(const GmmArgs& a, int64_t p)
 {
-    const uint16_t* d = a.depth + int64_t(f) * a.Wd * a.Hd;
+    const uint16_t* d = a.depth;
     if (a.Wd == a.W && a.Hd == a.H) return d[p];
-    const int y = int(p / a.W), x = int(p - int64_t(y) * a.W);
+    const int y = int(uint32_t(p) / uint32_t(a.W)), x = int(p) - y * a.W;  // P < 2^28
     return d[depth_index(x, y, a.W, a.H, a.Wd, a.Hd)];
 }
 
@@ -212,12 +212,15 @@ __global__ void __launch_bounds__(kFramesThreads) gmm_frames_kernel(const GmmArg
     Mix<KD, 1> md[1];
     if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md);
     GmmArgs b = a;
-    uint32_t r = a.rgb[3 * p], g = a.rgb[3 * p + 1], bl = a.rgb[3 * p + 2], d = depth_at(a, p);
+    // the pixel's depth reading (the same index in every frame) and the depth frame stride
+    const int y = int(uint32_t(p) / uint32_t(a.W)), x = int(p) - y * a.W;
+    const int64_t pd = depth_index(x, y, a.W, a.H, a.Wd, a.Hd), Pd = int64_t(a.Wd) * a.Hd;
+    uint32_t r = a.rgb[3 * p], g = a.rgb[3 * p + 1], bl = a.rgb[3 * p + 2], d = a.depth[pd];
     for (int f = 0; f < n; ++f) {
         uint32_t r1 = 0, g1 = 0, b1 = 0, d1 = 0;
         if (f + 1 < n) {
             const int64_t q = int64_t(f + 1) * a.P + p;
-            r1 = a.rgb[3 * q]; g1 = a.rgb[3 * q + 1]; b1 = a.rgb[3 * q + 2]; d1 = depth_at(a, p, f + 1);
+            r1 = a.rgb[3 * q]; g1 = a.rgb[3 * q + 1]; b1 = a.rgb[3 * q + 2]; d1 = a.depth[int64_t(f + 1) * Pd + pd];
         }
         b.init = (f == 0) ? a.init : 0;
         a.mask[int64_t(f) * a.P + p] = gmm_pixel<KR, KD>(mr[0], md[0], r, g, bl, d, b);

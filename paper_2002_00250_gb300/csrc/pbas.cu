@@ -56,6 +56,9 @@ __device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, u
 {
     using G = Geo<PX, TY>;
     const int tid = threadIdx.y * 32 + threadIdx.x;
+    // depth of another size: the nearest-neighbour source of each colour pixel
+    // (products below 2^28 for sizes up to 16384: 32-bit arithmetic)
+    const bool mapped = a.Wd != a.W || a.Hd != a.H;
     for (int idx = tid; idx < G::SH * G::SW; idx += 32 * TY) {
         const int r = idx / G::SW, col = idx - r * G::SW;
         const int gx = min(max(x0 - 1 + col, 0), a.W - 1);
@@ -65,7 +68,9 @@ __device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, u
         sm[o] = a.rgb[3 * p];
         sm[G::CH + o] = a.rgb[3 * p + 1];
         sm[2 * G::CH + o] = a.rgb[3 * p + 2];
-        const int64_t pd = depth_index(gx, gy, a.W, a.H, a.Wd, a.Hd);
+        const int64_t pd = mapped ? int64_t(uint32_t(gy * a.Hd) / uint32_t(a.H)) * a.Wd +
+                                        int64_t(uint32_t(gx * a.Wd) / uint32_t(a.W))
+                                  : p;
         sm[3 * G::CH + o] = uint8_t(depth_to_u8(a.depth[pd], a.depth_fs));
     }
 }
