@@ -593,7 +593,9 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 }
 
 template <int NT, int PX, int TY>
-__global__ void __launch_bounds__(32 * TY) pbas_classify_kernel(const PbasArgs a)
+// four 256-thread blocks per SM (64 registers): more warps to hide the
+// memory latency than the three an unbounded register count leaves room for
+__global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1) pbas_classify_kernel(const PbasArgs a)
 {
     __shared__ ClassifySmem<PX, TY> S;
     classify_tile<NT, PX, TY>(a, nullptr, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, S, true);
