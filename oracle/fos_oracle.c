@@ -469,14 +469,17 @@ typedef struct {
     int coin1, k1, coin2, j, k2;
 } or_draws;
 
-static or_draws or_pbas_draws(const or_pbas_params* p, int64_t pix, int64_t t, int c, float prob)
+static or_draws or_pbas_draws(const or_pbas_params* p, int W, int64_t pix, int64_t t, int c, float prob)
 {
     or_draws d;
     if (p->forced_rng) {
+        /* mode 1: every pixel the same direction t mod 8; mode 2: east from
+         * columns 0, 1 (mod 4) and west from columns 2, 3, so a pixel can
+         * receive two requests for the same slot (tests the conflict rule) */
         d.coin1 = 1;
         d.coin2 = 1;
         d.k1 = (int)(t % p->N);
-        d.j = (int)(t % 8);
+        d.j = p->forced_rng == 2 ? ((((pix % W) >> 1) & 1) == 0 ? 2 : 6) : (int)(t % 8);
         d.k2 = (int)((t + 1) % p->N);
         return d;
     }
@@ -570,7 +573,7 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
 
                 float Tx = T[i * 4 + c];
                 float prob = 1.0f / Tx;
-                or_draws d = or_pbas_draws(p, i, t, c, prob);
+                or_draws d = or_pbas_draws(p, W, i, t, c, prob);
 
                 if (!fg && d.coin1) {
                     sv[b + d.k1] = (uint8_t)v;
@@ -605,8 +608,27 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
             mask[i] = any_fg ? 255 : 0;
         }
 
+        /* phase 2, spatial propagation: a requested neighbour y takes the
+         * requesting pixel's value; for each slot of y the requests apply in
+         * increasing direction index (the requester at y - dir(j) made request
+         * j), so the highest index wins. */
+        if (p->propagate) {
+            for (int64_t n = 0; n < P; ++n) {
+                const int tx = (int)(n % W), ty = (int)(n / W);
+                for (int c = 0; c < 4; ++c)
+                    for (int j = 0; j < 8; ++j) {
+                        const int rx = tx - OR_DIRX[j], ry = ty - OR_DIRY[j];
+                        if (rx < 0 || rx >= W || ry < 0 || ry >= H) continue;
+                        const int64_t r = (int64_t)ry * W + rx;
+                        if (req_j[r * 4 + c] != j) continue;
+                        const int64_t b = (n * 4 + c) * N + req_k[r * 4 + c];
+                        sv[b] = ch[c * P + r];
+                        sg[b] = gr[c * P + r];
+                    }
+            }
+        }
         /* phase 2: neighbour updates; the neighbour y takes its own current value. */
-        for (int64_t i = 0; i < P; ++i) {
+        for (int64_t i = 0; i < P && !p->propagate; ++i) {
             int x = (int)(i % W), y = (int)(i / W);
             for (int c = 0; c < 4; ++c) {
                 int j = req_j[i * 4 + c];

@@ -178,3 +178,80 @@ def test_seed_and_stream_change_draws(orc):
         outs.append(p.sD.copy())
     assert (outs[0] == outs[1]).all()
     assert (outs[0] != outs[2]).any() and (outs[0] != outs[3]).any()
+
+
+# ---- spatial propagation (neighbour takes the updating pixel's value) ----
+
+def _two_frames(W, H, seed):
+    """A textured frame and the same frame 2 levels brighter: gradients are
+    unchanged, so every pixel stays background and takes its draws, while
+    neighbouring pixels hold different values."""
+    y, x = np.mgrid[0:H, 0:W]
+    f0 = np.stack([60 + (37 * x + 53 * y + 29 * c + 7 * seed) % 120 for c in range(3)], axis=-1).astype(np.uint8)
+    f1 = (f0 + 2).astype(np.uint8)
+    d = (1000 + 113 * x + 271 * y).astype(np.uint16)
+    return f0, f1, d
+
+
+def _channels(orc, rgb, depth):
+    d8 = orc.depth_to_u8(depth)
+    ch = [rgb[..., c] for c in range(3)] + [d8]
+    return [(c_.astype(np.uint8), orc.sobel_grad_u8(c_.astype(np.uint8))) for c_ in ch]
+
+
+def test_propagation_takes_the_requesters_value(orc):
+    """Forced draws at t = 1: every pixel asks its north-east neighbour (slot
+    (t+1) mod N = 0); with propagation that slot gets the asking pixel's
+    frame-1 value and gradient; pixels nobody asks keep their bootstrap value."""
+    W, H, N = 5, 4, 2
+    f0, f1, d = _two_frames(W, H, 1)
+    p = orc.PBAS(W, H, N=N, forced_rng=1, propagate=1)
+    p.step(f0, d)
+    p.step(f1, d)
+    chs = _channels(orc, f1, d)
+    boot = _channels(orc, f0, d)
+    for yy in range(H):
+        for xx in range(W):
+            rx, ry = xx - 1, yy + 1          # the pixel whose NE neighbour this is
+            i = yy * W + xx
+            for c in range(4):
+                if 0 <= rx < W and 0 <= ry < H:
+                    want = (chs[c][0][ry, rx], chs[c][1][ry, rx])
+                else:
+                    want = (boot[c][0][yy, xx], boot[c][1][yy, xx])
+                assert (p.sv[i, c, 0], p.sg[i, c, 0]) == want, (xx, yy, c)
+                # own update (slot t mod N = 1) with its own frame-1 value
+                assert (p.sv[i, c, 1], p.sg[i, c, 1]) == (chs[c][0][yy, xx], chs[c][1][yy, xx])
+
+
+def test_propagation_conflict_highest_direction_wins(orc):
+    """Forced mode 2: columns 0,1 (mod 4) ask east, 2,3 ask west, so columns
+    1 and 2 (mod 4) are asked by both sides for the same slot; the request
+    with the higher direction index (west, 6, from the right) wins.  Without
+    propagation every asked pixel takes its own value."""
+    W, H, N = 9, 3, 2
+    f0, f1, d = _two_frames(W, H, 2)
+    chs = _channels(orc, f1, d)
+    boot = _channels(orc, f0, d)
+    east = lambda x: ((x >> 1) & 1) == 0
+    for prop in (1, 0):
+        p = orc.PBAS(W, H, N=N, forced_rng=2, propagate=prop)
+        p.step(f0, d)
+        p.step(f1, d)
+        for yy in range(H):
+            for u in range(W):
+                from_left = u - 1 >= 0 and east(u - 1)
+                from_right = u + 1 < W and not east(u + 1)
+                if not (from_left or from_right):
+                    src = None
+                elif not prop:
+                    src = u
+                else:
+                    src = u + 1 if from_right else u - 1
+                for c in range(4):
+                    got = (p.sv[yy * W + u, c, 0], p.sg[yy * W + u, c, 0])
+                    if src is None:
+                        want = (boot[c][0][yy, u], boot[c][1][yy, u])
+                    else:
+                        want = (chs[c][0][yy, src], chs[c][1][yy, src])
+                    assert got == want, (prop, u, yy, c)
