@@ -85,7 +85,9 @@ typedef struct fos_params {
     float eps_d;               /* floor of the mean minimal distance */
     uint32_t seed;             /* Philox4x32-10 key word 0 */
     uint32_t stream_id;        /* Philox4x32-10 key word 1 (camera stream) */
-    int32_t forced_rng;        /* 0: Philox; 1: deterministic test draws */
+    int32_t forced_rng;        /* 0: Philox; 1, 2: deterministic test draws (every coin fires,
+                                  own slot t mod N, neighbour slot (t+1) mod N; direction t mod 8,
+                                  or with 2 east from columns 0,1 mod 4 and west from 2,3) */
     /* ---- input conversion (Sec. 4.2) ---- */
     uint32_t depth_full_scale_mm; /* depth mapped onto 1..255, 0 = invalid */
     /* ---- GMM as the paper prints it (Sec. 3.1, Eq. 1) ---- */
@@ -94,6 +96,11 @@ typedef struct fos_params {
                                   0: the FP32 isotropic model with the distance score */
     float density_scale;       /* s (paper: 10000) */
     float density_threshold;   /* background iff the product of the factors >= this */
+    /* ---- PBAS neighbour update variant ---- */
+    int32_t pbas_propagate;    /* 0: a chosen neighbour takes its own value (the base method);
+                                  1: it takes the updating pixel's value (spatial propagation,
+                                  as in ViBe); requests for the same slot apply in increasing
+                                  direction index (N, NE, E, SE, S, SW, W, NW), the last wins */
 } fos_params;
 
 typedef struct fos_ctx fos_ctx;

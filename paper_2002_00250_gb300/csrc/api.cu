@@ -101,6 +101,9 @@ fos_status validate_params(const fos_params* p, std::string& why)
         if (p->N < 1 || p->N > 31 || p->n_min < 1 || p->n_min > p->N) {
             why = "PBAS needs 1 <= n_min <= N <= 31"; return FOS_ERR_INVALID_ARG;
         }
+        if ((p->pbas_propagate != 0 && p->pbas_propagate != 1) || p->forced_rng < 0 || p->forced_rng > 2) {
+            why = "pbas_propagate must be 0 or 1, forced_rng 0..2"; return FOS_ERR_INVALID_ARG;
+        }
         if (!(p->T_lower > 0.f) || !(p->T_upper >= p->T_lower) || !(p->eps_d > 0.f) ||
             !(p->R_lower_rgb > 0.f) || !(p->R_lower_d > 0.f) || !(p->R_incdec >= 0.f && p->R_incdec < 1.f)) {
             why = "PBAS parameter out of range"; return FOS_ERR_INVALID_ARG;
@@ -166,8 +169,16 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     a.Wd = c->Wd; a.Hd = c->Hd;
     a.Wp = c->Wp; a.spr = c->spr; a.nseg = c->nseg; a.plane = c->pplane;
     a.rgb = rgb; a.depth = depth; a.mask = mask;
-    a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S; a.prev = c->prev;
+    a.samp = c->samp; a.Dq = c->Dq; a.R = c->R; a.T = c->T; a.S = c->S;
     const int64_t t = c->t;
+    a.propagate = p.pbas_propagate;
+    if (p.pbas_propagate) {  // planes by frame parity: write frame t, read frame t-1
+        a.prev = c->prev + (t & 1) * c->pplane;
+        a.prev_src = c->prev + ((t + 1) & 1) * c->pplane;
+    } else {
+        a.prev = c->prev;
+        a.prev_src = c->prev;
+    }
     a.req_cur = c->req + (t & 1) * c->pplane;
     a.req_prev = c->req + ((t + 1) & 1) * c->pplane;      // buffer of frame t-1
     a.gsum_prev = c->aux + ((t + 2) % 3) * 4;             // frame t-1
@@ -467,7 +478,10 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->T), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->S), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->req), 2 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
-        if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
+        // with propagation two planes by frame parity: the requesters' values of
+        // frame t-1 are read while frame t's values are written
+        const size_t nprev = params->pbas_propagate ? 2 : 1;
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), nprev * pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
     if ((e = dev_alloc(reinterpret_cast<void**>(&c->aux), 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
     if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);

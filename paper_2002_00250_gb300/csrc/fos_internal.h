@@ -129,6 +129,9 @@ struct PbasArgs {
     int px, ty;    // tile shape: pixels per thread (used when W % px == 0), rows
     int mask_vec;  // mask pointer aligned for PX-wide stores
     int Wd, Hd;    // depth frame size (resampled on staging when it differs from W x H)
+    int propagate;               // 1: a neighbour update writes the requester's value
+    const uint64_t* prev_src;    // values of frame t-1 the pending requests write: the
+                                 // requesters' (propagate; a second plane) or prev itself
 };
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);

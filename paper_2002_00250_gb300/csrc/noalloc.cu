@@ -87,6 +87,9 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
                             "fos_pbas_step_noalloc: frame too large: 128*ceil(width/128)*height "
                             "exceeds FOS_NOALLOC_MAX_PIXELS (2097152)");
     const fos_params& p = *params;
+    if (p.pbas_propagate)
+        return noalloc_fail(FOS_ERR_UNSUPPORTED,
+                            "fos_pbas_step_noalloc: spatial propagation needs a second value plane (not in the scratch)");
     if (p.N < 1 || p.N > 31 || p.n_min < 1 || p.n_min > p.N || !(p.T_lower > 0.f) ||
         !(p.T_upper >= p.T_lower) || !(p.eps_d > 0.f) || p.depth_full_scale_mm == 0)
         return noalloc_fail(FOS_ERR_INVALID_ARG, "fos_pbas_step_noalloc: PBAS parameter out of range");
@@ -108,6 +111,7 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
     PbasArgs a{};
     a.W = width; a.H = height; a.P = int64_t(width) * height;
     a.Wd = width; a.Hd = height;
+    a.propagate = 0;
     a.Wp = spr * kSeg; a.spr = spr; a.nseg = int64_t(spr) * height; a.plane = padded;
     a.rgb = d_rgb; a.depth = d_depth; a.mask = d_mask;
     a.samp = reinterpret_cast<uint16_t*>(m);
@@ -117,6 +121,7 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
     a.S = reinterpret_cast<uint32_t*>(m + 16 * N * padded + 32 * padded);
     unsigned long long* gsum = reinterpret_cast<unsigned long long*>(m + 16 * N * padded + 48 * padded);
     a.prev = reinterpret_cast<uint64_t*>(sc + kReqBytes);
+    a.prev_src = a.prev;
     a.req_cur = reinterpret_cast<uint32_t*>(sc);
     a.req_prev = reinterpret_cast<uint32_t*>(sc);
     const int64_t t = frame_index;

@@ -257,10 +257,10 @@ struct Draws {
 __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c, float prob, int N)
 {
     Draws d;
-    if (a.forced) {
+    if (a.forced) {  // test draws; mode 2: east from columns 0, 1 (mod 4), west from 2, 3
         d.coin1 = d.coin2 = true;
         d.k1 = a.t % uint32_t(N);
-        d.j = a.t % 8u;
+        d.j = a.forced == 2 ? ((((p % uint32_t(a.W)) >> 1) & 1u) == 0u ? 2u : 6u) : a.t % 8u;
         d.k2 = (a.t + 1u) % uint32_t(N);
         return d;
     }
@@ -397,13 +397,18 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             uint32_t mm = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1) : 0u;
-            if (((pw[i] >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;  // depth was invalid
-            while (mm) {
+            // the pixel's own depth of frame t-1 was invalid: no depth write
+            // (with propagation the requester's depth is written, which was valid)
+            if (!a.propagate && ((pw[i] >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;
+            while (mm) {  // increasing bit 4j + c: for one channel, the last direction wins
                 const int b = __ffs(mm) - 1;
                 mm &= mm - 1u;
                 const int j = b >> 2, c = b & 3;
                 const int k = request_slot<G::SW>(sreq, ly, lx0 + i + 1, j, c);
-                a.samp[sidx(a, N, c, k, x + i, y)] = uint16_t(pw[i] >> (16 * c));
+                const uint64_t src = a.propagate
+                    ? a.prev_src[int64_t(y - dir_dy(j)) * a.Wp + (x + i - dir_dx(j))]  // the requester
+                    : pw[i];
+                a.samp[sidx(a, N, c, k, x + i, y)] = uint16_t(src >> (16 * c));
                 cnt7[5] += 1;
             }
         }
@@ -624,15 +629,16 @@ __global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     uint32_t applied[1] = {0};
     if (x < a.W && y < a.H) {
-        const uint64_t pw = a.prev[int64_t(y) * a.Wp + x];
+        const uint64_t pw = a.prev_src[int64_t(y) * a.Wp + x];
         uint32_t mm = request_matches<G::SW>(sreq, threadIdx.y, threadIdx.x + 1);
-        if (((pw >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;  // depth was invalid
+        if (!a.propagate && ((pw >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;  // depth was invalid
         while (mm) {
             const int b = __ffs(mm) - 1;
             mm &= mm - 1u;
             const int j = b >> 2, c = b & 3;
             const int k = request_slot<G::SW>(sreq, threadIdx.y, threadIdx.x + 1, j, c);
-            a.samp[sidx(a, N, c, k, x, y)] = uint16_t(pw >> (16 * c));
+            const uint64_t src = a.propagate ? a.prev_src[int64_t(y - dir_dy(j)) * a.Wp + (x - dir_dx(j))] : pw;
+            a.samp[sidx(a, N, c, k, x, y)] = uint16_t(src >> (16 * c));
             applied[0] += 1;
         }
     }

@@ -26,7 +26,9 @@ def oracle_gmm_params(p):
 
 def oracle_pbas_params(p):
     d = p.as_dict()
-    return {k: d[k] for k in PBAS_KEYS}
+    out = {k: d[k] for k in PBAS_KEYS}
+    out["propagate"] = d["pbas_propagate"]
+    return out
 
 
 def scene(W, H, n, seed=0, **kw):

@@ -139,3 +139,23 @@ def test_fused_gmm_pbas_launch_gives_identical_bits(W, H):
     np.testing.assert_array_equal(ma[0], mb[0])
     np.testing.assert_array_equal(ma[1], mb[1])
     np.testing.assert_array_equal(a.get_state(), b.get_state())
+
+
+# ---- spatial propagation: a neighbour update writes the requester's value ----
+
+@pytest.mark.parametrize("W,H,seed", [(67, 45, 5), (136, 40, 6)])
+def test_propagation_bit_exact(orc, W, H, seed):
+    assert run_parity(orc, W, H, 14, seed=seed, pbas_propagate=1) > 0
+
+
+def test_propagation_pending_requests(orc):
+    """State read every 4th frame: the requests of the frames in between are
+    applied by the next frame's kernel from the second value plane."""
+    run_parity(orc, 64, 40, 13, seed=7, every=4, pbas_propagate=1)
+
+
+@pytest.mark.parametrize("forced", [1, 2])
+def test_propagation_forced_draws(orc, forced):
+    """Forced mode 2 makes pixels receive two requests for the same slot: the
+    kernel must apply the oracle's rule (the highest direction index wins)."""
+    run_parity(orc, 35, 17, 9, seed=8, forced_rng=forced, N=4, pbas_propagate=1)
