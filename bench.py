@@ -623,6 +623,33 @@ def run_table(args):
                  "frac_of_peak": round(moved / (ms * 1e-3) / 1e9 / peak, 3)})
     del rgb, depth, mg
 
+    # PBAS with spatial propagation (the neighbour takes the requester's
+    # value) on the 1280x720 sequence, against the base update, with quality
+    w, h, n = 1280, 720, 300
+    sc = synth.RGBDScene(synth.config_720p(seed=0), device=dev)
+    rgb, depth, gt = sc.sequence(0, n)
+    mp = torch.empty((n, h, w), dtype=torch.uint8, device=dev)
+    prop = {}
+    for label, flag in (("propagation", 1), ("own value", 0)):
+        seg = fos.Segmenter(w, h, methods=fos.METHOD_PBAS, pbas_propagate=flag)
+        for _ in range(args.warmup):
+            seg.reset()
+            seg.process_device(rgb, depth, None, mp)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            seg.reset()
+            seg.process_device(rgb, depth, None, mp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        seg.close()
+        q = fos.quality(fos.quality_counts(mp[1:].contiguous(), gt[1:].contiguous()).cpu().tolist())
+        prop[label] = {"mpx_frames_per_s": round(w * h * n / (ms * 1e-3) / 1e6, 1),
+                       "PWC": round(q["PWC"], 3), "Si": round(q["Si"], 4)}
+    rows.append({"config": f"{w}x{h}x{n}", "method": "PBAS neighbour update", "mpx_frames_per_s": prop})
+    del rgb, depth, gt, mp
+
     # the paper-literal GMM (K = 7 + 3, FP64, per-channel variances, density
     # product decision) on the 1280x720 sequence: throughput, its kernel
     # against HBM (934 B per pixel-frame: 58 doubles read and written, 5 B
