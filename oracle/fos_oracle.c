@@ -475,12 +475,24 @@ static or_draws or_pbas_draws(const or_pbas_params* p, int W, int64_t pix, int64
     if (p->forced_rng) {
         /* mode 1: every pixel the same direction t mod 8; mode 2: east from
          * columns 0, 1 (mod 4) and west from columns 2, 3, so a pixel can
-         * receive two requests for the same slot (tests the conflict rule) */
+         * receive two requests for the same slot (tests the conflict rule);
+         * mode 3: north from even columns, south-east from odd ones, so every
+         * even column is asked from below and from the north-west; pixels of
+         * even rows ask for the slot of their own update (t mod N), odd rows
+         * for (t + 1) mod N */
+        const int64_t col = pix % W, row = pix / W;
         d.coin1 = 1;
         d.coin2 = 1;
         d.k1 = (int)(t % p->N);
-        d.j = p->forced_rng == 2 ? ((((pix % W) >> 1) & 1) == 0 ? 2 : 6) : (int)(t % 8);
         d.k2 = (int)((t + 1) % p->N);
+        if (p->forced_rng == 1) {
+            d.j = (int)(t % 8);
+        } else if (p->forced_rng == 2) {
+            d.j = ((col >> 1) & 1) == 0 ? 2 : 6;
+        } else {
+            d.j = (col & 1) == 0 ? 0 : 3;
+            if ((row & 1) == 0) d.k2 = d.k1;
+        }
         return d;
     }
     uint32_t ctr[4] = {(uint32_t)pix, (uint32_t)t, (uint32_t)c, 0u};
@@ -512,6 +524,7 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
     uint8_t* valid = (uint8_t*)malloc((size_t)P);
     int8_t* req_j = (int8_t*)malloc((size_t)(4 * P));
     int8_t* req_k = (int8_t*)malloc((size_t)(4 * P));
+    int8_t* own_k = (int8_t*)malloc((size_t)(4 * P));   /* slot of this frame's own update */
     for (int64_t i = 0; i < P; ++i) {
         ch[0 * P + i] = rgb[3 * i + 0];
         ch[1 * P + i] = rgb[3 * i + 1];
@@ -556,6 +569,7 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
             for (int c = 0; c < 4; ++c) {
                 req_j[i * 4 + c] = -1;
                 req_k[i * 4 + c] = -1;
+                own_k[i * 4 + c] = -1;
                 if (c == 3 && !valid[i]) continue;
                 int64_t b = (i * 4 + c) * N;
                 int v = ch[c * P + i], g = gr[c * P + i];
@@ -576,6 +590,7 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
                 or_draws d = or_pbas_draws(p, W, i, t, c, prob);
 
                 if (!fg && d.coin1) {
+                    own_k[i * 4 + c] = (int8_t)d.k1;
                     sv[b + d.k1] = (uint8_t)v;
                     sg[b + d.k1] = (uint8_t)g;
                     float q16 = dmin * 16.0f;
@@ -609,22 +624,30 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
         }
 
         /* phase 2, spatial propagation: a requested neighbour y takes the
-         * requesting pixel's value; for each slot of y the requests apply in
-         * increasing direction index (the requester at y - dir(j) made request
-         * j), so the highest index wins. */
+         * requesting pixel's value.  A slot that y's own update of this frame
+         * wrote keeps y's value; the other slots go to the first request met
+         * when y looks at its neighbours in direction order N, NE, ..., NW
+         * (the neighbour r = y + dir(jy) made request j = jy ^ 4, the
+         * opposite direction, if it points at y). */
         if (p->propagate) {
             for (int64_t n = 0; n < P; ++n) {
                 const int tx = (int)(n % W), ty = (int)(n / W);
-                for (int c = 0; c < 4; ++c)
-                    for (int j = 0; j < 8; ++j) {
-                        const int rx = tx - OR_DIRX[j], ry = ty - OR_DIRY[j];
+                for (int c = 0; c < 4; ++c) {
+                    char taken[32] = {0};
+                    if (own_k[n * 4 + c] >= 0) taken[(int)own_k[n * 4 + c]] = 1;
+                    for (int jy = 0; jy < 8; ++jy) {
+                        const int rx = tx + OR_DIRX[jy], ry = ty + OR_DIRY[jy];
                         if (rx < 0 || rx >= W || ry < 0 || ry >= H) continue;
                         const int64_t r = (int64_t)ry * W + rx;
-                        if (req_j[r * 4 + c] != j) continue;
-                        const int64_t b = (n * 4 + c) * N + req_k[r * 4 + c];
+                        if (req_j[r * 4 + c] != (jy ^ 4)) continue;
+                        const int k = req_k[r * 4 + c];
+                        if (taken[k]) continue;
+                        taken[k] = 1;
+                        const int64_t b = (n * 4 + c) * N + k;
                         sv[b] = ch[c * P + r];
                         sg[b] = gr[c * P + r];
                     }
+                }
             }
         }
         /* phase 2: neighbour updates; the neighbour y takes its own current value. */
@@ -655,6 +678,7 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
     free(valid);
     free(req_j);
     free(req_k);
+    free(own_k);
 }
 
 /* ======================================================================== */

@@ -117,13 +117,14 @@ typedef struct {
     float alpha_g;              /* gradient weight numerator */
     float eps_d;                /* floor of the mean minimal distance */
     uint32_t seed, stream_id;   /* Philox key */
-    int forced_rng;             /* 1, 2: test-only deterministic draws (see or_pbas_draws) */
+    int forced_rng;             /* 1..3: test-only deterministic draws (see or_pbas_draws) */
     uint32_t depth_full_scale_mm;
     int propagate;              /* neighbour update: 0 = the neighbour takes its own value
                                    (the base method); 1 = it takes the updating pixel's value
-                                   (spatial propagation as in ViBe); requests for the same
-                                   slot then apply in increasing direction index, so the
-                                   request with the highest index wins */
+                                   (spatial propagation as in ViBe); a slot the pixel's own
+                                   update of the same frame wrote keeps that value, and among
+                                   neighbours asking for the same slot the one with the
+                                   lowest direction index as seen from the pixel wins */
 } or_pbas_params;
 
 /*

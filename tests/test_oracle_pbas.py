@@ -224,11 +224,12 @@ def test_propagation_takes_the_requesters_value(orc):
                 assert (p.sv[i, c, 1], p.sg[i, c, 1]) == (chs[c][0][yy, xx], chs[c][1][yy, xx])
 
 
-def test_propagation_conflict_highest_direction_wins(orc):
+def test_propagation_conflict_east_neighbour_wins(orc):
     """Forced mode 2: columns 0,1 (mod 4) ask east, 2,3 ask west, so columns
-    1 and 2 (mod 4) are asked by both sides for the same slot; the request
-    with the higher direction index (west, 6, from the right) wins.  Without
-    propagation every asked pixel takes its own value."""
+    1 and 2 (mod 4) are asked by both sides for the same slot; seen from the
+    asked pixel the right neighbour lies east (direction 2) and the left one
+    west (6), so the right one wins.  Without propagation every asked pixel
+    takes its own value."""
     W, H, N = 9, 3, 2
     f0, f1, d = _two_frames(W, H, 2)
     chs = _channels(orc, f1, d)
@@ -255,3 +256,39 @@ def test_propagation_conflict_highest_direction_wins(orc):
                     else:
                         want = (chs[c][0][yy, src], chs[c][1][yy, src])
                     assert got == want, (prop, u, yy, c)
+
+
+def test_propagation_own_update_and_lowest_direction_win(orc):
+    """Forced mode 3 at t = 1 (N = 2, own slot 1): even columns ask north,
+    odd ones south-east, so every pixel of an even column is asked from below
+    (direction 4 seen from it) and from the north-west (7).  Requesters on
+    even rows ask for slot 1, the slot of the asked pixel's own update, which
+    keeps the pixel's own value; requesters on odd rows ask for slot 0, which
+    takes the value of the neighbour below where there is one, else of the
+    north-west one.  Without propagation an asked slot 0 takes the pixel's
+    own value."""
+    W, H, N = 8, 6, 2
+    f0, f1, d = _two_frames(W, H, 3)
+    chs = _channels(orc, f1, d)
+    boot = _channels(orc, f0, d)
+    for prop in (1, 0):
+        p = orc.PBAS(W, H, N=N, forced_rng=3, propagate=prop)
+        p.step(f0, d)
+        p.step(f1, d)
+        for v in range(H):
+            for u in range(W):
+                below = u % 2 == 0 and v + 1 < H
+                northwest = u % 2 == 0 and u >= 1 and v >= 1
+                if v % 2 == 1 or not (below or northwest):
+                    src = None                        # slot 0 not asked for
+                elif not prop:
+                    src = (u, v)
+                else:
+                    src = (u, v + 1) if below else (u - 1, v - 1)
+                for c in range(4):
+                    i = v * W + u
+                    want = (boot[c][0][v, u], boot[c][1][v, u]) if src is None else \
+                        (chs[c][0][src[1], src[0]], chs[c][1][src[1], src[0]])
+                    assert (p.sv[i, c, 0], p.sg[i, c, 0]) == want, (prop, u, v, c)
+                    # slot 1: the own update, never overwritten by a neighbour
+                    assert (p.sv[i, c, 1], p.sg[i, c, 1]) == (chs[c][0][v, u], chs[c][1][v, u]), (prop, u, v, c)
