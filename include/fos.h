@@ -85,9 +85,11 @@ typedef struct fos_params {
     float eps_d;               /* floor of the mean minimal distance */
     uint32_t seed;             /* Philox4x32-10 key word 0 */
     uint32_t stream_id;        /* Philox4x32-10 key word 1 (camera stream) */
-    int32_t forced_rng;        /* 0: Philox; 1, 2: deterministic test draws (every coin fires,
-                                  own slot t mod N, neighbour slot (t+1) mod N; direction t mod 8,
-                                  or with 2 east from columns 0,1 mod 4 and west from 2,3) */
+    int32_t forced_rng;        /* 0: Philox; 1..3: deterministic test draws (every coin fires,
+                                  own slot t mod N, neighbour slot (t+1) mod N; direction t mod 8;
+                                  with 2 east from columns 0,1 mod 4 and west from 2,3; with 3
+                                  north from even columns, south-east from odd ones, and pixels
+                                  of even rows ask for slot t mod N) */
     /* ---- input conversion (Sec. 4.2) ---- */
     uint32_t depth_full_scale_mm; /* depth mapped onto 1..255, 0 = invalid */
     /* ---- GMM as the paper prints it (Sec. 3.1, Eq. 1) ---- */
@@ -99,8 +101,10 @@ typedef struct fos_params {
     /* ---- PBAS neighbour update variant ---- */
     int32_t pbas_propagate;    /* 0: a chosen neighbour takes its own value (the base method);
                                   1: it takes the updating pixel's value (spatial propagation,
-                                  as in ViBe); requests for the same slot apply in increasing
-                                  direction index (N, NE, E, SE, S, SW, W, NW), the last wins */
+                                  as in ViBe); a slot the neighbour's own update of the same
+                                  frame wrote keeps that value, and among requests for one
+                                  slot the requester at the lowest direction index seen from
+                                  the neighbour (N, NE, E, SE, S, SW, W, NW) wins */
 } fos_params;
 
 typedef struct fos_ctx fos_ctx;

@@ -101,8 +101,8 @@ fos_status validate_params(const fos_params* p, std::string& why)
         if (p->N < 1 || p->N > 31 || p->n_min < 1 || p->n_min > p->N) {
             why = "PBAS needs 1 <= n_min <= N <= 31"; return FOS_ERR_INVALID_ARG;
         }
-        if ((p->pbas_propagate != 0 && p->pbas_propagate != 1) || p->forced_rng < 0 || p->forced_rng > 2) {
-            why = "pbas_propagate must be 0 or 1, forced_rng 0..2"; return FOS_ERR_INVALID_ARG;
+        if ((p->pbas_propagate != 0 && p->pbas_propagate != 1) || p->forced_rng < 0 || p->forced_rng > 3) {
+            why = "pbas_propagate must be 0 or 1, forced_rng 0..3"; return FOS_ERR_INVALID_ARG;
         }
         if (!(p->T_lower > 0.f) || !(p->T_upper >= p->T_lower) || !(p->eps_d > 0.f) ||
             !(p->R_lower_rgb > 0.f) || !(p->R_lower_d > 0.f) || !(p->R_incdec >= 0.f && p->R_incdec < 1.f)) {
@@ -175,6 +175,7 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     if (p.pbas_propagate) {  // planes by frame parity: write frame t, read frame t-1
         a.prev = c->prev + (t & 1) * c->pplane;
         a.prev_src = c->prev + ((t + 1) & 1) * c->pplane;
+        a.own = reinterpret_cast<uint32_t*>(c->prev + 2 * c->pplane);
     } else {
         a.prev = c->prev;
         a.prev_src = c->prev;
@@ -478,10 +479,11 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->T), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(T)", e);
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->S), 4 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(S)", e);
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->req), 2 * pp * 4)) != cudaSuccess) return bail("cudaMalloc(req)", e);
-        // with propagation two planes by frame parity: the requesters' values of
-        // frame t-1 are read while frame t's values are written
-        const size_t nprev = params->pbas_propagate ? 2 : 1;
-        if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), nprev * pp * 8)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
+        // with propagation two planes by frame parity (the requesters' values of
+        // frame t-1 are read while frame t's values are written) and, behind
+        // them, a uint32 plane with the slots of each pixel's own updates
+        const size_t prev_bytes = params->pbas_propagate ? pp * (2 * 8 + 4) : pp * 8;
+        if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), prev_bytes)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
     if ((e = dev_alloc(reinterpret_cast<void**>(&c->aux), 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
     if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);

@@ -141,7 +141,7 @@ size_t fos_stream_device_bytes(int32_t width, int32_t height, const fos_params* 
     if (p->methods & FOS_METHOD_GMM) bytes += size_t(5 * p->K_rgb + 3 * p->K_d) * plane * 4;
     if (p->methods & FOS_METHOD_PBAS)
         bytes += 2 * 4 * size_t(p->N) * pp * 2 + 3 * 4 * pp * 4 + 2 * pp * 4 +
-                 (p->pbas_propagate ? 2 : 1) * pp * 8;
+                 (p->pbas_propagate ? 2 * 8 + 4 : 8) * pp;
     return bytes;
 }
 

@@ -132,6 +132,8 @@ struct PbasArgs {
     int propagate;               // 1: a neighbour update writes the requester's value
     const uint64_t* prev_src;    // values of frame t-1 the pending requests write: the
                                  // requesters' (propagate; a second plane) or prev itself
+    uint32_t* own;               // [plane] propagate only: byte c = slot of the pixel's own
+                                 // update in channel c of the last frame (0x1F none)
 };
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);

@@ -245,6 +245,54 @@ __device__ __forceinline__ int64_t sidx(const PbasArgs& a, int N, int c, int k, 
     return ((int64_t(c) * a.nseg + seg) * N + k) * kSeg + (x & (kSeg - 1));
 }
 
+// Neighbour updates of frame t-1 into pixel (x, y) (staged at row ly + 1,
+// column col; mm from request_matches), base method: every asked slot takes
+// the pixel's own frame-(t-1) value pw (4 x (value | gradient << 8)); the
+// depth slot only if that depth was valid.  Every writer of a slot writes
+// the same value, so the order does not matter.  Returns the writes made.
+template <int SW>
+__device__ __forceinline__ uint32_t apply_own_value(const PbasArgs& a, int N, const uint32_t* sreq, int ly,
+                                                    int col, int x, int y, uint32_t mm, uint64_t pw)
+{
+    if (((pw >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;
+    uint32_t n = 0;
+    while (mm) {
+        const int b = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        const int j = b >> 2, c = b & 3;
+        const int k = request_slot<SW>(sreq, ly, col, j, c);
+        a.samp[sidx(a, N, c, k, x, y)] = uint16_t(pw >> (16 * c));
+        ++n;
+    }
+    return n;
+}
+
+// Spatial propagation: an asked slot takes the requester's frame-(t-1) value
+// (prev_src at the requester).  A slot the pixel's own update of frame t-1
+// wrote (byte c of `own`, 0x1F for none) keeps it; among requests for the
+// same slot, the requester at the lowest direction index jy seen from this
+// pixel wins (it made request j = jy ^ 4).  Rotating the mask by 16 bits
+// turns bit 4j + c into bit 4jy + c; walking it from the top writes the
+// winner last.  Returns the writes made.
+template <int SW>
+__device__ __forceinline__ uint32_t apply_propagated(const PbasArgs& a, int N, const uint32_t* sreq, int ly,
+                                                     int col, int x, int y, uint32_t mm, uint32_t own)
+{
+    mm = __byte_perm(mm, 0u, 0x1032);
+    uint32_t n = 0;
+    while (mm) {
+        const int b = 31 - __clz(mm);
+        mm &= ~(1u << b);
+        const int j = (b >> 2) ^ 4, c = b & 3;
+        const int k = request_slot<SW>(sreq, ly, col, j, c);
+        if (uint32_t(k) == ((own >> (8 * c)) & 0xFFu)) continue;
+        const uint64_t src = a.prev_src[int64_t(y - dir_dy(j)) * a.Wp + (x - dir_dx(j))];
+        a.samp[sidx(a, N, c, k, x, y)] = uint16_t(src >> (16 * c));
+        ++n;
+    }
+    return n;
+}
+
 struct Draws {
     bool coin1, coin2;
     uint32_t k1, j, k2;
@@ -257,11 +305,19 @@ struct Draws {
 __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c, float prob, int N)
 {
     Draws d;
-    if (a.forced) {  // test draws; mode 2: east from columns 0, 1 (mod 4), west from 2, 3
+    if (a.forced) {  // test draws (see fos_params.forced_rng)
+        const uint32_t col = p % uint32_t(a.W), row = p / uint32_t(a.W);
         d.coin1 = d.coin2 = true;
         d.k1 = a.t % uint32_t(N);
-        d.j = a.forced == 2 ? ((((p % uint32_t(a.W)) >> 1) & 1u) == 0u ? 2u : 6u) : a.t % 8u;
         d.k2 = (a.t + 1u) % uint32_t(N);
+        if (a.forced == 1) {
+            d.j = a.t % 8u;
+        } else if (a.forced == 2) {  // east from columns 0, 1 (mod 4), west from 2, 3
+            d.j = ((col >> 1) & 1u) == 0u ? 2u : 6u;
+        } else {  // north from even columns, south-east from odd; even rows ask for k1
+            d.j = (col & 1u) == 0u ? 0u : 3u;
+            if ((row & 1u) == 0u) d.k2 = d.k1;
+        }
         return d;
     }
     const uint4 u = philox4x32_10(make_uint4(p, a.t, c, 0u), make_uint2(a.seed, a.stream_id));
@@ -370,9 +426,10 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
     const uint32_t pix0 = uint32_t(y) * uint32_t(a.W) + uint32_t(x);  // Philox counter
     const bool vec = (PX > 1) && inb[0];  // W % PX == 0 on this path: all PX in frame
     uint32_t reqw[PX];
+    uint32_t ownw[PX];  // slot of each channel's own update (byte c; 0x1F none), propagation only
     bool anyfg[PX];
 #pragma unroll
-    for (int i = 0; i < PX; ++i) { reqw[i] = kReqNone4; anyfg[i] = false; }
+    for (int i = 0; i < PX; ++i) { reqw[i] = kReqNone4; ownw[i] = kReqNone4; anyfg[i] = false; }
     uint32_t cnt7[7] = {0, 0, 0, 0, 0, 0, 0};  // gsum R,G,B,D; own; neighbour writes; requests
 
     // Neighbour updates of frame t-1: this pixel's own frame-(t-1) value (prev,
@@ -396,20 +453,12 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         }
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
-            uint32_t mm = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1) : 0u;
-            // the pixel's own depth of frame t-1 was invalid: no depth write
-            // (with propagation the requester's depth is written, which was valid)
-            if (!a.propagate && ((pw[i] >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;
-            while (mm) {  // increasing bit 4j + c: for one channel, the last direction wins
-                const int b = __ffs(mm) - 1;
-                mm &= mm - 1u;
-                const int j = b >> 2, c = b & 3;
-                const int k = request_slot<G::SW>(sreq, ly, lx0 + i + 1, j, c);
-                const uint64_t src = a.propagate
-                    ? a.prev_src[int64_t(y - dir_dy(j)) * a.Wp + (x + i - dir_dx(j))]  // the requester
-                    : pw[i];
-                a.samp[sidx(a, N, c, k, x + i, y)] = uint16_t(src >> (16 * c));
-                cnt7[5] += 1;
+            const uint32_t mm = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1) : 0u;
+            if (a.propagate) {
+                cnt7[5] += apply_propagated<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm,
+                                                   mm ? a.own[q0 + i] : kReqNone4);
+            } else {
+                cnt7[5] += apply_own_value<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm, pw[i]);
             }
         }
     }
@@ -528,6 +577,7 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         for (int i = 0; i < PX; ++i) {
             if (slot[i] < 0) continue;
             a.samp[oidx[i]] = uint16_t(pv[i]);
+            ownw[i] = (ownw[i] & ~(0xFFu << (8 * c))) | (uint32_t(slot[i]) << (8 * c));
             const float q16 = __fmul_rn(dmin[i], 16.0f);
             const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
             Sv[i] = Sv[i] + q - dold[i];
@@ -586,10 +636,14 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
     }
     if (vec) {
         stu<PX>(a.req_cur + q0, reqw);
+        if (a.propagate) stu<PX>(a.own + q0, ownw);
     } else {
 #pragma unroll
         for (int i = 0; i < PX; ++i)
-            if (inb[i]) a.req_cur[q0 + i] = reqw[i];
+            if (inb[i]) {
+                a.req_cur[q0 + i] = reqw[i];
+                if (a.propagate) a.own[q0 + i] = ownw[i];
+            }
     }
 
     block_add<TY, 7>(cnt7, [&](int q) {
@@ -629,18 +683,13 @@ __global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     uint32_t applied[1] = {0};
     if (x < a.W && y < a.H) {
-        const uint64_t pw = a.prev_src[int64_t(y) * a.Wp + x];
-        uint32_t mm = request_matches<G::SW>(sreq, threadIdx.y, threadIdx.x + 1);
-        if (!a.propagate && ((pw >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;  // depth was invalid
-        while (mm) {
-            const int b = __ffs(mm) - 1;
-            mm &= mm - 1u;
-            const int j = b >> 2, c = b & 3;
-            const int k = request_slot<G::SW>(sreq, threadIdx.y, threadIdx.x + 1, j, c);
-            const uint64_t src = a.propagate ? a.prev_src[int64_t(y - dir_dy(j)) * a.Wp + (x - dir_dx(j))] : pw;
-            a.samp[sidx(a, N, c, k, x, y)] = uint16_t(src >> (16 * c));
-            applied[0] += 1;
-        }
+        const int64_t q = int64_t(y) * a.Wp + x;
+        const uint32_t mm = request_matches<G::SW>(sreq, threadIdx.y, threadIdx.x + 1);
+        if (a.propagate)
+            applied[0] = apply_propagated<G::SW>(a, N, sreq, threadIdx.y, threadIdx.x + 1, x, y, mm,
+                                                 mm ? a.own[q] : kReqNone4);
+        else
+            applied[0] = apply_own_value<G::SW>(a, N, sreq, threadIdx.y, threadIdx.x + 1, x, y, mm, a.prev_src[q]);
     }
     block_add<TY, 1>(applied, [&](int) { return a.counters + 1; });
 }
@@ -665,6 +714,7 @@ __device__ __forceinline__ void init_tile(const PbasArgs& a, const GmmArgs* gm, 
         const int col = lx0 + i + 1;
         const int64_t q = int64_t(y) * a.Wp + x + i;
         uint64_t pw = 0ull;
+        if (a.propagate) a.own[q] = kReqNone4;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];

@@ -22,13 +22,13 @@ def _frames(sizes, n, seed0=30):
     return out
 
 
-def _run(sizes, n, shape=None, joins=None, leaves=None, autotune=False):
+def _run(sizes, n, shape=None, joins=None, leaves=None, autotune=False, **kw):
     import torch
     from paper_2002_00250_gb300 import fos
     joins = joins or {}
     leaves = leaves or {}
     frames = _frames(sizes, n)
-    b = fos.Batch(len(sizes))
+    b = fos.Batch(len(sizes), **kw)
     if shape:
         b.set_shape(*shape)
     slots = {}
@@ -39,7 +39,7 @@ def _run(sizes, n, shape=None, joins=None, leaves=None, autotune=False):
         for i, (W, H) in enumerate(sizes):
             if i not in slots and joins.get(i, 0) == step:
                 slots[i] = b.add(W, H, stream_id=100 + i)
-                alone[i] = fos.Segmenter(W, H, stream_id=100 + i)
+                alone[i] = fos.Segmenter(W, H, stream_id=100 + i, **kw)
                 t_of[i] = 0
         active = [i for i in slots if leaves.get(i, n + 1) > step]
         if autotune and step == 1:
@@ -95,3 +95,10 @@ def test_streams_join_and_leave():
 
 def test_autotune_keeps_results():
     _run(SIZES, 5, autotune=True)
+
+
+@pytest.mark.parametrize("forced", [0, 3])
+def test_batch_with_propagation(forced):
+    """Spatial propagation in the batched kernel, with the Philox draws and
+    with the conflict-making forced draws; streams join and leave."""
+    _run(SIZES, 6, joins={2: 1}, leaves={0: 4}, pbas_propagate=1, forced_rng=forced, N=4)

@@ -154,8 +154,28 @@ def test_propagation_pending_requests(orc):
     run_parity(orc, 64, 40, 13, seed=7, every=4, pbas_propagate=1)
 
 
-@pytest.mark.parametrize("forced", [1, 2])
-def test_propagation_forced_draws(orc, forced):
-    """Forced mode 2 makes pixels receive two requests for the same slot: the
-    kernel must apply the oracle's rule (the highest direction index wins)."""
-    run_parity(orc, 35, 17, 9, seed=8, forced_rng=forced, N=4, pbas_propagate=1)
+@pytest.mark.parametrize("every", [1, 3])
+@pytest.mark.parametrize("forced", [1, 2, 3])
+def test_propagation_forced_draws(orc, forced, every):
+    """Forced modes 2 and 3 make pixels receive two requests for the same
+    slot, and mode 3 also requests for the slot of the pixel's own update:
+    the kernel must apply the oracle's rule (the own update keeps its slot;
+    the lowest direction index seen from the asked pixel wins), both in the
+    flush before a state read (every frame) and inside the next frame's
+    classify kernel (state read every 3rd frame)."""
+    run_parity(orc, 35, 17, 9, seed=8, every=every, forced_rng=forced, N=4, pbas_propagate=1)
+
+
+@pytest.mark.parametrize("W,H", [(136, 40), (67, 45)])
+def test_propagation_forced_conflicts_fused(orc, W, H):
+    """Both methods in one kernel (the fused path) with the conflict-making
+    draws: the PBAS state still matches the oracle bit for bit."""
+    from paper_2002_00250_gb300 import fos
+    rgb, depth, _ = scene(W, H, 9, seed=9, n_objects=3, hole_fraction=0.05)
+    seg = fos.Segmenter(W, H, forced_rng=3, N=4, pbas_propagate=1)
+    p = orc.PBAS(W, H, **oracle_pbas_params(seg.params))
+    for t in range(9):
+        mo = p.step(rgb[t], depth[t])
+        _, mp = seg.process_host(rgb[t], depth[t])
+        np.testing.assert_array_equal(mp, mo, err_msg=f"mask frame {t}")
+    assert_same(seg.decode_state().pbas, p, 8)
