@@ -77,7 +77,7 @@ class _PbasParams(ctypes.Structure):
                 ("alpha_g", ctypes.c_float), ("eps_d", ctypes.c_float),
                 ("seed", ctypes.c_uint32), ("stream_id", ctypes.c_uint32),
                 ("forced_rng", ctypes.c_int), ("depth_full_scale_mm", ctypes.c_uint32),
-                ("propagate", ctypes.c_int)]
+                ("propagate", ctypes.c_int), ("joint", ctypes.c_int)]
 
 
 def _p(a: np.ndarray):
@@ -119,7 +119,7 @@ GMM_DEFAULTS = dict(K_rgb=3, K_d=3, alpha=0.001, lambda_=2.5, w_depth=0.5, T_bg=
 PBAS_DEFAULTS = dict(N=20, n_min=2, R_lower_rgb=18.0, R_lower_d=4.0, R_scale=5.0,
                      R_incdec=0.05, T_lower=2.0, T_upper=200.0, T_inc=1.0, T_dec=0.05,
                      alpha_g=10.0, eps_d=1.0 / 16.0, seed=0, stream_id=0, forced_rng=0,
-                     depth_full_scale_mm=10000, propagate=0)
+                     depth_full_scale_mm=10000, propagate=0, joint=0)
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

@@ -562,9 +562,76 @@ void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
         const float one_plus_r = 1.0f + p->R_incdec;
         const float n16 = (float)(16 * N);
 
+        /* phase 1, joint-channel variant: one distance per sample over the
+         * active channels, one decision, one draw and one R, T, D per pixel
+         * (kept in channel 0's entries). */
+        const int64_t P_joint = p->joint ? P : 0, P_sep = p->joint ? 0 : P;
+#pragma omp parallel for schedule(static) num_threads(OR_THREADS(nthreads))
+        for (int64_t i = 0; i < P_joint; ++i) {
+            const int nc = valid[i] ? 4 : 3;
+            const float inv_nc = 1.0f / (float)nc;
+            for (int c = 0; c < 4; ++c) {
+                req_j[i * 4 + c] = -1;
+                req_k[i * 4 + c] = -1;
+                own_k[i * 4 + c] = -1;
+            }
+            float Rx = R[i * 4];
+            int count = 0;
+            float dmin = INFINITY;
+            for (int k = 0; k < N; ++k) {
+                float sum = 0.0f;
+                for (int c = 0; c < nc; ++c) {
+                    int64_t b = (i * 4 + c) * N + k;
+                    float a = wg[c] * (float)abs((int)gr[c * P + i] - (int)sg[b]);
+                    float dist_c = a + (float)abs((int)ch[c * P + i] - (int)sv[b]);
+                    sum = sum + dist_c;
+                }
+                float dist = sum * inv_nc;
+                if (dist < Rx) ++count;
+                if (dist < dmin) dmin = dist;
+            }
+            int fg = count < p->n_min;
+            float Tx = T[i * 4];
+            or_draws d = or_pbas_draws(p, W, i, t, 0, 1.0f / Tx);
+            if (!fg && d.coin1) {
+                for (int c = 0; c < nc; ++c) {
+                    int64_t b = (i * 4 + c) * N + d.k1;
+                    sv[b] = ch[c * P + i];
+                    sg[b] = gr[c * P + i];
+                    own_k[i * 4 + c] = (int8_t)d.k1;
+                }
+                float q16 = dmin * 16.0f;
+                uint32_t q = q16 >= 65535.0f ? 65535u : (uint32_t)rintf(q16);
+                S[i * 4] = S[i * 4] + q - sD[i * 4 * N + d.k1];
+                sD[i * 4 * N + d.k1] = (uint16_t)q;
+            }
+            float dbar = (float)S[i * 4] / n16;
+            if (dbar < p->eps_d) dbar = p->eps_d;
+            float Rs = dbar * p->R_scale;
+            Rx = Rx > Rs ? Rx * one_minus_r : Rx * one_plus_r;
+            if (Rx < p->R_lower_rgb) Rx = p->R_lower_rgb;
+            R[i * 4] = Rx;
+            if (fg) Tx = Tx + p->T_inc / dbar;
+            else Tx = Tx - p->T_dec / dbar;
+            if (Tx < p->T_lower) Tx = p->T_lower;
+            if (Tx > p->T_upper) Tx = p->T_upper;
+            T[i * 4] = Tx;
+            if (!fg && d.coin2) {
+                /* the whole sample: all four channels (phase 2 writes the
+                 * asked pixel's depth only where it is valid); with
+                 * propagation the requester's active channels */
+                const int nreq = p->propagate ? nc : 4;
+                for (int c = 0; c < nreq; ++c) {
+                    req_j[i * 4 + c] = (int8_t)d.j;
+                    req_k[i * 4 + c] = (int8_t)d.k2;
+                }
+            }
+            mask[i] = fg ? 255 : 0;
+        }
+
         /* phase 1: classify every pixel and update its own model. */
 #pragma omp parallel for schedule(static) num_threads(OR_THREADS(nthreads))
-        for (int64_t i = 0; i < P; ++i) {
+        for (int64_t i = 0; i < P_sep; ++i) {
             int any_fg = 0;
             for (int c = 0; c < 4; ++c) {
                 req_j[i * 4 + c] = -1;

@@ -125,6 +125,11 @@ typedef struct {
                                    update of the same frame wrote keeps that value, and among
                                    neighbours asking for the same slot the one with the
                                    lowest direction index as seen from the pixel wins */
+    int joint;                  /* 0: each channel has its own R, T, D and decision (the
+                                   base method; foreground if any channel is); 1: one R, T,
+                                   D per pixel (channel 0's entries) and one decision on the
+                                   joint distance over the active channels (see
+                                   or_pbas_frame) */
 } or_pbas_params;
 
 /*
@@ -133,6 +138,17 @@ typedef struct {
  * minimal distance x16); R[p*4+c], T[p*4+c] (float), S[p*4+c] (u32, sum of
  * the N D values).  gsum[4] holds the gradient sums of the previous frame
  * (read at t >= 1, rewritten every frame).
+ *
+ * Joint-channel variant (p->joint): the active channels A of a pixel are R,
+ * G, B, and D where the depth reading is valid; n = |A|.  The distance of
+ * sample k is the mean over A of the per-channel distances: the FP32 sum of
+ * fl(fl(wg_c |dg|) + |dv|) in channel order, times fl(1/n).  One decision
+ * per pixel (fewer than #min samples within R: foreground), one draw per
+ * pixel (channel word 0 of the counter), and the pixel's R, T, S and D are
+ * those of channel 0 (R floor R_lower_rgb); the entries of channels 1..3
+ * keep their bootstrap values.  The own update writes every channel of A
+ * into the slot; a neighbour request covers all four channels (with
+ * propagation, the requester's active ones).
  */
 void or_pbas_frame(const or_pbas_params* p, int W, int H, int64_t t,
                    const uint8_t* rgb, const uint16_t* depth,
