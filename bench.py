@@ -131,13 +131,12 @@ def _traffic_for(kernel: str, pixels: int):
     """DRAM bytes per launch from the committed ncu summary, if it still
     describes the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_1280x720.md")
-    src = os.path.join(ROOT, "paper_2002_00250_gb300", "csrc",
-                       "gmm.cu" if kernel == "gmm_step" else "pbas.cu")
-    if kernel == "fused_classify":  # the fused kernel also compiles the GMM device code
-        src = [src, os.path.join(ROOT, "paper_2002_00250_gb300", "csrc", "gmm_dev.cuh")]
+    files = {"gmm_step": ["gmm.cu", "gmm_dev.cuh"], "pbas_classify": ["pbas.cu", "pbas_dev.cuh"],
+             # the fused kernel also compiles the GMM device code
+             "fused_classify": ["pbas.cu", "pbas_dev.cuh", "gmm_dev.cuh"]}.get(kernel, [])
+    srcs = [os.path.join(ROOT, "paper_2002_00250_gb300", "csrc", f) for f in files]
     try:
         txt = open(path).read()
-        srcs = src if isinstance(src, list) else [src]
         sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         fields = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes_per_pixel:", "source_sha:")))
         if fields.get("source_sha", "").strip() != sha:
@@ -648,7 +647,59 @@ def run_table(args):
         prop[label] = {"mpx_frames_per_s": round(w * h * n / (ms * 1e-3) / 1e6, 1),
                        "PWC": round(q["PWC"], 3), "Si": round(q["Si"], 4)}
     rows.append({"config": f"{w}x{h}x{n}", "method": "PBAS neighbour update", "mpx_frames_per_s": prop})
-    del rgb, depth, gt, mp
+
+    # joint-channel PBAS (one R, T, D per pixel, one decision on the mean
+    # distance over the active channels) against the per-channel base method;
+    # its dense bytes per pixel-frame: 160 B samples + 12 B R, T, S read + 8 B
+    # R, T written + 5 B input + 1 B mask = 186 B
+    joint = {}
+    for label, flag in (("joint channels", 1), ("per channel", 0)):
+        seg = fos.Segmenter(w, h, methods=fos.METHOD_PBAS, pbas_joint=flag)
+        for _ in range(args.warmup):
+            seg.reset()
+            seg.process_device(rgb, depth, None, mp)
+        torch.cuda.synchronize()
+        seg.get_timing()
+        seg.set_timing(1 << fos.KERNEL_PBAS_CLASSIFY)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            seg.reset()
+            seg.process_device(rgb, depth, None, mp)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        tm = seg.get_timing()["pbas_classify"]
+        seg.set_timing(0)
+        seg.close()
+        avg_us = tm[1] / max(1, tm[0]) * 1e3
+        dense = (186.0 if flag else ALGO_BYTES["pbas_classify"]) * w * h
+        q = fos.quality(fos.quality_counts(mp[1:].contiguous(), gt[1:].contiguous()).cpu().tolist())
+        joint[label] = {"mpx_frames_per_s": round(w * h * n / (ms * 1e-3) / 1e6, 1),
+                        "kernel_avg_us": round(avg_us, 2),
+                        "dense_GBps": round(dense / (avg_us * 1e-6) / 1e9, 1),
+                        "dense_frac": round(dense / (avg_us * 1e-6) / 1e9 / peak, 3),
+                        "PWC": round(q["PWC"], 3), "Si": round(q["Si"], 4)}
+    rows.append({"config": f"{w}x{h}x{n}", "method": "PBAS channel coupling", "mpx_frames_per_s": joint,
+                 "note": "dense bytes only (sparse own/neighbour writes not counted)"})
+
+    # colour alone against colour + depth (Sec. 5 compares GMM, GMM+RGBD,
+    # PBAS, PBAS+RGBD): colour alone is the same run with every depth reading
+    # invalid (0), which both methods treat as absent
+    no_depth = torch.zeros_like(depth)
+    cmp_ = {}
+    mg = torch.empty_like(mp)
+    for label, dep in (("RGB", no_depth), ("RGB-D", depth)):
+        seg = fos.Segmenter(w, h)
+        seg.process_device(rgb, dep, mg, mp)
+        torch.cuda.synchronize()
+        seg.close()
+        for name, m in (("GMM", mg), ("PBAS", mp)):
+            q = fos.quality(fos.quality_counts(m[1:].contiguous(), gt[1:].contiguous()).cpu().tolist())
+            cmp_[f"{name} {label}"] = {k: round(q[k], 4) for k in ("PWC", "FNR", "FPR", "Si")}
+    rows.append({"config": f"{w}x{h}x{n}", "method": "quality, colour alone vs colour + depth",
+                 "quality": cmp_})
+    del rgb, depth, gt, mp, mg, no_depth
 
     # the paper-literal GMM (K = 7 + 3, FP64, per-channel variances, density
     # product decision) on the 1280x720 sequence: throughput, its kernel

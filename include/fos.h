@@ -105,6 +105,16 @@ typedef struct fos_params {
                                   frame wrote keeps that value, and among requests for one
                                   slot the requester at the lowest direction index seen from
                                   the neighbour (N, NE, E, SE, S, SW, W, NW) wins */
+    /* ---- PBAS channel coupling variant ---- */
+    int32_t pbas_joint;        /* 0: every channel has its own R, T, D and decision, foreground
+                                  if any channel is (the base method); 1: one R, T, D per pixel
+                                  and one decision on the mean of the per-channel distances
+                                  over the active channels (R, G, B, and depth where valid),
+                                  computed as their FP32 sum in channel order times fl(1/n);
+                                  one draw per pixel; updates write whole samples; R, T, S
+                                  and D are kept in channel 0's entries of the state, the
+                                  other channels' entries keep their bootstrap values.
+                                  Not available in batches or the no-alloc entry point. */
 } fos_params;
 
 typedef struct fos_ctx fos_ctx;

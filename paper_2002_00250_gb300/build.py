@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                  "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 # PBAS arithmetic must round every operation once (bit-exact contract).
-PER_FILE = {"pbas.cu": ["--fmad=false"]}
+PER_FILE = {"pbas.cu": ["--fmad=false"], "pbas_joint.cu": ["--fmad=false"]}
 
 
 def nvcc() -> str:

@@ -101,8 +101,9 @@ fos_status validate_params(const fos_params* p, std::string& why)
         if (p->N < 1 || p->N > 31 || p->n_min < 1 || p->n_min > p->N) {
             why = "PBAS needs 1 <= n_min <= N <= 31"; return FOS_ERR_INVALID_ARG;
         }
-        if ((p->pbas_propagate != 0 && p->pbas_propagate != 1) || p->forced_rng < 0 || p->forced_rng > 3) {
-            why = "pbas_propagate must be 0 or 1, forced_rng 0..3"; return FOS_ERR_INVALID_ARG;
+        if ((p->pbas_propagate != 0 && p->pbas_propagate != 1) || (p->pbas_joint != 0 && p->pbas_joint != 1) ||
+            p->forced_rng < 0 || p->forced_rng > 3) {
+            why = "pbas_propagate and pbas_joint must be 0 or 1, forced_rng 0..3"; return FOS_ERR_INVALID_ARG;
         }
         if (!(p->T_lower > 0.f) || !(p->T_upper >= p->T_lower) || !(p->eps_d > 0.f) ||
             !(p->R_lower_rgb > 0.f) || !(p->R_lower_d > 0.f) || !(p->R_incdec >= 0.f && p->R_incdec < 1.f)) {
@@ -221,8 +222,8 @@ GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t*
 // GMM and PBAS of a frame in one launch: both methods, the 3+3 model, option on.
 bool ctx_fused(const fos_ctx* c)
 {
-    return gmm_on(c) && pbas_on(c) && !c->prm.gmm_literal && c->prm.K_rgb == 3 && c->prm.K_d == 3 &&
-           c->opt[FOS_OPT_FUSE] != 0;
+    return gmm_on(c) && pbas_on(c) && !c->prm.gmm_literal && !c->prm.pbas_joint && c->prm.K_rgb == 3 &&
+           c->prm.K_d == 3 && c->opt[FOS_OPT_FUSE] != 0;
 }
 
 fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t* mg,
@@ -273,7 +274,8 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
             c->pending = false;
         } else {
             TimedScope ts(c, FOS_KERNEL_PBAS_CLASSIFY, s);
-            fos_status st = launch_result(c, launch_pbas_classify(a, s), "pbas_classify");
+            fos_status st = c->prm.pbas_joint ? launch_result(c, launch_pbas_joint(a, s), "pbas_joint")
+                                              : launch_result(c, launch_pbas_classify(a, s), "pbas_classify");
             if (st != FOS_OK) return st;
             c->pending = true;
         }

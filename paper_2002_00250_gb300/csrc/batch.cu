@@ -160,6 +160,10 @@ fos_batch* fos_batch_create(int32_t max_streams, const fos_params* params)
         bfail(nullptr, FOS_ERR_UNSUPPORTED, "batched launches take the FP32 GMM only (gmm_literal = 0)");
         return nullptr;
     }
+    if ((params->methods & FOS_METHOD_PBAS) && params->pbas_joint) {
+        bfail(nullptr, FOS_ERR_UNSUPPORTED, "batched launches take the per-channel PBAS only (pbas_joint = 0)");
+        return nullptr;
+    }
     fos_batch* b = new fos_batch();
     b->prm = *params;
     b->max_streams = max_streams;

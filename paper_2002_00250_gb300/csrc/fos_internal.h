@@ -139,6 +139,8 @@ struct PbasArgs {
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);
+// Joint-channel variant of the classify pass (pbas_joint.cu).
+LaunchResult launch_pbas_joint(const PbasArgs& a, cudaStream_t s);
 
 // GMM (3+3 components) and PBAS of one frame in one launch (frames >= 1).
 LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStream_t s);

@@ -90,6 +90,8 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
     if (p.pbas_propagate)
         return noalloc_fail(FOS_ERR_UNSUPPORTED,
                             "fos_pbas_step_noalloc: spatial propagation needs a second value plane (not in the scratch)");
+    if (p.pbas_joint)
+        return noalloc_fail(FOS_ERR_UNSUPPORTED, "fos_pbas_step_noalloc: the per-channel PBAS only (pbas_joint = 0)");
     if (p.N < 1 || p.N > 31 || p.n_min < 1 || p.n_min > p.N || !(p.T_lower > 0.f) ||
         !(p.T_upper >= p.T_lower) || !(p.eps_d > 0.f) || p.depth_full_scale_mm == 0)
         return noalloc_fail(FOS_ERR_INVALID_ARG, "fos_pbas_step_noalloc: PBAS parameter out of range");

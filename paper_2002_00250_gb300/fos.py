@@ -49,7 +49,8 @@ class Params(ctypes.Structure):
                 ("seed", ctypes.c_uint32), ("stream_id", ctypes.c_uint32),
                 ("forced_rng", ctypes.c_int32), ("depth_full_scale_mm", ctypes.c_uint32),
                 ("gmm_literal", ctypes.c_int32), ("density_scale", ctypes.c_float),
-                ("density_threshold", ctypes.c_float), ("pbas_propagate", ctypes.c_int32)]
+                ("density_threshold", ctypes.c_float), ("pbas_propagate", ctypes.c_int32),
+                ("pbas_joint", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

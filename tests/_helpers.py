@@ -28,6 +28,7 @@ def oracle_pbas_params(p):
     d = p.as_dict()
     out = {k: d[k] for k in PBAS_KEYS}
     out["propagate"] = d["pbas_propagate"]
+    out["joint"] = d["pbas_joint"]
     return out
 
 
