@@ -57,64 +57,66 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
     const int64_t q0 = int64_t(y) * a.Wp + x;
     const uint32_t pix0 = uint32_t(y) * uint32_t(a.W) + uint32_t(x);
     const bool vec = (PX > 1) && inb[0];  // W % PX == 0 on this path
-    uint32_t cnt7[7] = {0, 0, 0, 0, 0, 0, 0};  // gsum R,G,B,D; own; neighbour writes; requests
+    uint32_t cnt5[5] = {0, 0, 0, 0, 0};  // gsum R,G,B,D; neighbour writes
+    uint32_t cnt2[2] = {0, 0};           // own-update sample writes; requests
+
+    // R, and the words the neighbour updates need, are loaded before any of
+    // this thread's stores (a load behind scattered stores waits for them)
+    float Rv[PX];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) Rv[i] = 0.f;
+    if (vec) {
+        ldf<PX>(a.R + q0, Rv);
+    } else {
+#pragma unroll
+        for (int i = 0; i < PX; ++i) Rv[i] = inb[i] ? a.R[q0 + i] : 0.f;
+    }
 
     // neighbour updates requested during frame t-1 (whole samples)
     if (a.apply) {
+        uint32_t mm[PX];
+        uint64_t pw[PX];
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
-            if (!inb[i]) continue;
-            const uint32_t mm = request_matches<G::SW>(sreq, ly, lx0 + i + 1);
+            mm[i] = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1) : 0u;
+            // base method: the pixel's own value; propagation: its own-slot word
+            pw[i] = mm[i] ? (a.propagate ? uint64_t(a.own[q0 + i]) : a.prev[q0 + i]) : 0ull;
+        }
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if (!mm[i]) continue;
             if (a.propagate)
-                cnt7[5] += apply_propagated<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm,
-                                                   mm ? a.own[q0 + i] : kReqNone4);
-            else if (mm)
-                cnt7[5] += apply_own_value<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm, a.prev[q0 + i]);
+                cnt5[4] += apply_propagated<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm[i], uint32_t(pw[i]));
+            else
+                cnt5[4] += apply_own_value<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm[i], pw[i]);
         }
     }
 
-    // this frame's features: (value | gradient << 8) per channel and pixel
-    uint32_t pv[4][PX];
+    // this frame's features: (value | gradient << 8) per channel and pixel,
+    // pixel i in half i & 1 of word own[c][i >> 1] (the only copy kept live
+    // through the distance loop, so that registers go to loads in flight)
+    uint32_t own[4][NW];
     bool dval[PX];
-    uint64_t pnew[PX];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int w = 0; w < NW; ++w) own[c][w] = 0u;
 #pragma unroll
     for (int i = 0; i < PX; ++i) {
         const int col = lx0 + i + 1;
-        pnew[i] = 0ull;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
             const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
-            pv[c][i] = v | (g << 8);
-            if (inb[i]) cnt7[c] += g;
-            pnew[i] |= uint64_t(pv[c][i]) << (16 * c);
+            own[c][i >> 1] |= (v | (g << 8)) << (16 * (i & 1));
+            if (inb[i]) cnt5[c] += g;
         }
         dval[i] = inb[i] && sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0;
     }
+    block_add<TY, 5>(cnt5, [&](int q) { return q < 4 ? a.gsum_cur + q : a.counters + 1; });
 
     if (inb[0]) {
-        float Rv[PX], Tv[PX];
-        uint32_t Sv[PX];
-        if (vec) {
-            ldf<PX>(a.R + q0, Rv);
-            ldf<PX>(a.T + q0, Tv);
-            ldu<PX>(a.S + q0, Sv);
-        } else {
-#pragma unroll
-            for (int i = 0; i < PX; ++i) {
-                Rv[i] = inb[i] ? a.R[q0 + i] : 0.f;
-                Tv[i] = inb[i] ? a.T[q0 + i] : 1.f;
-                Sv[i] = inb[i] ? a.S[q0 + i] : 0u;
-            }
-        }
-
         // joint distances to the N samples: count within R, minimum
-        uint32_t own[4][NW];
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int w = 0; w < NW; ++w)
-                own[c][w] = pv[c][2 * w] | (2 * w + 1 < PX ? pv[c][2 * w + 1] << 16 : 0u);
         float inv[PX];
         int cnt[PX];
         float dmin[PX];
@@ -156,44 +158,84 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
             }
         }
 
+        float Tv[PX];
+        uint32_t Sv[PX];
+        if (vec) {
+            ldf<PX>(a.T + q0, Tv);
+            ldu<PX>(a.S + q0, Sv);
+        } else {
+#pragma unroll
+            for (int i = 0; i < PX; ++i) {
+                Tv[i] = inb[i] ? a.T[q0 + i] : 1.f;
+                Sv[i] = inb[i] ? a.S[q0 + i] : 0u;
+            }
+        }
+        uint32_t pv[4][PX];
+        uint64_t pnew[PX];
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            pnew[i] = 0ull;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                pv[c][i] = (own[c][i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                pnew[i] |= uint64_t(pv[c][i]) << (16 * c);
+            }
+        }
         const float omr = __fsub_rn(1.0f, a.R_incdec), opr = __fadd_rn(1.0f, a.R_incdec);
         const float n16 = __int2float_rn(16 * N);
+        // decisions and draws, then every D read before any store: a load
+        // issued behind this thread's scattered sample stores waits for them
         uint32_t reqw[PX], ownw[PX];
         uint8_t mk[PX];
+        int slot[PX];
+        int64_t di[PX];
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             reqw[i] = kReqNone4;
             ownw[i] = kReqNone4;
             mk[i] = 0;
+            slot[i] = -1;
+            di[i] = 0;
             if (!inb[i]) continue;
             const bool fg = cnt[i] < a.n_min;
             mk[i] = fg ? 255 : 0;
-            if (!fg) {
-                const Draws d = draws(a, pix0 + uint32_t(i), 0u, __frcp_rn(Tv[i]), N);
-                const int nc = dval[i] ? 4 : 3;
-                if (d.coin1) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (c >= nc) break;
-                        a.samp[sidx(a, N, c, int(d.k1), x + i, y)] = uint16_t(pv[c][i]);
-                        ownw[i] = (ownw[i] & ~(0xFFu << (8 * c))) | (d.k1 << (8 * c));
-                    }
-                    const int64_t di = sidx(a, N, 0, int(d.k1), x + i, y);
-                    const float q16 = __fmul_rn(dmin[i], 16.0f);
-                    const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
-                    Sv[i] = Sv[i] + q - uint32_t(a.Dq[di]);
-                    a.Dq[di] = uint16_t(q);
-                    cnt7[4] += uint32_t(nc);
-                }
-                if (d.coin2) {
-                    // the whole sample; with propagation only the requester's active channels
-                    const uint32_t byte = (d.j << 5) | d.k2;
-                    reqw[i] = byte * 0x01010101u;
-                    if (a.propagate && !dval[i]) reqw[i] = (reqw[i] & 0x00FFFFFFu) | 0x1F000000u;
-                    cnt7[6] += 1;
-                }
+            if (fg) continue;
+            const Draws d = draws(a, pix0 + uint32_t(i), 0u, __frcp_rn(Tv[i]), N);
+            if (d.coin1) {
+                slot[i] = int(d.k1);
+                di[i] = sidx(a, N, 0, int(d.k1), x + i, y);
             }
-            // adaptive threshold R and learning parameter T
+            if (d.coin2) {
+                // the whole sample; with propagation only the requester's active channels
+                reqw[i] = ((d.j << 5) | d.k2) * 0x01010101u;
+                if (a.propagate && !dval[i]) reqw[i] = (reqw[i] & 0x00FFFFFFu) | 0x1F000000u;
+                cnt2[1] += 1;
+            }
+        }
+        uint32_t dold[PX];
+#pragma unroll
+        for (int i = 0; i < PX; ++i) dold[i] = slot[i] >= 0 ? uint32_t(a.Dq[di[i]]) : 0u;
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if (slot[i] < 0) continue;
+            const int nc = dval[i] ? 4 : 3;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c >= nc) break;
+                a.samp[di[i] + int64_t(c) * cstride] = uint16_t(pv[c][i]);
+                ownw[i] = (ownw[i] & ~(0xFFu << (8 * c))) | (uint32_t(slot[i]) << (8 * c));
+            }
+            const float q16 = __fmul_rn(dmin[i], 16.0f);
+            const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
+            Sv[i] = Sv[i] + q - dold[i];
+            a.Dq[di[i]] = uint16_t(q);
+            cnt2[0] += uint32_t(nc);
+        }
+        // adaptive threshold R and learning parameter T
+#pragma unroll
+        for (int i = 0; i < PX; ++i) {
+            if (!inb[i]) continue;
+            const bool fg = mk[i] != 0;
             const float dbar = fmaxf(__fdiv_rn(__uint2float_rn(Sv[i]), n16), a.eps_d);
             const float Rs = __fmul_rn(dbar, a.R_scale);
             const float Rn = Rv[i] > Rs ? __fmul_rn(Rv[i], omr) : __fmul_rn(Rv[i], opr);
@@ -231,9 +273,7 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
         }
     }
 
-    block_add<TY, 7>(cnt7, [&](int q) {
-        return q < 4 ? a.gsum_cur + q : a.counters + (q == 4 ? 0 : (q == 5 ? 1 : 2));
-    });
+    block_add<TY, 2>(cnt2, [&](int q) { return a.counters + (q == 0 ? 0 : 2); });
 }
 
 }  // namespace
