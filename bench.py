@@ -221,7 +221,11 @@ def run_ours(args):
     P = W * H
     mg = torch.empty((NFRAMES, H, W), dtype=torch.uint8, device=dev)
     mp = torch.empty_like(mg)
-    seg = fos.Segmenter(W, H, stream_id=rank)
+    if args.pbas_joint:  # profiler captures of the joint-channel PBAS kernel alone
+        seg = fos.Segmenter(W, H, stream_id=rank, methods=fos.METHOD_PBAS, pbas_joint=1)
+        mg = None
+    else:
+        seg = fos.Segmenter(W, H, stream_id=rank)
     stream = torch.cuda.Stream(device=dev)
 
     def step():
@@ -269,7 +273,8 @@ def run_ours(args):
     for name, (n, tot) in timing.items():
         if name not in ALGO_BYTES or n == 0:
             continue
-        bytes_px = ALGO_BYTES[name] * P
+        # the joint-channel PBAS kernel reports as pbas_classify: 186 B dense
+        bytes_px = (186.0 if args.pbas_joint and name == "pbas_classify" else ALGO_BYTES[name]) * P
         if name in ("pbas_classify", "fused_classify"):
             bytes_px += (SPARSE_OWN * counters["own_updates"] +
                          SPARSE_NEIGH * counters["neighbour_writes"]) / max(1, n)
@@ -918,9 +923,13 @@ def main():
                     help="frames per step (a shorter sequence for profiler captures)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run the device-resident steps only (for profiler captures)")
+    ap.add_argument("--pbas-joint", action="store_true",
+                    help="with --kernels-only: the joint-channel PBAS variant alone (profiler captures)")
     ap.add_argument("--workload", default="720p", choices=["720p", "batch16", "softgmm", "serve32", "table"],
                     help="720p: the headline single-stream sequence; batch16: 16 mixed streams")
     args = ap.parse_args()
+    if args.pbas_joint and not args.kernels_only:
+        ap.error("--pbas-joint is for --kernels-only profiler captures")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch16":
