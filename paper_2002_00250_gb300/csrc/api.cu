@@ -294,6 +294,7 @@ fos_status ensure_staging(fos_ctx* c)
         FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mg[b]), size_t(c->P) + 16));
         FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mp[b]), size_t(c->P) + 16));
         FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
+        FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_k[b], cudaEventDisableTiming));
         FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
     }
     return FOS_OK;
@@ -327,11 +328,13 @@ void free_all(fos_ctx* c)
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
+        if (c->ev_k[b]) cudaEventDestroy(c->ev_k[b]);
         if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
     }
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->out_stream) cudaStreamDestroy(c->out_stream);
 }
 
 // Sample / D planes: blocked device layout <-> unpadded [c][k][P] export layout.
@@ -468,6 +471,7 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
     if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail("cudaGetDevice", e);
     if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
     if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
+    if ((e = cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("cudaStreamCreate", e);
     const size_t pl = size_t(c->plane);
     if (gmm_on(c)) {
         const size_t n = gmm_nplanes(c) * pl * gmm_elem(c);
@@ -497,6 +501,7 @@ void fos_destroy(fos_ctx* ctx)
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
     cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamSynchronize(ctx->out_stream);
     free_all(ctx);
     delete ctx;
 }
@@ -574,23 +579,31 @@ fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t
     if (pbas_on(ctx) && !mask_pbas && n_frames > 0) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_pbas must be non-NULL");
     fos_status st = ensure_staging(ctx);
     if (st != FOS_OK) return st;
+    // Three streams, two staging slots: the input copy of frame f+1 and the
+    // mask copy of frame f-1 run while frame f's kernels do.  Slot b is
+    // reused by frame f+2 only after frame f's kernels have read its inputs
+    // (ev_k) and its masks have left the device (ev_done).
     const size_t P = size_t(ctx->P), Pd = size_t(ctx->Pd);
     for (int32_t f = 0; f < n_frames; ++f) {
         const int b = f & 1;
-        FOS_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[b], 0));
+        FOS_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_k[b], 0));
         FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_rgb[b], rgb + f * P * 3, P * 3, cudaMemcpyHostToDevice, ctx->copy_stream));
         FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_depth[b], depth + f * Pd, Pd * 2, cudaMemcpyHostToDevice, ctx->copy_stream));
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_in[b], ctx->copy_stream));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[b], 0));
+        FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_done[b], 0));
         st = process_device(ctx, ctx->h_rgb[b], ctx->h_depth[b], ctx->h_mg[b], ctx->h_mp[b], ctx->stream);
         if (st != FOS_OK) return st;
+        FOS_TRY(ctx, cudaEventRecord(ctx->ev_k[b], ctx->stream));
+        FOS_TRY(ctx, cudaStreamWaitEvent(ctx->out_stream, ctx->ev_k[b], 0));
         if (gmm_on(ctx))
-            FOS_TRY(ctx, cudaMemcpyAsync(mask_gmm + f * P, ctx->h_mg[b], P, cudaMemcpyDeviceToHost, ctx->stream));
+            FOS_TRY(ctx, cudaMemcpyAsync(mask_gmm + f * P, ctx->h_mg[b], P, cudaMemcpyDeviceToHost, ctx->out_stream));
         if (pbas_on(ctx))
-            FOS_TRY(ctx, cudaMemcpyAsync(mask_pbas + f * P, ctx->h_mp[b], P, cudaMemcpyDeviceToHost, ctx->stream));
-        FOS_TRY(ctx, cudaEventRecord(ctx->ev_done[b], ctx->stream));
+            FOS_TRY(ctx, cudaMemcpyAsync(mask_pbas + f * P, ctx->h_mp[b], P, cudaMemcpyDeviceToHost, ctx->out_stream));
+        FOS_TRY(ctx, cudaEventRecord(ctx->ev_done[b], ctx->out_stream));
     }
     FOS_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    FOS_TRY(ctx, cudaStreamSynchronize(ctx->out_stream));
     return FOS_OK;
 }
 

@@ -24,8 +24,9 @@ struct fos_ctx {
     fos_params prm{};
     int64_t t = 0;
     int device = 0;
-    cudaStream_t stream = nullptr;       // host-pointer API: kernels + mask copies
+    cudaStream_t stream = nullptr;       // host-pointer API: kernels
     cudaStream_t copy_stream = nullptr;  // host-pointer API: input copies
+    cudaStream_t out_stream = nullptr;   // host-pointer API: mask copies
     float* gmm = nullptr;
     uint16_t* samp = nullptr;
     uint16_t* Dq = nullptr;
@@ -41,7 +42,9 @@ struct fos_ctx {
     uint16_t* h_depth[2] = {nullptr, nullptr};
     uint8_t* h_mg[2] = {nullptr, nullptr};
     uint8_t* h_mp[2] = {nullptr, nullptr};
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+    // by staging slot: inputs copied in, kernel done (inputs free, masks
+    // ready), masks copied out (mask staging free)
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_k[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
     uint32_t timing_mask = 0;
     std::vector<fos::TimedLaunch> timed;
     std::vector<cudaEvent_t> ev_pool;
