@@ -167,7 +167,7 @@ def cpu_oracle_sample(n_steps: int = 3, nthreads: int = 0, frames=None):
         p.step(*frames[t])
     dt = time.perf_counter() - t0
     return {"value": round(n_steps * W * H / dt / 1e6, 4), "unit": "Mpixel-frames/s",
-            "cores": threads, "kind": "oracle",
+            "cores": oracle.threads_used(threads), "kind": "oracle",
             "sample": f"frames 1..{n_steps} of {WORKLOAD} (after frame-0 bootstrap), GMM FP64 + PBAS, "
                       f"OpenMP over pixels, {dt:.1f} s"}
 
@@ -585,7 +585,7 @@ def run_table(args):
                 t0 = time.perf_counter()
                 for t in range(1, nf + 1):
                     o.step(*host[t])
-                cpu[str(threads)] = round(nf * w * h / (time.perf_counter() - t0) / 1e6, 3)
+                cpu[str(oracle.threads_used(threads))] = round(nf * w * h / (time.perf_counter() - t0) / 1e6, 3)
             rows.append({"config": f"{w}x{h}x{n}", "method": name,
                          "mpx_frames_per_s": round(w * h * n / (ms * 1e-3) / 1e6, 1),
                          "kernel": kern, "kernel_avg_us": round(avg_us, 2),

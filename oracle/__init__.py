@@ -101,6 +101,10 @@ def lib():
             L.or_pbas_frame.argtypes = [ctypes.POINTER(_PbasParams), i32, i32, i64, vp, vp,
                                         vp, vp, vp, vp, vp, vp, vp, vp, i32]
             L.or_quality.argtypes = [i64, vp, vp, vp]
+            L.or_openmp.argtypes = []
+            L.or_openmp.restype = ctypes.c_int
+            L.or_threads.argtypes = [ctypes.c_int]
+            L.or_threads.restype = ctypes.c_int
             L.or_gmm_literal_frame.argtypes = [ctypes.POINTER(_GmmLiteralParams), i32, i32, i64, vp, vp,
                                                vp, vp, vp, vp, vp, vp, vp, vp, i32]
             for f in ("or_philox4x32_10", "or_philox_many", "or_depth_to_u8", "or_depth_resample", "or_sobel_grad_u8",
@@ -120,6 +124,17 @@ PBAS_DEFAULTS = dict(N=20, n_min=2, R_lower_rgb=18.0, R_lower_d=4.0, R_scale=5.0
                      R_incdec=0.05, T_lower=2.0, T_upper=200.0, T_inc=1.0, T_dec=0.05,
                      alpha_g=10.0, eps_d=1.0 / 16.0, seed=0, stream_id=0, forced_rng=0,
                      depth_full_scale_mm=10000, propagate=0, joint=0)
+
+
+def openmp() -> bool:
+    """True when the oracle was built with OpenMP (its pixel loops use the
+    host's cores); the build falls back to one thread when gcc has none."""
+    return bool(lib().or_openmp())
+
+
+def threads_used(nthreads: int = 0) -> int:
+    """Threads the oracle's parallel loops run on for an `nthreads` argument."""
+    return int(lib().or_threads(nthreads))
 
 
 def philox4x32_10(ctr, key) -> np.ndarray:

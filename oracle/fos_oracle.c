@@ -21,6 +21,19 @@
 #define OR_THREADS(n) 1
 #endif
 
+/* 1 when built with OpenMP (the pixel loops then run on the host's cores). */
+int or_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+/* Threads a parallel loop of the oracle runs on for an nthreads argument. */
+int or_threads(int nthreads) { return OR_THREADS(nthreads); }
+
 /* ======================================================================== */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
 /* easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications     */

@@ -108,6 +108,11 @@ void or_gmm_literal_frame(const or_gmm_literal_params* p, int W, int H, int64_t 
                           double* w_d, double* mu_d, double* v_d,
                           uint8_t* mask, double* margin, int nthreads);
 
+/* 1 when the oracle was built with OpenMP, else 0 (every loop single-threaded). */
+int or_openmp(void);
+/* Threads a parallel loop runs on for an nthreads argument (0: the OpenMP default). */
+int or_threads(int nthreads);
+
 /* ---- Sec. 3.2: PBAS with samples holding (R, G, B, D), FP32 + integers. ---- */
 typedef struct {
     int N;                      /* samples per pixel, 1..32 */
