@@ -37,6 +37,7 @@ ALGO_BYTES = {
     "pbas_classify": 246.0,   # 160 B samples + 48 B R,T,S read + 32 B R,T written + 5 in + 1 mask
     "fused_classify": 439.0,  # both of the above, the 5 B input read once
 }
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for context beside the measured peak
 SPARSE_OWN = 10.0   # per own update: 2 B sample + 2 B D read + 2 B D write + 4 B S write
 SPARSE_NEIGH = 2.0  # per neighbour write: 2 B sample (applied inside pbas_classify)
 
@@ -291,6 +292,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
                 "peak": peak, "unit": "GB/s", "frac": round(d["gbs"] / peak, 3),
                 "peak_source": peak_src, "traffic": tr,
+                "frac_of_nominal": round(d["gbs"] / NOMINAL_HBM_GBS, 3),
                 "algo_bytes_per_launch": round(d["algo_bytes"]),
                 "kernels": {k: {"avg_us": v["avg_us"], "GBps": round(v["gbs"], 1),
                                 "share": v["share"]} for k, v in kern.items()}}
