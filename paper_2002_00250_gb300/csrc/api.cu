@@ -285,18 +285,37 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     return FOS_OK;
 }
 
-fos_status ensure_staging(fos_ctx* c)
+// Staging for `frames` host frames per slot (grown on demand; callers of the
+// host-pointer API have synchronised every earlier use before this runs).
+constexpr int kHostChunk = 8;  // host frames per staging slot
+
+fos_status ensure_staging(fos_ctx* c, int frames)
 {
-    if (c->h_rgb[0]) return FOS_OK;
-    for (int b = 0; b < 2; ++b) {
-        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_rgb[b]), size_t(c->P) * 3 + 16));
-        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_depth[b]), size_t(c->Pd) * 2 + 16));
-        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mg[b]), size_t(c->P) + 16));
-        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mp[b]), size_t(c->P) + 16));
-        FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
-        FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_k[b], cudaEventDisableTiming));
-        FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
+    if (!c->ev_in[0]) {
+        for (int b = 0; b < 2; ++b) {
+            FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_in[b], cudaEventDisableTiming));
+            FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_k[b], cudaEventDisableTiming));
+            FOS_TRY(c, cudaEventCreateWithFlags(&c->ev_done[b], cudaEventDisableTiming));
+        }
     }
+    if (c->stage_frames >= frames) return FOS_OK;
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    c->stage_rgb = up(size_t(c->P) * 3);
+    c->stage_depth = up(size_t(c->Pd) * 2);
+    c->stage_mask = up(size_t(c->P));
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
+        c->h_rgb[b] = nullptr; c->h_depth[b] = nullptr; c->h_mg[b] = nullptr; c->h_mp[b] = nullptr;
+    }
+    c->stage_frames = 0;
+    const size_t f = size_t(frames);
+    for (int b = 0; b < 2; ++b) {
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_rgb[b]), f * c->stage_rgb));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_depth[b]), f * c->stage_depth));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mg[b]), f * c->stage_mask));
+        FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->h_mp[b]), f * c->stage_mask));
+    }
+    c->stage_frames = frames;
     return FOS_OK;
 }
 
@@ -577,29 +596,43 @@ fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t
     if (n_frames > 0 && (!rgb || !depth)) return fail(ctx, FOS_ERR_INVALID_ARG, "rgb and depth must be non-NULL");
     if (gmm_on(ctx) && !mask_gmm && n_frames > 0) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_gmm must be non-NULL");
     if (pbas_on(ctx) && !mask_pbas && n_frames > 0) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_pbas must be non-NULL");
-    fos_status st = ensure_staging(ctx);
+    if (n_frames == 0) return FOS_OK;
+    // Three streams, two staging slots of up to kHostChunk frames: the input
+    // copy of chunk g+1 and the mask copy of chunk g-1 run while chunk g's
+    // kernels do, and the kernels of one chunk run back to back (one
+    // cross-stream wait per chunk, not per frame).  Slot b is reused by
+    // chunk g+2 only after chunk g's kernels have read its inputs (ev_k) and
+    // its masks have left the device (ev_done).
+    const int chunk = n_frames < kHostChunk ? n_frames : kHostChunk;
+    fos_status st = ensure_staging(ctx, chunk);
     if (st != FOS_OK) return st;
-    // Three streams, two staging slots: the input copy of frame f+1 and the
-    // mask copy of frame f-1 run while frame f's kernels do.  Slot b is
-    // reused by frame f+2 only after frame f's kernels have read its inputs
-    // (ev_k) and its masks have left the device (ev_done).
     const size_t P = size_t(ctx->P), Pd = size_t(ctx->Pd);
-    for (int32_t f = 0; f < n_frames; ++f) {
-        const int b = f & 1;
+    const size_t rp = ctx->stage_rgb, dp = ctx->stage_depth, mp = ctx->stage_mask;
+    for (int32_t f0 = 0, g = 0; f0 < n_frames; f0 += chunk, ++g) {
+        const int b = g & 1;
+        const size_t m = size_t(n_frames - f0 < chunk ? n_frames - f0 : chunk);
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_k[b], 0));
-        FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_rgb[b], rgb + f * P * 3, P * 3, cudaMemcpyHostToDevice, ctx->copy_stream));
-        FOS_TRY(ctx, cudaMemcpyAsync(ctx->h_depth[b], depth + f * Pd, Pd * 2, cudaMemcpyHostToDevice, ctx->copy_stream));
+        FOS_TRY(ctx, cudaMemcpy2DAsync(ctx->h_rgb[b], rp, rgb + size_t(f0) * P * 3, P * 3, P * 3, m,
+                                       cudaMemcpyHostToDevice, ctx->copy_stream));
+        FOS_TRY(ctx, cudaMemcpy2DAsync(ctx->h_depth[b], dp, depth + size_t(f0) * Pd, Pd * 2, Pd * 2, m,
+                                       cudaMemcpyHostToDevice, ctx->copy_stream));
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_in[b], ctx->copy_stream));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[b], 0));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_done[b], 0));
-        st = process_device(ctx, ctx->h_rgb[b], ctx->h_depth[b], ctx->h_mg[b], ctx->h_mp[b], ctx->stream);
-        if (st != FOS_OK) return st;
+        for (size_t i = 0; i < m; ++i) {
+            st = process_device(ctx, ctx->h_rgb[b] + i * rp, reinterpret_cast<const uint16_t*>(
+                                    reinterpret_cast<const uint8_t*>(ctx->h_depth[b]) + i * dp),
+                                ctx->h_mg[b] + i * mp, ctx->h_mp[b] + i * mp, ctx->stream);
+            if (st != FOS_OK) return st;
+        }
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_k[b], ctx->stream));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->out_stream, ctx->ev_k[b], 0));
         if (gmm_on(ctx))
-            FOS_TRY(ctx, cudaMemcpyAsync(mask_gmm + f * P, ctx->h_mg[b], P, cudaMemcpyDeviceToHost, ctx->out_stream));
+            FOS_TRY(ctx, cudaMemcpy2DAsync(mask_gmm + size_t(f0) * P, P, ctx->h_mg[b], mp, P, m,
+                                           cudaMemcpyDeviceToHost, ctx->out_stream));
         if (pbas_on(ctx))
-            FOS_TRY(ctx, cudaMemcpyAsync(mask_pbas + f * P, ctx->h_mp[b], P, cudaMemcpyDeviceToHost, ctx->out_stream));
+            FOS_TRY(ctx, cudaMemcpy2DAsync(mask_pbas + size_t(f0) * P, P, ctx->h_mp[b], mp, P, m,
+                                           cudaMemcpyDeviceToHost, ctx->out_stream));
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_done[b], ctx->out_stream));
     }
     FOS_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -617,9 +650,7 @@ fos_status fos_process_frame(fos_ctx* ctx, const uint8_t* rgb, const uint16_t* d
 {
     if (!ctx) return FOS_ERR_INVALID_ARG;
     if (!mask_out) return fail(ctx, FOS_ERR_INVALID_ARG, "mask_out must be non-NULL");
-    fos_status st = ensure_staging(ctx);
-    if (st != FOS_OK) return st;
-    // the mask of the method not returned goes to the context's staging buffer
+    // the mask of the method not returned goes to a host buffer of its own
     if (gmm_on(ctx)) {
         if (!pbas_on(ctx)) return fos_process_frames_host(ctx, 1, rgb, depth, mask_out, nullptr);
         std::vector<uint8_t> unused(size_t(ctx->P));

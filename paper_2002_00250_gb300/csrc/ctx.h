@@ -38,7 +38,11 @@ struct fos_ctx {
     bool pending = false;               // requests of the last frame not yet applied
     int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1, 1};  // kernel shapes (fos_set_option)
     unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
-    uint8_t* h_rgb[2] = {nullptr, nullptr};  // device staging for host frames
+    // device staging for host frames: two slots of stage_frames frames each,
+    // frame pitches rounded up to 256 bytes
+    int stage_frames = 0;
+    size_t stage_rgb = 0, stage_depth = 0, stage_mask = 0;
+    uint8_t* h_rgb[2] = {nullptr, nullptr};
     uint16_t* h_depth[2] = {nullptr, nullptr};
     uint8_t* h_mg[2] = {nullptr, nullptr};
     uint8_t* h_mp[2] = {nullptr, nullptr};
