@@ -457,7 +457,8 @@ fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, 
  * when the frame's tick runs, so they must stay valid and unchanged until
  * fos_server_poll reports the tag.  Pinned buffers (cudaHostAlloc /
  * cudaHostRegister) are copied by DMA; pageable ones work but are staged by
- * the driver.  Same refusals (FOS_ERR_BUDGET, FOS_ERR_BUSY) as
+ * the driver.  When both mask buffers are pinned (or NULL) the masks are
+ * copied straight into them, without the server's staging and host copy.  Same refusals (FOS_ERR_BUDGET, FOS_ERR_BUSY) as
  * fos_server_submit; frames of both kinds share the stream's queue_depth. */
 fos_status fos_server_submit_nocopy(fos_server* s, int32_t stream, const uint8_t* rgb, const uint16_t* depth,
                                     uint8_t* mask_gmm, uint8_t* mask_pbas, int64_t tag);

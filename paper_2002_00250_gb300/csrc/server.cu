@@ -44,12 +44,27 @@ struct Frame {
     const uint16_t* ext_depth;
     uint8_t* out_gmm;    // caller's buffers (nullable per method)
     uint8_t* out_pbas;
+    bool direct_out;     // the caller's mask buffers are pinned: masks are copied
+                         // straight into them (no staging, no host memcpy)
     double t_submit;
 };
 
 // Byte offset of the depth plane in an input buffer (host slot or device):
 // 16-byte aligned whatever the pixel count.
 size_t depth_offset(size_t P) { return (P * 3 + 15) / 16 * 16; }
+
+// True for NULL and for page-locked host memory (cudaHostAlloc /
+// cudaHostRegister), which the copy engines can write directly.
+bool host_pinned(const void* p)
+{
+    if (!p) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
 size_t input_bytes(size_t P) { return depth_offset(P) + P * 2; }
 
 struct Stream {
@@ -174,8 +189,10 @@ void publish(fos_server* s, Tick& t)
     for (TickItem& it : t.items) {
         Stream* st = s->streams[it.stream];
         const size_t P = size_t(st->W) * size_t(st->H);
-        if (it.f.out_gmm) std::memcpy(it.f.out_gmm, st->h_mg[it.parity], P);
-        if (it.f.out_pbas) std::memcpy(it.f.out_pbas, st->h_mp[it.parity], P);
+        if (!it.f.direct_out) {
+            if (it.f.out_gmm) std::memcpy(it.f.out_gmm, st->h_mg[it.parity], P);
+            if (it.f.out_pbas) std::memcpy(it.f.out_pbas, st->h_mp[it.parity], P);
+        }
         if (it.f.host_in) st->free_in.push_back(it.f.host_in);
         fos_server_result r{};
         r.stream = it.stream;
@@ -277,10 +294,12 @@ void worker_main(fos_server* s)
             for (TickItem& it : t.items) {
                 Stream* st = s->streams[it.stream];
                 const size_t P = size_t(st->W) * size_t(st->H);
-                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_GMM))
-                    e = cudaMemcpyAsync(st->h_mg[it.parity], st->d_mg[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
-                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_PBAS))
-                    e = cudaMemcpyAsync(st->h_mp[it.parity], st->d_mp[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
+                uint8_t* og = it.f.direct_out ? it.f.out_gmm : st->h_mg[it.parity];
+                uint8_t* op = it.f.direct_out ? it.f.out_pbas : st->h_mp[it.parity];
+                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_GMM) && og)
+                    e = cudaMemcpyAsync(og, st->d_mg[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
+                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_PBAS) && op)
+                    e = cudaMemcpyAsync(op, st->d_mp[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
             }
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventRecord(t.done, s->cs);
@@ -454,6 +473,7 @@ fos_status fos_server_submit_nocopy(fos_server* s, int32_t stream, const uint8_t
     f.ext_depth = depth;
     f.out_gmm = mask_gmm;
     f.out_pbas = mask_pbas;
+    f.direct_out = host_pinned(mask_gmm) && host_pinned(mask_pbas);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream] || s->streams[stream]->closing)

@@ -202,7 +202,9 @@ def test_concurrent_submitters():
 def test_zero_copy_submit_and_odd_sizes():
     """Frames read straight from pinned caller buffers, and odd pixel counts
     (the depth plane of a packed input must stay aligned): same masks as
-    each stream processed alone."""
+    each stream processed alone.  Stream 0 also gives pinned mask buffers
+    (written directly by the copy engine), stream 1 pageable ones (staged),
+    stream 2 copies its frames at submission."""
     import torch
     from paper_2002_00250_gb300 import fos
     sizes = [(67, 45), (33, 17), (64, 32)]
@@ -213,9 +215,16 @@ def test_zero_copy_submit_and_odd_sizes():
     srv = fos.Server(1 << 34, 4)
     sids = [srv.open_stream(W, H, stream_id=500 + i) for i, (W, H) in enumerate(sizes)]
     outs = {}
+    keep = []
     for f in range(n):
         for i, (W, H) in enumerate(sizes):
-            mg, mp = np.empty((H, W), np.uint8), np.empty((H, W), np.uint8)
+            if i == 0:  # pinned mask buffers: direct copies
+                tg, tp = torch.empty((H, W), dtype=torch.uint8).pin_memory(), \
+                    torch.empty((H, W), dtype=torch.uint8).pin_memory()
+                keep.append((tg, tp))
+                mg, mp = tg.numpy(), tp.numpy()
+            else:
+                mg, mp = np.empty((H, W), np.uint8), np.empty((H, W), np.uint8)
             outs[(i, f)] = (mg, mp)
             if i == 2:  # one stream through the copying path
                 rgb, depth, _ = data[i]
