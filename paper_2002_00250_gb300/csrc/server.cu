@@ -95,9 +95,20 @@ struct TickItem {
 
 struct Tick {
     std::vector<TickItem> items;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t in = nullptr;    // inputs on the device (copy-in stream)
+    cudaEvent_t k = nullptr;     // kernels done (compute stream)
+    cudaEvent_t done = nullptr;  // masks in host memory (copy-out stream)
     double t_launch = 0.0;
 };
+
+void destroy_events(Tick& t)
+{
+    for (cudaEvent_t* e : {&t.in, &t.k, &t.done})
+        if (*e) {
+            cudaEventDestroy(*e);
+            *e = nullptr;
+        }
+}
 
 }  // namespace
 
@@ -107,7 +118,9 @@ struct fos_server {
     int max_streams = 0;
     int queue_depth = 16;             // pinned input slots per stream
     fos_batch* batch = nullptr;
-    cudaStream_t cs = nullptr;
+    cudaStream_t cs = nullptr;        // batched kernels
+    cudaStream_t cin = nullptr;       // input copies
+    cudaStream_t cout = nullptr;      // mask copies
     int device = 0;
     std::mutex mu;
     std::condition_variable cv;
@@ -204,8 +217,7 @@ void publish(fos_server* s, Tick& t)
         st->inflight -= 1;
         s->frames_done += 1;
     }
-    cudaEventDestroy(t.done);
-    t.done = nullptr;
+    destroy_events(t);
 }
 
 // Streams that asked to close and have nothing left leave; their memory is freed.
@@ -273,12 +285,12 @@ void worker_main(fos_server* s)
                 const size_t od = depth_offset(P);
                 if (it.f.host_in) {  // one copy of the packed slot
                     if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.host_in, od + P * 2, cudaMemcpyHostToDevice, s->cs);
+                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.host_in, od + P * 2, cudaMemcpyHostToDevice, s->cin);
                 } else {             // zero-copy submit: straight from the caller's buffers
                     if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.ext_rgb, P * 3, cudaMemcpyHostToDevice, s->cs);
+                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.ext_rgb, P * 3, cudaMemcpyHostToDevice, s->cin);
                     if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(st->d_in[it.parity] + od, it.f.ext_depth, P * 2, cudaMemcpyHostToDevice, s->cs);
+                        e = cudaMemcpyAsync(st->d_in[it.parity] + od, it.f.ext_depth, P * 2, cudaMemcpyHostToDevice, s->cin);
                 }
                 slots.push_back(st->slot);
                 rgb.push_back(st->d_in[it.parity]);
@@ -286,23 +298,32 @@ void worker_main(fos_server* s)
                 mg.push_back(st->d_mg[it.parity]);
                 mp.push_back(st->d_mp[it.parity]);
             }
+            // the input copies of this tick overlap the previous tick's kernels,
+            // its mask copies the next tick's (at most two ticks in flight, and
+            // a stream's consecutive frames use different buffers)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.in, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.k, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(t.in, s->cin);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, t.in, 0);
             t.t_launch = now_us();
             fos_status bst = FOS_OK;
             if (e == cudaSuccess)
                 bst = fos_batch_process_device(s->batch, int32_t(slots.size()), slots.data(), rgb.data(),
                                                dep.data(), mg.data(), mp.data(), s->cs);
+            if (e == cudaSuccess && bst == FOS_OK) e = cudaEventRecord(t.k, s->cs);
+            if (e == cudaSuccess && bst == FOS_OK) e = cudaStreamWaitEvent(s->cout, t.k, 0);
             for (TickItem& it : t.items) {
                 Stream* st = s->streams[it.stream];
                 const size_t P = size_t(st->W) * size_t(st->H);
                 uint8_t* og = it.f.direct_out ? it.f.out_gmm : st->h_mg[it.parity];
                 uint8_t* op = it.f.direct_out ? it.f.out_pbas : st->h_mp[it.parity];
-                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_GMM) && og)
-                    e = cudaMemcpyAsync(og, st->d_mg[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
-                if (e == cudaSuccess && (s->prm.methods & FOS_METHOD_PBAS) && op)
-                    e = cudaMemcpyAsync(op, st->d_mp[it.parity], P, cudaMemcpyDeviceToHost, s->cs);
+                if (e == cudaSuccess && bst == FOS_OK && (s->prm.methods & FOS_METHOD_GMM) && og)
+                    e = cudaMemcpyAsync(og, st->d_mg[it.parity], P, cudaMemcpyDeviceToHost, s->cout);
+                if (e == cudaSuccess && bst == FOS_OK && (s->prm.methods & FOS_METHOD_PBAS) && op)
+                    e = cudaMemcpyAsync(op, st->d_mp[it.parity], P, cudaMemcpyDeviceToHost, s->cout);
             }
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventRecord(t.done, s->cs);
+            if (e == cudaSuccess && bst == FOS_OK) e = cudaEventRecord(t.done, s->cout);
             if (e != cudaSuccess || bst != FOS_OK) {
                 std::lock_guard<std::mutex> lk(s->mu);
                 s->err = e != cudaSuccess ? cudaGetErrorString(e) : fos_batch_last_error(s->batch);
@@ -316,7 +337,7 @@ void worker_main(fos_server* s)
                     s->streams[it.stream]->inflight -= 1;
                     if (it.f.host_in) s->streams[it.stream]->free_in.push_back(it.f.host_in);
                 }
-                if (t.done) cudaEventDestroy(t.done);
+                destroy_events(t);
                 break;
             }
             inflight.push_back(std::move(t));
@@ -366,8 +387,12 @@ fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes,
     s->queue_depth = queue_depth;
     cudaGetDevice(&s->device);
     s->batch = fos_batch_create(max_streams, params);
-    if (!s->batch || cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess) {
+    if (!s->batch || cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->cout, cudaStreamNonBlocking) != cudaSuccess) {
         if (s->batch) fos_batch_destroy(s->batch);
+        for (cudaStream_t q : {s->cs, s->cin, s->cout})
+            if (q) cudaStreamDestroy(q);
         delete s;
         return nullptr;
     }
@@ -391,6 +416,8 @@ void fos_server_destroy(fos_server* s)
     }
     fos_batch_destroy(s->batch);
     cudaStreamDestroy(s->cs);
+    cudaStreamDestroy(s->cin);
+    cudaStreamDestroy(s->cout);
     delete s;
 }
 
