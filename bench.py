@@ -805,7 +805,7 @@ def run_serve32(args):
         pinned.append((pr, pd, pr.numpy(), pd.numpy(), ring.numpy(), ring))
     p = fos.default_params()
     lib = fos.load()
-    need = [lib.fos_stream_device_bytes(w, h, p) + 14 * w * h for w, h in sizes]
+    need = [lib.fos_stream_device_bytes(w, h, p) + 21 * w * h for w, h in sizes]
     leaving = [s_id for s_id in range(32) if s_id % 5 == 4]
     # everything that stays fits, plus the largest stream that leaves: the last
     # streams to join wait for admission until the first ones leave

@@ -402,15 +402,17 @@ fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
  * Serving loop with continuous batching.  No counterpart in the paper.
  *
  * A server owns a batch and a worker thread.  Streams (cameras) are admitted
- * by a device-memory budget: each needs fos_stream_device_bytes plus two
- * input and two mask buffers; a stream that does not fit, or finds no free
+ * by a device-memory budget: each needs fos_stream_device_bytes plus three
+ * input and three mask buffers (3 * 7 bytes per pixel, plus up to 15 bytes of
+ * alignment per input buffer); a stream that does not fit, or finds no free
  * slot, waits in FIFO order until others close.  fos_server_submit copies a
  * frame into one of the stream's queue_depth pinned input slots (allocated at
  * admission) and returns at once.  Each worker tick takes
  * the oldest pending frame of every admitted stream (frames of one stream run
  * in order), runs them as one batched launch, and writes the masks into the
- * caller's buffers given at submit time; two ticks are in flight, so frames
- * that arrive while one runs join the next.  Results are identical to
+ * caller's buffers given at submit time; three ticks are in flight (the
+ * input copies of one, the kernels of another and the mask copies of a third
+ * overlap), so frames that arrive while one runs join the next.  Results are identical to
  * processing each stream alone.  All calls are thread-safe.
  * ------------------------------------------------------------------------- */
 typedef struct fos_server fos_server;

@@ -1,16 +1,17 @@
 // server.cu -- serving loop with continuous batching over camera streams.
 //
 // No counterpart in the paper (one camera there).  Streams are admitted by
-// an HBM budget: a stream needs its device-resident models plus two input and
-// two mask buffers; a stream that does not fit waits (FIFO) until others
+// an HBM budget: a stream needs its device-resident models plus three input
+// and three mask buffers; a stream that does not fit waits (FIFO) until others
 // leave.  fos_server_submit copies a frame into one of the stream's pinned
 // input slots (allocated once, at admission) and returns at once; with no
 // free slot, or before admission, it refuses the frame (backpressure).  A worker thread runs ticks: each tick takes the oldest
 // pending frame of every admitted stream (at most one per stream, so every
 // stream's frames run in order), copies them to the device, runs ONE batched
-// launch over all of them (fos_batch), and copies the masks back.  Two ticks
-// are in flight: frames that arrive while a tick runs are admitted into the
-// next one.  Completed frames are delivered into the caller's mask buffers
+// launch over all of them (fos_batch), and copies the masks back.  Three
+// ticks are in flight, on three CUDA streams (input copies, kernels, mask
+// copies): frames that arrive while a tick runs are admitted into the next
+// one.  Completed frames are delivered into the caller's mask buffers
 // and reported by fos_server_poll with their latency.
 #include <chrono>
 #include <condition_variable>
@@ -53,6 +54,10 @@ struct Frame {
 // 16-byte aligned whatever the pixel count.
 size_t depth_offset(size_t P) { return (P * 3 + 15) / 16 * 16; }
 
+// Ticks in flight: the input copies of one tick, the kernels of another and
+// the mask copies of a third run at the same time.
+constexpr int kTicks = 3;
+
 // True for NULL and for page-locked host memory (cudaHostAlloc /
 // cudaHostRegister), which the copy engines can write directly.
 bool host_pinned(const void* p)
@@ -76,11 +81,13 @@ struct Stream {
     bool closing = false;
     std::deque<Frame> pending;
     int inflight = 0;    // frames of this stream in ticks not yet completed
-    uint8_t* d_in[2] = {nullptr, nullptr};     // device rgb+depth, by frame parity
-    uint8_t* d_mg[2] = {nullptr, nullptr};
-    uint8_t* d_mp[2] = {nullptr, nullptr};
-    uint8_t* h_mg[2] = {nullptr, nullptr};     // pinned mask staging
-    uint8_t* h_mp[2] = {nullptr, nullptr};
+    // by frame number mod kTicks: a stream has at most one frame in each of
+    // the kTicks ticks in flight
+    uint8_t* d_in[kTicks] = {};                // device rgb+depth
+    uint8_t* d_mg[kTicks] = {};
+    uint8_t* d_mp[kTicks] = {};
+    uint8_t* h_mg[kTicks] = {};                // pinned mask staging
+    uint8_t* h_mp[kTicks] = {};
     int64_t nframes = 0;
     uint8_t* arena = nullptr;                    // pinned input slots, allocated at admission
     int copying = 0;                             // submits writing into a slot right now
@@ -139,7 +146,7 @@ namespace {
 size_t stream_bytes(const fos_server* s, int32_t W, int32_t H)
 {
     const size_t P = size_t(W) * size_t(H);
-    return fos_stream_device_bytes(W, H, &s->prm) + 2 * (input_bytes(P) + 2 * P);
+    return fos_stream_device_bytes(W, H, &s->prm) + kTicks * (input_bytes(P) + 2 * P);
 }
 
 void free_stream_buffers(Stream* st)
@@ -147,7 +154,7 @@ void free_stream_buffers(Stream* st)
     cudaFreeHost(st->arena);
     st->arena = nullptr;
     st->free_in.clear();
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kTicks; ++k) {
         cudaFree(st->d_in[k]);
         cudaFree(st->d_mg[k]);
         cudaFree(st->d_mp[k]);
@@ -177,7 +184,7 @@ void admit(fos_server* s)
             st->free_in.clear();
             for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(st->arena + size_t(q) * slot_bytes);
         }
-        for (int k = 0; k < 2 && ok; ++k) {
+        for (int k = 0; k < kTicks && ok; ++k) {
             ok = cudaMalloc(&st->d_in[k], input_bytes(P)) == cudaSuccess &&
                  cudaMalloc(&st->d_mg[k], P + 16) == cudaSuccess &&
                  cudaMalloc(&st->d_mp[k], P + 16) == cudaSuccess &&
@@ -265,10 +272,10 @@ void worker_main(fos_server* s)
             // whose previous frame is not still using this parity's buffers
             for (size_t h = 0; h < s->streams.size(); ++h) {
                 Stream* st = s->streams[h];
-                if (!st || st->slot < 0 || st->pending.empty() || st->inflight >= 2) continue;
+                if (!st || st->slot < 0 || st->pending.empty() || st->inflight >= kTicks) continue;
                 TickItem it;
                 it.stream = int(h);
-                it.parity = int(st->nframes & 1);
+                it.parity = int(st->nframes % kTicks);
                 it.f = st->pending.front();
                 st->pending.pop_front();
                 st->nframes += 1;
@@ -299,8 +306,8 @@ void worker_main(fos_server* s)
                 mp.push_back(st->d_mp[it.parity]);
             }
             // the input copies of this tick overlap the previous tick's kernels,
-            // its mask copies the next tick's (at most two ticks in flight, and
-            // a stream's consecutive frames use different buffers)
+            // its mask copies the next tick's (at most kTicks ticks in flight,
+            // and a stream's frames in them use different buffers)
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.in, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.k, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
@@ -342,10 +349,10 @@ void worker_main(fos_server* s)
             }
             inflight.push_back(std::move(t));
         }
-        // deliver finished ticks; keep at most two in flight
+        // deliver finished ticks; keep at most kTicks in flight
         while (!inflight.empty()) {
             Tick& old = inflight.front();
-            const bool full = inflight.size() >= 2;
+            const bool full = inflight.size() >= size_t(kTicks);
             const cudaError_t q = full ? cudaEventSynchronize(old.done) : cudaEventQuery(old.done);
             if (q == cudaErrorNotReady) break;
             std::lock_guard<std::mutex> lk(s->mu);
