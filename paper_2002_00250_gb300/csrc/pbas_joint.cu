@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
     using G = Geo<PX, TY>;
     constexpr int NW = SWords<PX>::NW;
     constexpr float kThird = 1.0f / 3.0f;  // fl(1/3)
+    constexpr int kAhead = 4;              // sample rows prefetched into L1 ahead of use
     __shared__ ClassifySmem<PX, TY> S;
     uint8_t* sm = S.sm;
     uint32_t* sreq = S.sreq;
@@ -35,6 +36,20 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
 
+    {
+        // L1 prefetch of R, T, S and the first kAhead sample rows of every channel
+        const int px = x0 + int(threadIdx.x) * PX, py = y0 + int(threadIdx.y);
+        if (py < a.H && px < a.W) {
+            const int64_t q = int64_t(py) * a.Wp + px;
+            prefetch_l1(a.R + q); prefetch_l1(a.T + q); prefetch_l1(a.S + q);
+            const int64_t sb = sidx(a, N, 0, 0, px, py), cs = a.nseg * int64_t(N) * kSeg;
+#pragma unroll
+            for (int k = 0; k < kAhead; ++k)
+                if (k < N)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) prefetch_l1(a.samp + sb + c * cs + int64_t(k) * kSeg);
+        }
+    }
     stage_input<PX, TY>(a, x0, y0, sm);
     if (a.apply) stage_requests<PX, TY>(a, x0, y0, sreq);
     if (tid < 4) {
@@ -126,6 +141,9 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
         const int64_t cstride = a.nseg * int64_t(N) * kSeg;  // channel c + 1 lies this far after c
 #pragma unroll(NT > 0 ? NT : 4)
         for (int k = 0; k < N; ++k) {
+            if (k + kAhead < N)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) prefetch_l1(a.samp + sb + int64_t(c) * cstride + int64_t(k + kAhead) * kSeg);
             uint32_t s[4][NW];
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
