@@ -258,7 +258,8 @@ def test_propagation_conflict_east_neighbour_wins(orc):
                     assert got == want, (prop, u, yy, c)
 
 
-def test_propagation_own_update_and_lowest_direction_win(orc):
+@pytest.mark.parametrize("joint", [0, 1])
+def test_propagation_own_update_and_lowest_direction_win(orc, joint):
     """Forced mode 3 at t = 1 (N = 2, own slot 1): even columns ask north,
     odd ones south-east, so every pixel of an even column is asked from below
     (direction 4 seen from it) and from the north-west (7).  Requesters on
@@ -266,13 +267,14 @@ def test_propagation_own_update_and_lowest_direction_win(orc):
     keeps the pixel's own value; requesters on odd rows ask for slot 0, which
     takes the value of the neighbour below where there is one, else of the
     north-west one.  Without propagation an asked slot 0 takes the pixel's
-    own value."""
+    own value.  The joint-channel variant (one draw per pixel, whole-sample
+    requests) gives the same slots in every channel."""
     W, H, N = 8, 6, 2
     f0, f1, d = _two_frames(W, H, 3)
     chs = _channels(orc, f1, d)
     boot = _channels(orc, f0, d)
     for prop in (1, 0):
-        p = orc.PBAS(W, H, N=N, forced_rng=3, propagate=prop)
+        p = orc.PBAS(W, H, N=N, forced_rng=3, propagate=prop, joint=joint)
         p.step(f0, d)
         p.step(f1, d)
         for v in range(H):
