@@ -552,13 +552,23 @@ fos_status fos_softgmm_backward(fos_softgmm* g, const uint8_t* d_rgb, const uint
  *     D uint16 (same shape) at 8*N*Sp, R float32 [4][Sp] at 16*N*Sp,
  *     T float32 [4][Sp] at 16*N*Sp + 16*Sp, S uint32 [4][Sp] at
  *     16*N*Sp + 32*Sp, gradient sums uint64 [3][4] at 16*N*Sp + 48*Sp.
- *     256-byte aligned.  Its contents need no initialisation before frame 0.
+ *     Must be 256-byte aligned (else FOS_ERR_INVALID_ARG).  Its contents
+ *     need no initialisation before frame 0.
+ * params: checked as fos_create checks them for a PBAS-only context; spatial
+ *     propagation and the joint-channel variant give FOS_ERR_UNSUPPORTED.
  * stream: cudaStream_t (NULL = legacy default stream); asynchronous.
  *
- * The first call on a device looks up the scratch array's device address;
- * make that first call before any stream capture begins.  All calls share
- * the one scratch array: calls whose kernels may overlap on the GPU (other
- * streams, other threads) race on it and must be serialised by the caller.
+ * First call on a device: the CUDA runtime loads the library's device code
+ * on a device when it is first used there (lazy module loading), and that
+ * load is when the scratch array is allocated; it may also synchronise the
+ * device.  The first call on each device therefore allocates implicitly and
+ * can fail with FOS_ERR_CUDA if the device has no room for the array.  It
+ * also looks up the array's device address.  Callers with a no-allocation
+ * window should make one call on every device they will use (frame 0 of any
+ * model will do) before that window opens, and before any stream capture.
+ * All calls share the one scratch array: calls whose kernels may overlap on
+ * the GPU (other streams, other threads) race on it and must be serialised
+ * by the caller.
  * Errors: status code, text from fos_last_error(NULL) on the calling thread.
  * ------------------------------------------------------------------------- */
 #define FOS_NOALLOC_MAX_PIXELS 2097152

@@ -16,7 +16,9 @@
 // the model the call leaves behind already contains them.
 #include <cstdio>
 #include <mutex>
+#include <string>
 
+#include "ctx.h"
 #include "fos.h"
 #include "fos_internal.h"
 
@@ -86,15 +88,21 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
         return noalloc_fail(FOS_ERR_INVALID_ARG,
                             "fos_pbas_step_noalloc: frame too large: 128*ceil(width/128)*height "
                             "exceeds FOS_NOALLOC_MAX_PIXELS (2097152)");
+    if (reinterpret_cast<uintptr_t>(d_model) % 256 != 0)
+        return noalloc_fail(FOS_ERR_INVALID_ARG, "fos_pbas_step_noalloc: d_model must be 256-byte aligned");
+    // the same parameter checks as a PBAS-only context (methods is ignored here)
+    fos_params pv = *params;
+    pv.methods = FOS_METHOD_PBAS;
+    pv.gmm_literal = 0;
+    std::string why;
+    const fos_status vs = ctx_validate_params(&pv, why);
+    if (vs != FOS_OK) return noalloc_fail(vs, ("fos_pbas_step_noalloc: " + why).c_str());
     const fos_params& p = *params;
     if (p.pbas_propagate)
         return noalloc_fail(FOS_ERR_UNSUPPORTED,
                             "fos_pbas_step_noalloc: spatial propagation needs a second value plane (not in the scratch)");
     if (p.pbas_joint)
         return noalloc_fail(FOS_ERR_UNSUPPORTED, "fos_pbas_step_noalloc: the per-channel PBAS only (pbas_joint = 0)");
-    if (p.N < 1 || p.N > 31 || p.n_min < 1 || p.n_min > p.N || !(p.T_lower > 0.f) ||
-        !(p.T_upper >= p.T_lower) || !(p.eps_d > 0.f) || p.depth_full_scale_mm == 0)
-        return noalloc_fail(FOS_ERR_INVALID_ARG, "fos_pbas_step_noalloc: PBAS parameter out of range");
 
     void* scratch = nullptr;
     cudaError_t e = scratch_address(&scratch);

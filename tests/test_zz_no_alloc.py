@@ -29,15 +29,17 @@ def _planes(buf, W, H):
     return buf.reshape(4, H, spr * 128)[..., :W].reshape(4, H * W)
 
 
-@pytest.mark.parametrize("W,H", [(200, 48), (67, 45)])
-def test_noalloc_matches_context(W, H):
+@pytest.mark.parametrize("W,H,N,forced", [(200, 48, 20, 0), (67, 45, 20, 0), (136, 40, 8, 0), (136, 40, 20, 3)])
+def test_noalloc_matches_context(W, H, N, forced):
+    """N = 8 runs the kernels' generic slot count, forced_rng = 3 the draws
+    that make neighbour requests collide; after the first call, further calls
+    leave the device's free memory unchanged."""
     import torch
     from paper_2002_00250_gb300 import fos
 
     n = 6
     rgb, depth, _ = scene(W, H, n, seed=21, hole_fraction=0.05)
-    params = fos.default_params(methods=fos.METHOD_PBAS)
-    N = params.N
+    params = fos.default_params(methods=fos.METHOD_PBAS, N=N, forced_rng=forced)
     Sp = ((W + 127) // 128) * 128 * H
     model = torch.zeros(16 * N * Sp + 48 * Sp + 96, dtype=torch.uint8, device="cuda")
     d_rgb = torch.from_numpy(rgb).cuda()
@@ -68,6 +70,15 @@ def test_noalloc_matches_context(W, H):
         np.testing.assert_array_equal(R.T, want["R"])
         np.testing.assert_array_equal(T.T, want["T"])
         np.testing.assert_array_equal(S.T, want["S"])
+    # more frames, nothing else in between: the free device memory must not move
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for t in range(n, n + 4):
+        st = lib.fos_pbas_step_noalloc(W, H, ctypes.byref(params), t, d_rgb[t % n].data_ptr(),
+                                       d_dep[t % n].data_ptr(), model.data_ptr(), mask.data_ptr(), stream)
+        assert st == 0, lib.fos_last_error(None)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_rejects_oversized_frames():
@@ -78,3 +89,19 @@ def test_noalloc_rejects_oversized_frames():
     st = lib.fos_pbas_step_noalloc(2048, 1025, ctypes.byref(params), 0, 16, 16, 16, 16, None)
     assert st == 1
     assert b"FOS_NOALLOC_MAX_PIXELS" in lib.fos_last_error(None)
+
+
+def test_noalloc_rejects_bad_model_alignment_and_parameters():
+    """Host-side checks only (no kernel is launched): a model buffer off the
+    256-byte boundary, and parameters that fos_create refuses for a PBAS
+    context, are refused here too."""
+    from paper_2002_00250_gb300 import fos
+    lib = fos.load()
+    params = fos.default_params(methods=fos.METHOD_PBAS)
+    st = lib.fos_pbas_step_noalloc(64, 32, ctypes.byref(params), 0, 16, 16, 16 + 1, 16, None)
+    assert st == 1 and b"256-byte" in lib.fos_last_error(None)
+    for bad in (dict(R_lower_rgb=0.0), dict(R_lower_d=-1.0), dict(R_incdec=1.0), dict(forced_rng=4),
+                dict(pbas_propagate=2), dict(depth_full_scale_mm=65535 * 4 + 1)):
+        p = fos.default_params(methods=fos.METHOD_PBAS, **bad)
+        st = lib.fos_pbas_step_noalloc(64, 32, ctypes.byref(p), 0, 256, 256, 256, 256, None)
+        assert st == 1, bad
