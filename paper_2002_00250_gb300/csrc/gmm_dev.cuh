@@ -1,10 +1,14 @@
 // gmm_dev.cuh -- per-pixel GMM device code shared by the GMM kernels and the
 // fused GMM+PBAS tile kernel (paper Sec. 3.1, Eq. 1).
 //
-// Every floating-point operation is written as an explicit round-to-nearest
-// intrinsic (fused multiply-adds where intended), so the result does not
-// depend on the compiler's contraction setting of the including file: all
-// kernels produce the same bits for the same pixel.
+// Every floating-point operation is written as an explicit intrinsic (fused
+// multiply-adds where intended), so the result does not depend on the
+// compiler's contraction setting of the including file: all kernels produce
+// the same bits for the same pixel.  Quotients use the hardware reciprocal
+// approximation (__fdividef, at most 2 ulp) rather than the correctly rounded
+// division, which costs about twenty instructions each: the FP32 model is held
+// to the FP64 definition only within 1e-4 relative, and fourteen divisions per
+// pixel made the update a quarter of the fused kernel's instructions.
 #pragma once
 #include <cmath>
 
@@ -62,7 +66,7 @@ __device__ __forceinline__ float mix_step(Mix<K, C>& m, const float (&x)[C], flo
             s = __fmaf_rn(diff[c][k], diff[c][k], s);
         }
         ss[k] = s;
-        d2[k] = __fdiv_rn(s, __fmul_rn(float(C), m.v[k]));
+        d2[k] = __fdividef(s, __fmul_rn(float(C), m.v[k]));
     }
     float cum = 0.f, dB = INFINITY;
     bool open = true;
@@ -86,7 +90,7 @@ __device__ __forceinline__ float mix_step(Mix<K, C>& m, const float (&x)[C], flo
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (k == match) {
-                const float rho = __fdiv_rn(alpha, m.w[k]);
+                const float rho = __fdividef(alpha, m.w[k]);
 #pragma unroll
                 for (int c = 0; c < C; ++c) m.mu[c][k] = __fmaf_rn(rho, diff[c][k], m.mu[c][k]);
                 const float dv = __fsub_rn(__fmul_rn(ss[k], 1.f / float(C)), m.v[k]);
@@ -103,12 +107,18 @@ __device__ __forceinline__ float mix_step(Mix<K, C>& m, const float (&x)[C], flo
     float s = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) s = __fadd_rn(s, m.w[k]);
+    const float inv = __fdividef(1.f, s);
 #pragma unroll
-    for (int k = 0; k < K; ++k) m.w[k] = __fdiv_rn(m.w[k], s);
+    for (int k = 0; k < K; ++k) m.w[k] = __fmul_rn(m.w[k], inv);
 
     float key[K];
+    bool ranked = true;  // already in order: the network below would not swap
 #pragma unroll
-    for (int k = 0; k < K; ++k) key[k] = __fmul_rn(m.w[k], rsqrtf(m.v[k]));
+    for (int k = 0; k < K; ++k) {
+        key[k] = __fmul_rn(m.w[k], rsqrtf(m.v[k]));
+        if (k > 0) ranked &= !(key[k] > key[k - 1]);
+    }
+    if (ranked) return dB;
 #pragma unroll
     for (int pass = 0; pass < K - 1; ++pass) {
 #pragma unroll
@@ -229,6 +239,67 @@ __device__ __forceinline__ void move_mix(float* st, int64_t plane, int64_t p, in
             else m.mu[c][k] = *mu;
         }
     }
+}
+
+// One mixture of two adjacent pixels (p even, plane 8-byte aligned) moved
+// between registers and its planes with one 8-byte access per parameter.
+template <int K, int C, bool STORE>
+__device__ __forceinline__ void move_mix2(float* st, int64_t plane, int64_t p, int q0, Mix<K, C> (&m)[2])
+{
+    auto mv = [&](int q, float& a0, float& a1) {
+        float2* ptr = reinterpret_cast<float2*>(st + int64_t(q) * plane + p);
+        if (STORE) {
+            *ptr = make_float2(a0, a1);
+        } else {
+            const float2 v = *ptr;
+            a0 = v.x;
+            a1 = v.y;
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        mv(q0 + k, m[0].w[k], m[1].w[k]);
+        mv(q0 + (1 + C) * K + k, m[0].v[k], m[1].v[k]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) mv(q0 + (1 + c) * K + k, m[0].mu[c][k], m[1].mu[c][k]);
+    }
+}
+
+// Two adjacent pixels (p even, inputs already converted: colour bytes r, g, b
+// and the 8-bit depth, 0 = invalid reading), frames >= 1: the colour mixtures
+// of both, then the depth mixtures of both (moved only if either reading is
+// valid; a pixel with an invalid reading writes its model back unchanged).
+// Returns the two mask bytes in bits 0-7 and 8-15.
+template <int KR, int KD>
+__device__ __forceinline__ uint32_t gmm_pair(const GmmArgs& a, int64_t p, const uint32_t (&r)[2],
+                                             const uint32_t (&g)[2], const uint32_t (&b)[2],
+                                             const uint32_t (&d8)[2])
+{
+    float Q[2];
+    {
+        Mix<KR, 3> mr[2];
+        move_mix2<KR, 3, false>(a.state, a.plane, p, 0, mr);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float xr[3] = {float(r[i]), float(g[i]), float(b[i])};
+            Q[i] = mix_step(mr[i], xr, a.alpha, a.lam2, a.T_bg, a.v_init_rgb, a.v_min_rgb);
+        }
+        move_mix2<KR, 3, true>(a.state, a.plane, p, 0, mr);
+    }
+    if (d8[0] | d8[1]) {
+        Mix<KD, 1> md[2];
+        move_mix2<KD, 1, false>(a.state, a.plane, p, 5 * KR, md);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (d8[i] != 0) {
+                const float xd[1] = {float(d8[i])};
+                const float dB_d = mix_step(md[i], xd, a.alpha, a.lam2, a.T_bg, a.v_init_d, a.v_min_d);
+                Q[i] = __fmaf_rn(a.w_depth, dB_d, __fmul_rn(__fsub_rn(1.f, a.w_depth), Q[i]));
+            }
+        }
+        move_mix2<KD, 1, true>(a.state, a.plane, p, 5 * KR, md);
+    }
+    return (Q[0] >= a.lam2 ? 0xFFu : 0u) | (Q[1] >= a.lam2 ? 0xFF00u : 0u);
 }
 
 // One pixel with the two mixtures handled one after the other (lower

@@ -209,9 +209,7 @@ __device__ __forceinline__ void block_add(const uint32_t (&v)[NV], Dst dst)
     __shared__ uint32_t red[NV][TY];
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        uint32_t s = v[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        const uint32_t s = __reduce_add_sync(0xFFFFFFFFu, v[q]);
         if (threadIdx.x == 0) red[q][threadIdx.y] = s;
     }
     __syncthreads();
@@ -297,7 +295,8 @@ struct Draws {
 
 // Random draws for pixel p, frame t, channel c: Philox4x32-10 with counter
 // (p, t, c, 0) and key (seed, stream_id).  Words 0 and 2 give the two coins
-// (24-bit uniform < 1/T), word 1 the own slot, word 3 the direction (3 bits)
+// (24-bit uniform < prob = fl(1/T), T the pixel's learning parameter before
+// this frame's update), word 1 the own slot, word 3 the direction (3 bits)
 // and the neighbour slot (29 bits).
 __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c, float prob, int N)
 {
@@ -330,7 +329,7 @@ __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c
 // GMM classify + update (Sec. 3.1) of the tile's own pixels, reading the
 // colour and the converted depth from the staged tile (fused GMM+PBAS path).
 // The model state and the mask are addressed as in the GMM kernels.
-template <int KR, int KD, int PX, int TY>
+template <int KR, int KD, int PX, int TY, bool PAIR = true>
 __device__ __forceinline__ void gmm_tile_part(const GmmArgs& g, const PbasArgs& a, int x0, int y0,
                                               const uint8_t* sm)
 {
@@ -340,6 +339,22 @@ __device__ __forceinline__ void gmm_tile_part(const GmmArgs& g, const PbasArgs& 
     if (y >= a.H || x >= a.W) return;
     const int64_t p0 = int64_t(y) * a.W + x;
     const int o = (ly + 1) * G::SWP + lx0 + 1;
+    if constexpr (PX == 2 && PAIR) {
+        // W is even on this path: both pixels in the frame, 8-byte state accesses
+        const uint32_t r[2] = {sm[o], sm[o + 1]}, gg[2] = {sm[G::CH + o], sm[G::CH + o + 1]};
+        const uint32_t b[2] = {sm[2 * G::CH + o], sm[2 * G::CH + o + 1]};
+        const uint32_t d8[2] = {sm[3 * G::CH + o], sm[3 * G::CH + o + 1]};
+        if (!g.init) {
+            const uint32_t m = gmmdev::gmm_pair<KR, KD>(g, p0, r, gg, b, d8);
+            if ((reinterpret_cast<uintptr_t>(g.mask) & 1u) == 0) {  // p0 is even
+                *reinterpret_cast<uint16_t*>(g.mask + p0) = uint16_t(m);
+            } else {
+                g.mask[p0] = uint8_t(m);
+                g.mask[p0 + 1] = uint8_t(m >> 8);
+            }
+            return;
+        }
+    }
 #pragma unroll 1
     for (int i = 0; i < PX; ++i) {
         if (x + i >= a.W) break;
@@ -371,14 +386,31 @@ __device__ __forceinline__ void prefetch_channel(const PbasArgs& a, int N, int c
     prefetch_l1(a.S + pc);
 }
 
+// fl(S / d) for an integer 0 <= S < 2^24 and an integer divisor 1 <= d < 2^23,
+// given z = fl(1/d): the quotient from the product, corrected once with the
+// exact remainder (both steps fused multiply-adds).  The result is the
+// correctly rounded quotient: the remainder r = S - q0 d is exact, the
+// corrected value q0 + r z differs from S/d by |r (z - 1/d)| < ulp(S/d) 2^-24,
+// while a quotient of two integers that is not a float lies at least
+// ulp/(2d) from every rounding midpoint (and is never on one here, since d's
+// odd part divides neither side of a midpoint at these magnitudes).  Three
+// instructions instead of the general division's twenty.
+__device__ __forceinline__ float div_int_const(uint32_t S, float d, float z)
+{
+    const float y = __uint2float_rn(S);
+    const float q0 = __fmul_rn(y, z);
+    const float r = __fmaf_rn(-q0, d, y);
+    return __fmaf_rn(r, z, q0);
+}
+
 // Shared memory of one classify tile.
 template <int PX, int TY>
 struct ClassifySmem {
     using G = Geo<PX, TY>;
     __align__(16) uint8_t sm[4 * G::CH];  // staged channels with halo
     uint32_t sreq[G::SH * G::SW];         // staged request words with halo
-    float wtab[4][256];                   // fl(wg_c * dg) for every gradient difference dg
     float wgs[4];
+    float rn16;                           // fl(1 / (16 N)) for div_int_const
 };
 
 }  // namespace

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
     constexpr float kThird = 1.0f / 3.0f;  // fl(1/3)
     constexpr int kAhead = 4;              // sample rows prefetched into L1 ahead of use
     __shared__ ClassifySmem<PX, TY> S;
+    __shared__ float wtab[4][256];  // fl(wg_c * dg) for every gradient difference dg
     uint8_t* sm = S.sm;
     uint32_t* sreq = S.sreq;
     const int N = NT > 0 ? NT : a.N;
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
     if (x0 == 0 && y0 == 0 && tid >= 4 && tid < 8) a.gsum_next[tid - 4] = 0ull;
     __syncthreads();
     for (int e = tid; e < 1024; e += 32 * TY)
-        S.wtab[e >> 8][e & 255] = __fmul_rn(S.wgs[e >> 8], __int2float_rn(e & 255));
+        wtab[e >> 8][e & 255] = __fmul_rn(S.wgs[e >> 8], __int2float_rn(e & 255));
     __syncthreads();
 
     const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(32 * TY, 1024 / (32 * TY)) pbas_joint_kernel(c
                     for (int c = 0; c < 4; ++c) {
                         const uint32_t dv = (d[c] >> (16 * h)) & 0xFFu;
                         const uint32_t dg = (d[c] >> (16 * h + 8)) & 0xFFu;
-                        const float dc = __fadd_rn(S.wtab[c][dg], __uint2float_rn(dv));
+                        const float dc = __fadd_rn(wtab[c][dg], __uint2float_rn(dv));
                         if (c == 0) sum = dc;
                         else if (c < 3 || dval[i]) sum = __fadd_rn(sum, dc);
                     }
