@@ -2,14 +2,15 @@
 //
 // A batch owns up to max_streams stream contexts (ordinary fos_ctx objects,
 // so every single-stream call -- state export, reset, options -- works on
-// them).  One frame step of any subset of the streams is one CUDA graph
-// replay: a copy of the per-stream kernel arguments from pinned host memory,
-// a persistent GMM kernel and a persistent PBAS kernel that walk the
-// (stream, tile) work of the step with a grid stride.  The counts are read
-// from device memory, so the same graph serves every composition; two graphs
-// alternate over two argument buffers so the host can fill one while the
-// other is in flight.  Results are bit-identical to processing each stream
-// alone: every pixel runs the same code on the same data.
+// them).  One frame step of up to kBatchLaunchMax streams is one replay of a
+// CUDA graph holding one persistent kernel (GMM and PBAS of every tile, or
+// one per method when they do not run together) that walks the (stream, tile)
+// work of the step round-robin.  The per-stream arguments of the step form a
+// table that rides in the kernel node's parameters (updated in the
+// instantiated graph before each replay), so the kernels read them from the
+// constant bank; larger steps take one replay per kBatchLaunchMax streams.
+// Results are bit-identical to processing each stream alone: every pixel runs
+// the same code on the same data.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -27,17 +28,20 @@ struct fos_batch {
     int max_streams = 0;
     int sms = 0;
     std::vector<fos_ctx*> slot;
-    // argument buffers: [2] x (gmm entries | pbas entries | header)
-    size_t gmm_bytes = 0, pbas_bytes = 0, buf_bytes = 0;
-    uint8_t* dev = nullptr;
-    uint8_t* host = nullptr;  // pinned
-    cudaEvent_t done[2] = {nullptr, nullptr};
-    bool used[2] = {false, false};
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int graph_key[2] = {-1, -1};
+    cudaEvent_t done = nullptr;  // after the last step's kernels
+    bool used = false;
+    // the step graph: its kernel nodes (GMM, PBAS; null where unused) and the
+    // parameters they were captured with
+    cudaGraph_t graph_src = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_key = -1;
+    cudaGraphNode_t node[2] = {nullptr, nullptr};
+    cudaKernelNodeParams kp[2] = {};
+    int blocks[2] = {0, 0};
     cudaStream_t cap = nullptr;
-    int tick = 0;
     int gmm_px = 2, pbas_px = 2, pbas_ty = 8;  // tuned shapes
+    GmmBatchTable gt{};
+    PbasBatchTable pt{};
     std::string err;
 };
 
@@ -63,14 +67,6 @@ fos_status bcuda(fos_batch* b, const char* what, cudaError_t e)
         if (e_ != cudaSuccess) return bcuda(b, #call, e_); \
     } while (0)
 
-GmmBatchEntry* dev_gmm(fos_batch* b, int k) { return reinterpret_cast<GmmBatchEntry*>(b->dev + k * b->buf_bytes); }
-PbasBatchEntry* dev_pbas(fos_batch* b, int k)
-{
-    return reinterpret_cast<PbasBatchEntry*>(b->dev + k * b->buf_bytes + b->gmm_bytes);
-}
-int* dev_hdr(fos_batch* b, int k) { return reinterpret_cast<int*>(b->dev + k * b->buf_bytes + b->gmm_bytes + b->pbas_bytes); }
-uint8_t* host_buf(fos_batch* b, int k) { return b->host + k * b->buf_bytes; }
-
 bool gmm_on(const fos_batch* b) { return b->prm.methods & FOS_METHOD_GMM; }
 bool pbas_on(const fos_batch* b) { return b->prm.methods & FOS_METHOD_PBAS; }
 // Both methods with the 3+3 model: every tile runs GMM and PBAS in one kernel.
@@ -85,45 +81,91 @@ int effective_pbas_px(const fos_batch* b, int n, const int32_t* slots)
     return b->pbas_px;
 }
 
-// Captures (or reuses) the graph of argument buffer k for the shapes in use.
-fos_status ensure_graph(fos_batch* b, int k, int pbas_px)
+void drop_graph(fos_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_src) cudaGraphDestroy(b->graph_src);
+    b->graph = nullptr;
+    b->graph_src = nullptr;
+    b->node[0] = b->node[1] = nullptr;
+    b->graph_key = -1;
+}
+
+// Captures (or reuses) the step graph for the shapes in use: one launch of
+// each kernel the methods need, with the (empty) tables as parameters; the
+// kernel nodes are kept so each step can write its tables into them.
+fos_status ensure_graph(fos_batch* b, int pbas_px)
 {
     const int gpx = gmm_batch_px(b->prm.K_rgb, b->prm.K_d, b->gmm_px);
     const int key = gpx * 10000 + pbas_px * 100 + b->pbas_ty;
-    if (b->graph[k] && b->graph_key[k] == key) return FOS_OK;
-    if (b->graph[k]) {
-        cudaGraphExecDestroy(b->graph[k]);
-        b->graph[k] = nullptr;
-    }
-    int gblocks = 0, pblocks = 0;
+    if (b->graph && b->graph_key == key) return FOS_OK;
+    drop_graph(b);
     const bool fz = fused(b);
-    if (gmm_on(b) && !fz) gblocks = b->sms * std::max(1, gmm_batch_blocks_per_sm(b->prm.K_rgb, b->prm.K_d, b->gmm_px));
-    if (pbas_on(b)) pblocks = b->sms * std::max(1, pbas_batch_blocks_per_sm(b->prm.N, pbas_px, b->pbas_ty, fz));
+    b->blocks[0] = b->blocks[1] = 0;
+    if (gmm_on(b) && !fz) b->blocks[0] = b->sms * std::max(1, gmm_batch_blocks_per_sm(b->prm.K_rgb, b->prm.K_d, b->gmm_px));
+    if (pbas_on(b)) b->blocks[1] = b->sms * std::max(1, pbas_batch_blocks_per_sm(b->prm.N, pbas_px, b->pbas_ty, fz));
+    b->gt.n = b->gt.total = 0;
+    b->pt.n = b->pt.total = 0;
     FOS_BTRY(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemcpyAsync(b->dev + k * b->buf_bytes, host_buf(b, k), b->buf_bytes,
-                                    cudaMemcpyHostToDevice, b->cap);
     LaunchResult r = kLaunchOk;
-    if (e == cudaSuccess && gmm_on(b) && !fz)
-        r = launch_gmm_batch(dev_gmm(b, k), dev_hdr(b, k), gblocks, b->prm.K_rgb, b->prm.K_d, b->gmm_px, b->cap);
-    if (e == cudaSuccess && r == kLaunchOk && pbas_on(b))
-        r = launch_pbas_batch(dev_pbas(b, k), fz ? dev_gmm(b, k) : nullptr, dev_hdr(b, k), pblocks, b->prm.N,
-                              pbas_px, b->pbas_ty, b->cap);
+    if (b->blocks[0])
+        r = launch_gmm_batch(b->gt, b->blocks[0], b->prm.K_rgb, b->prm.K_d, b->gmm_px, b->cap);
+    if (r == kLaunchOk && b->blocks[1])
+        r = launch_pbas_batch(b->pt, fz, b->blocks[1], b->prm.N, pbas_px, b->pbas_ty, b->cap);
     cudaGraph_t g = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
-    if (e != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        return bcuda(b, "cudaMemcpyAsync (capture)", e);
-    }
+    cudaError_t e = cudaStreamEndCapture(b->cap, &g);
     if (r != kLaunchOk) {
         if (g) cudaGraphDestroy(g);
         return r == kLaunchUnsupported ? bfail(b, FOS_ERR_UNSUPPORTED, "batch: shape not compiled in")
                                        : bcuda(b, "batch launch (capture)", cudaGetLastError());
     }
-    if (e2 != cudaSuccess) return bcuda(b, "cudaStreamEndCapture", e2);
-    e = cudaGraphInstantiate(&b->graph[k], g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return bcuda(b, "cudaGraphInstantiate", e);
-    b->graph_key[k] = key;
+    if (e != cudaSuccess) return bcuda(b, "cudaStreamEndCapture", e);
+    b->graph_src = g;
+    // the kernel nodes in launch order (a chain: GMM first when present)
+    size_t n = 0;
+    FOS_BTRY(b, cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    FOS_BTRY(b, cudaGraphGetNodes(g, nodes.data(), &n));
+    int k = b->blocks[0] ? 0 : 1;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        FOS_BTRY(b, cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeKernel || k > 1) continue;
+        b->node[k] = nd;
+        FOS_BTRY(b, cudaGraphKernelNodeGetParams(nd, &b->kp[k]));
+        k = (k == 0 && b->blocks[1]) ? 1 : 2;
+    }
+    if ((b->blocks[0] && !b->node[0]) || (b->blocks[1] && !b->node[1])) {
+        drop_graph(b);
+        return bfail(b, FOS_ERR_CUDA, "batch: kernel node missing from the captured graph");
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e != cudaSuccess) {
+        drop_graph(b);
+        return bcuda(b, "cudaGraphInstantiate", e);
+    }
+    b->graph_key = key;
+    return FOS_OK;
+}
+
+// Writes the step's tables into the graph's kernel nodes and replays it.
+fos_status replay(fos_batch* b, cudaStream_t s)
+{
+    void* gargs[1] = {&b->gt};
+    void* pargs[1] = {&b->pt};
+    if (b->node[0]) {
+        cudaKernelNodeParams p = b->kp[0];
+        p.kernelParams = gargs;
+        p.extra = nullptr;
+        FOS_BTRY(b, cudaGraphExecKernelNodeSetParams(b->graph, b->node[0], &p));
+    }
+    if (b->node[1]) {
+        cudaKernelNodeParams p = b->kp[1];
+        p.kernelParams = pargs;
+        p.extra = nullptr;
+        FOS_BTRY(b, cudaGraphExecKernelNodeSetParams(b->graph, b->node[1], &p));
+    }
+    FOS_BTRY(b, cudaGraphLaunch(b->graph, s));
     return FOS_OK;
 }
 
@@ -168,39 +210,27 @@ fos_batch* fos_batch_create(int32_t max_streams, const fos_params* params)
     b->prm = *params;
     b->max_streams = max_streams;
     b->slot.assign(size_t(max_streams), nullptr);
-    auto round = [](size_t v) { return (v + 255) / 256 * 256; };
-    b->gmm_bytes = round(sizeof(GmmBatchEntry) * size_t(max_streams));
-    b->pbas_bytes = round(sizeof(PbasBatchEntry) * size_t(max_streams));
-    b->buf_bytes = b->gmm_bytes + b->pbas_bytes + 256;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev, 2 * b->buf_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->host, 2 * b->buf_bytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&b->done[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         bcuda(nullptr, "fos_batch_create", e);
         fos_batch_destroy(b);
         return nullptr;
     }
-    std::memset(b->host, 0, 2 * b->buf_bytes);
     return b;
 }
 
 void fos_batch_destroy(fos_batch* b)
 {
     if (!b) return;
-    for (int k = 0; k < 2; ++k)
-        if (b->done[k] && b->used[k]) cudaEventSynchronize(b->done[k]);
+    if (b->done && b->used) cudaEventSynchronize(b->done);
     for (fos_ctx* c : b->slot) fos_destroy(c);
-    for (int k = 0; k < 2; ++k) {
-        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
-        if (b->done[k]) cudaEventDestroy(b->done[k]);
-    }
+    drop_graph(b);
+    if (b->done) cudaEventDestroy(b->done);
     if (b->cap) cudaStreamDestroy(b->cap);
-    cudaFree(b->dev);
-    cudaFreeHost(b->host);
     delete b;
 }
 
@@ -232,8 +262,7 @@ fos_status fos_batch_remove_stream(fos_batch* b, int32_t slot)
     if (!b || slot < 0 || slot >= b->max_streams || !b->slot[slot])
         return bfail(b, FOS_ERR_INVALID_ARG, "no stream in that slot");
     // a step still in flight may use the stream's memory
-    for (int k = 0; k < 2; ++k)
-        if (b->used[k]) FOS_BTRY(b, cudaEventSynchronize(b->done[k]));
+    if (b->used) FOS_BTRY(b, cudaEventSynchronize(b->done));
     fos_destroy(b->slot[slot]);
     b->slot[slot] = nullptr;
     return FOS_OK;
@@ -266,44 +295,49 @@ fos_status fos_batch_process_device(fos_batch* b, int32_t n, const int32_t* slot
             return bfail(b, FOS_ERR_INVALID_ARG, "NULL frame pointer");
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int k = b->tick & 1;
-    if (b->used[k]) FOS_BTRY(b, cudaEventSynchronize(b->done[k]));  // host buffer k is free again
     const int px = effective_pbas_px(b, n, slots);
-    fos_status st = ensure_graph(b, k, px);
+    fos_status st = ensure_graph(b, px);
     if (st != FOS_OK) return st;
 
-    // per-stream arguments of this step
-    uint8_t* hb = host_buf(b, k);
-    GmmBatchEntry* ge = reinterpret_cast<GmmBatchEntry*>(hb);
-    PbasBatchEntry* pe = reinterpret_cast<PbasBatchEntry*>(hb + b->gmm_bytes);
-    int* hdr = reinterpret_cast<int*>(hb + b->gmm_bytes + b->pbas_bytes);
+    // per-stream arguments of this step, kBatchLaunchMax streams per replay
     const int gpx = gmm_batch_px(b->prm.K_rgb, b->prm.K_d, b->gmm_px);
-    int gblocks = 0, ptiles = 0;
-    for (int i = 0; i < n; ++i) {
-        fos_ctx* c = b->slot[slots[i]];
-        if (c->t == 0) FOS_BTRY(b, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
-        if (gmm_on(b)) {
-            ge[i].a = ctx_gmm_args(c, d_rgb[i], d_depth[i], d_mask_gmm[i]);
-            ge[i].block_off = gblocks;
-            gblocks += int((c->P + int64_t(kGmmBatchThreads) * gpx - 1) / (int64_t(kGmmBatchThreads) * gpx));
+    const bool fz = fused(b);
+    for (int i0 = 0; i0 < n; i0 += kBatchLaunchMax) {
+        const int m = std::min(n - i0, kBatchLaunchMax);
+        int gblocks = 0, ptiles = 0;
+        for (int j = 0; j < m; ++j) {
+            const int i = i0 + j;
+            fos_ctx* c = b->slot[slots[i]];
+            if (c->t == 0) FOS_BTRY(b, cudaMemsetAsync(c->aux, 0, 12 * sizeof(unsigned long long), s));
+            if (gmm_on(b)) {
+                const GmmArgs ga = ctx_gmm_args(c, d_rgb[i], d_depth[i], d_mask_gmm[i]);
+                if (fz) {
+                    b->pt.g[j] = ga;
+                } else {
+                    b->gt.e[j].a = ga;
+                    b->gt.e[j].block_off = gblocks;
+                    gblocks += int((c->P + int64_t(kGmmBatchThreads) * gpx - 1) / (int64_t(kGmmBatchThreads) * gpx));
+                }
+            }
+            if (pbas_on(b)) {
+                PbasBatchEntry& e = b->pt.e[j];
+                e.a = ctx_pbas_args(c, d_rgb[i], d_depth[i], d_mask_pbas[i]);
+                e.a.mask_vec = (reinterpret_cast<uintptr_t>(d_mask_pbas[i]) % uintptr_t(px)) == 0 ? 1 : 0;
+                e.tile_off = ptiles;
+                e.tiles_x = (c->W + 32 * px - 1) / (32 * px);
+                e.init = c->t == 0 ? 1 : 0;
+                ptiles += e.tiles_x * ((c->H + b->pbas_ty - 1) / b->pbas_ty);
+            }
         }
-        if (pbas_on(b)) {
-            pe[i].a = ctx_pbas_args(c, d_rgb[i], d_depth[i], d_mask_pbas[i]);
-            pe[i].a.mask_vec = (reinterpret_cast<uintptr_t>(d_mask_pbas[i]) % uintptr_t(px)) == 0 ? 1 : 0;
-            pe[i].tile_off = ptiles;
-            pe[i].tiles_x = (c->W + 32 * px - 1) / (32 * px);
-            pe[i].init = c->t == 0 ? 1 : 0;
-            ptiles += pe[i].tiles_x * ((c->H + b->pbas_ty - 1) / b->pbas_ty);
-        }
+        b->gt.n = gmm_on(b) && !fz ? m : 0;
+        b->gt.total = gblocks;
+        b->pt.n = pbas_on(b) ? m : 0;
+        b->pt.total = ptiles;
+        st = replay(b, s);
+        if (st != FOS_OK) return st;
     }
-    hdr[0] = n;
-    hdr[1] = ptiles;
-    hdr[2] = gblocks;
-    hdr[3] = 0;  // tile counter of the PBAS kernel (copied in with the arguments)
-    FOS_BTRY(b, cudaGraphLaunch(b->graph[k], s));
-    FOS_BTRY(b, cudaEventRecord(b->done[k], s));
-    b->used[k] = true;
-    b->tick += 1;
+    FOS_BTRY(b, cudaEventRecord(b->done, s));
+    b->used = true;
     for (int i = 0; i < n; ++i) ctx_frame_done(b->slot[slots[i]]);
     return FOS_OK;
 }

@@ -67,18 +67,28 @@ int gmm_literal_planes(int Kr, int Kd);
 bool gmm_literal_supported(int Kr, int Kd);
 LaunchResult launch_gmm_literal(const GmmLiteralArgs& a, int Kr, int Kd, cudaStream_t s);
 
-// One stream of a batched GMM launch (device memory).
+// Streams per batched launch: the argument table of a launch travels as a
+// __grid_constant__ kernel parameter (below the 32 KB parameter limit), so
+// the kernels read every stream's arguments from the constant bank with
+// block-uniform indexed loads and nothing is staged through device memory.
+// A step with more streams takes several launches.
+constexpr int kBatchLaunchMax = 48;
+
+// One stream of a batched GMM launch.
 struct GmmBatchEntry {
     GmmArgs a;
     int block_off;  // first block of this stream in the launch
     int pad[3];
 };
-// Persistent batched GMM launch over hdr[0] entries and hdr[2] blocks of
-// kGmmBatchThreads threads; every stream uses the same (Kr, Kd) and pixels
-// per thread.
+struct GmmBatchTable {
+    int n, total;  // entries, blocks of kGmmBatchThreads threads
+    int pad[2];
+    GmmBatchEntry e[kBatchLaunchMax];
+};
+// Persistent batched GMM launch over t.n entries and t.total blocks; every
+// stream uses the same (Kr, Kd) and pixels per thread.
 constexpr int kGmmBatchThreads = 128;
-LaunchResult launch_gmm_batch(const GmmBatchEntry* E, const int* hdr, int blocks, int Kr, int Kd,
-                              int px, cudaStream_t s);
+LaunchResult launch_gmm_batch(const GmmBatchTable& t, int blocks, int Kr, int Kd, int px, cudaStream_t s);
 int gmm_batch_px(int Kr, int Kd, int px);
 int gmm_batch_blocks_per_sm(int Kr, int Kd, int px);
 
@@ -145,7 +155,7 @@ LaunchResult launch_pbas_joint(const PbasArgs& a, cudaStream_t s);
 // GMM (3+3 components) and PBAS of one frame in one launch (frames >= 1).
 LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStream_t s);
 
-// One stream of a batched launch (device memory, one entry per stream).
+// One stream of a batched launch (one entry per stream).
 struct PbasBatchEntry {
     PbasArgs a;
     int tile_off;  // first tile of this stream in the launch
@@ -153,11 +163,17 @@ struct PbasBatchEntry {
     int init;      // 1: frame 0 of this stream
     int pad;
 };
-// Persistent batched PBAS launch over hdr[0] entries and hdr[1] tiles; hdr[3]
-// is the tile counter the blocks claim from (must be zero at launch).  With
-// G non-NULL (3+3-component GMM) each tile also runs the GMM of its pixels.
-LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, int* hdr,
-                               int blocks, int N, int px, int ty, cudaStream_t s);
+struct PbasBatchTable {
+    int n, total;  // entries, tiles
+    int pad[2];
+    PbasBatchEntry e[kBatchLaunchMax];
+    GmmArgs g[kBatchLaunchMax];  // fused launches: the GMM arguments of entry i
+};
+// Persistent batched PBAS launch over t.n entries and t.total tiles (blocks
+// take tiles round-robin).  fused (3+3-component GMM): each tile also runs the
+// GMM of its pixels.
+LaunchResult launch_pbas_batch(const PbasBatchTable& t, bool fused, int blocks, int N, int px, int ty,
+                               cudaStream_t s);
 int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused);
 
 // Depth frame sw x sh resampled onto dw x dh (nearest, floor mapping).

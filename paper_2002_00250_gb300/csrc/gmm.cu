@@ -86,34 +86,21 @@ __global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
     gmm_pixels<KR, KD, PX>(a, (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * PX);
 }
 
-// Many streams in one persistent launch: entry i holds stream i's arguments
-// and its first block in the launch; blocks walk the launch's blocks with a
-// grid stride (counts read from device memory, see the PBAS batch kernel).
+// Many streams in one persistent launch: entry i of the table (a
+// __grid_constant__ parameter, read from the constant bank) holds stream i's
+// arguments and its first block in the launch; blocks take the launch's
+// blocks round-robin.
 template <int KR, int KD, int PX>
-__global__ void __launch_bounds__(kGmmBatchThreads) gmm_batch_kernel(const GmmBatchEntry* __restrict__ E,
-                                                        const int* __restrict__ hdr)
+__global__ void __launch_bounds__(kGmmBatchThreads) gmm_batch_kernel(const __grid_constant__ GmmBatchTable T)
 {
-    __shared__ __align__(16) GmmArgs sa;
-    const int n = hdr[0], total = hdr[2];
-    const int chunk = (total + int(gridDim.x) - 1) / int(gridDim.x);
-    const int it0 = int(blockIdx.x) * chunk, it1 = min(total, it0 + chunk);
-    int cur = -1;
-    for (int it = it0; it < it1; ++it) {
-        int lo = 0, hi = n - 1;
+    for (int it = blockIdx.x; it < T.total; it += gridDim.x) {
+        int lo = 0, hi = T.n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (E[mid].block_off <= it) lo = mid;
+            if (T.e[mid].block_off <= it) lo = mid;
             else hi = mid - 1;
         }
-        if (lo != cur) {
-            __syncthreads();
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&E[lo].a);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
-            for (int w = threadIdx.x; w < int(sizeof(GmmArgs) / 4); w += blockDim.x) dst[w] = src[w];
-            __syncthreads();
-            cur = lo;
-        }
-        gmm_pixels<KR, KD, PX>(sa, (int64_t(it - E[lo].block_off) * blockDim.x + threadIdx.x) * PX);
+        gmm_pixels<KR, KD, PX>(T.e[lo].a, (int64_t(it - T.e[lo].block_off) * blockDim.x + threadIdx.x) * PX);
     }
 }
 
@@ -162,13 +149,12 @@ int gmm_batch_px(int Kr, int Kd, int px)
     X(3, 1, 1) X(3, 2, 1) X(5, 2, 1) X(7, 2, 1) X(1, 2, 1) X(1, 3, 1) X(2, 3, 1)        \
     X(5, 1, 1) X(7, 1, 1)
 
-LaunchResult launch_gmm_batch(const GmmBatchEntry* E, const int* hdr, int blocks, int Kr, int Kd,
-                              int px, cudaStream_t s)
+LaunchResult launch_gmm_batch(const GmmBatchTable& t, int blocks, int Kr, int Kd, int px, cudaStream_t s)
 {
     const int p = gmm_batch_px(Kr, Kd, px);
 #define FOS_B(R, D, PX)                                                                    \
     if (Kr == R && Kd == D && p == PX) {                                                   \
-        gmm_batch_kernel<R, D, PX><<<blocks, kGmmBatchThreads, 0, s>>>(E, hdr);            \
+        gmm_batch_kernel<R, D, PX><<<blocks, kGmmBatchThreads, 0, s>>>(t);                 \
         return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;           \
     }
     FOS_GMM_BATCH_CASES(FOS_B)

@@ -29,7 +29,9 @@ namespace {
 
 // One tile (32*PX x TY pixels at x0, y0) of the classify pass of one stream.
 // build_table: recompute the gradient-weight table (the stream changed).
-template <int NT, int PX, int TY, int KR = 0, int KD = 0>
+// GPAIR: the GMM part moves two pixels' state with 8-byte accesses (more
+// registers live; the persistent batched kernel keeps the one-pixel form).
+template <int NT, int PX, int TY, int KR = 0, int KD = 0, bool GPAIR = true>
 __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* gm, int x0, int y0,
                                               ClassifySmem<PX, TY>& S, bool build_table)
 {
@@ -44,23 +46,20 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         if (py < a.H && px < a.W) prefetch_channel<NT>(a, N, 0, px, py, int64_t(py) * a.Wp + px);
     }
     stage_input<PX, TY>(a, x0, y0, sm);
+    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
     if (a.apply) stage_requests<PX, TY>(a, x0, y0, sreq);
     if (build_table && tid < 4) {
         // gradient weight: alpha_g / mean gradient magnitude of the previous frame
         float mean = __fdiv_rn(__ull2float_rn(a.gsum_prev[tid]), __ll2float_rn(a.P));
         mean = fmaxf(mean, 1.0f);
         S.wgs[tid] = __fdiv_rn(a.alpha_g, mean);
+        if (tid == 0) S.rn16 = __frcp_rn(__int2float_rn(16 * N));
     }
     if (x0 == 0 && y0 == 0 && tid >= 4 && tid < 8) a.gsum_next[tid - 4] = 0ull;
     __syncthreads();
-    if (build_table) {
-        for (int e = tid; e < 1024; e += 32 * TY)
-            S.wtab[e >> 8][e & 255] = __fmul_rn(S.wgs[e >> 8], __int2float_rn(e & 255));
-        __syncthreads();
-    }
-    if constexpr (KR > 0) gmm_tile_part<KR, KD, PX, TY>(*gm, a, x0, y0, sm);
 
-    const int lx0 = threadIdx.x * PX, ly = threadIdx.y;
+    if constexpr (KR > 0) gmm_tile_part<KR, KD, PX, TY, GPAIR>(*gm, a, x0, y0, sm);
+
     const int x = x0 + lx0, y = y0 + ly;
     bool inb[PX];
 #pragma unroll
@@ -114,7 +113,6 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 
 #pragma unroll 1
     for (int c = 0; c < 4; ++c) {
-        const float* tab = S.wtab[c];
         uint32_t pv[PX];   // this frame's (value | gradient << 8)
         bool act[PX];
         bool any = false;
@@ -157,7 +155,7 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         if (c < 3 && inb[0]) prefetch_channel<NT>(a, N, c + 1, x, y, q0);
 
         // distances to the N samples: count within R, minimum.
-        // dist = fl(fl(wg * |dg|) + |dv|): the product comes from the table.
+        // dist = fl(fl(wg * |dg|) + |dv|), each operation rounded once.
         uint32_t own[NW];
 #pragma unroll
         for (int w = 0; w < NW; ++w) own[w] = pv[2 * w] | (2 * w + 1 < PX ? pv[2 * w + 1] << 16 : 0u);
@@ -166,6 +164,9 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 #pragma unroll
         for (int i = 0; i < PX; ++i) { cnt[i] = 0; dmin[i] = INFINITY; }
         const int64_t sb = inb[0] ? sidx(a, N, c, 0, x, y) : 0;  // slot 0 of pixel x
+        // dist = fl(fl(wg * |dg|) + |dv|): a byte b is the float (2^23 + b) - 2^23
+        // exactly (a byte permute and a subtraction instead of a conversion)
+        const float wgc = S.wgs[c];
 #pragma unroll(NT > 0 ? NT : 4)
         for (int k = 0; k < N; ++k) {
             uint32_t s[NW];
@@ -176,14 +177,16 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
             }
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
-                const uint32_t d = __vabsdiffu4(s[w], own[w]);
+                const uint32_t d = __vabsdiffu4(s[w], own[w]);  // |dv0| |dg0| |dv1| |dg1|
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int i = 2 * w + h;
                     if (i >= PX) break;
-                    const uint32_t dv = (d >> (16 * h)) & 0xFFu;
-                    const uint32_t dg = (d >> (16 * h + 8)) & 0xFFu;
-                    const float dist = __fadd_rn(tab[dg], __uint2float_rn(dv));
+                    const float fv = __fsub_rn(__uint_as_float(__byte_perm(d, 0x4B000000u, h ? 0x7442 : 0x7440)),
+                                               8388608.f);
+                    const float fgd = __fsub_rn(__uint_as_float(__byte_perm(d, 0x4B000000u, h ? 0x7443 : 0x7441)),
+                                                8388608.f);
+                    const float dist = __fadd_rn(__fmul_rn(wgc, fgd), fv);
                     cnt[i] += dist < Rv[i] ? 1 : 0;
                     dmin[i] = fminf(dmin[i], dist);
                 }
@@ -200,8 +203,7 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
             slot[i] = -1;
             oidx[i] = 0;
             if (act[i] && !fg[i]) {
-                const float prob = __frcp_rn(Tv[i]);
-                const Draws d = draws(a, pix0 + uint32_t(i), uint32_t(c), prob, N);
+                const Draws d = draws(a, pix0 + uint32_t(i), uint32_t(c), __frcp_rn(Tv[i]), N);
                 if (d.coin1) {
                     slot[i] = int(d.k1);
                     oidx[i] = sidx(a, N, c, int(d.k1), x + i, y);
@@ -234,12 +236,14 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             if (!act[i]) continue;
-            const float dbar = fmaxf(__fdiv_rn(__uint2float_rn(Sv[i]), n16), a.eps_d);
+            // mean quantised minimal distance S / (16 N), correctly rounded
+            const float dbar = fmaxf(div_int_const(Sv[i], n16, S.rn16), a.eps_d);
             const float Rs = __fmul_rn(dbar, a.R_scale);
             const float Rn = Rv[i] > Rs ? __fmul_rn(Rv[i], omr) : __fmul_rn(Rv[i], opr);
             Rv[i] = Rn < Rlo ? Rlo : Rn;
-            float Tn = fg[i] ? __fadd_rn(Tv[i], __fdiv_rn(a.T_inc, dbar))
-                             : __fsub_rn(Tv[i], __fdiv_rn(a.T_dec, dbar));
+            // T + T_inc / dbar or T - T_dec / dbar: one division of the chosen
+            // numerator (fl(-x / y) = -fl(x / y))
+            float Tn = __fadd_rn(Tv[i], __fdiv_rn(fg[i] ? a.T_inc : -a.T_dec, dbar));
             Tn = Tn < a.T_lower ? a.T_lower : Tn;
             Tv[i] = Tn > a.T_upper ? a.T_upper : Tn;
         }
@@ -387,55 +391,32 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
     init_tile<NT, PX, TY>(a, nullptr, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, sm);
 }
 
-// Many streams in one persistent launch.  Entry i of the batch holds stream
-// i's arguments, whether it is at frame 0, its tile offset in the launch
-// (prefix sum) and its tiles per row.  Blocks claim tiles one at a time from
-// a counter (hdr[3], zero at launch) in launch order, so the hardware keeps
-// every block busy whatever the mix of stream sizes and tile costs.  The
-// count of entries and tiles is read from device memory, so one captured
-// graph serves any batch composition.
+// Many streams in one persistent launch.  Entry i of the table holds stream
+// i's arguments, whether it is at frame 0, its first tile in the launch
+// (prefix sum) and its tiles per row; the table is a __grid_constant__
+// parameter, so the arguments are read from the constant bank (one copy per
+// launch, shared by every block).  Blocks take tiles round-robin: tiles of
+// one stream cost alike, and consecutive tiles of a block come from streams
+// spread over the launch, so the blocks finish together without a work
+// counter.
 template <int NT, int PX, int TY, int KR>
 __global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
-pbas_batch_kernel(const PbasBatchEntry* __restrict__ E, const GmmBatchEntry* __restrict__ GE,
-                  int* __restrict__ hdr)
+pbas_batch_kernel(const __grid_constant__ PbasBatchTable T)
 {
     constexpr int KD = KR;
     __shared__ ClassifySmem<PX, TY> S;
-    __shared__ __align__(16) PbasArgs sa;
-    __shared__ __align__(16) GmmArgs sg;
-    __shared__ int s_it;
-    const int n = hdr[0], total = hdr[1];
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    int cur = -1;  // entry whose arguments (and weight table) are loaded
-    for (;;) {
-        if (tid == 0) s_it = atomicAdd(&hdr[3], 1);
-        __syncthreads();
-        const int it = s_it;
-        if (it >= total) break;
-        int lo = 0, hi = n - 1;  // entry whose tile range holds `it`
+    for (int it = blockIdx.x; it < T.total; it += gridDim.x) {
+        int lo = 0, hi = T.n - 1;  // entry whose tile range holds `it`
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (E[mid].tile_off <= it) lo = mid;
+            if (T.e[mid].tile_off <= it) lo = mid;
             else hi = mid - 1;
         }
-        const bool fresh = lo != cur;
-        if (fresh) {
-            __syncthreads();
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&E[lo].a);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&sa);
-            for (int w = tid; w < int(sizeof(PbasArgs) / 4); w += 32 * TY) dst[w] = src[w];
-            if constexpr (KR > 0) {
-                const uint32_t* gsrc = reinterpret_cast<const uint32_t*>(&GE[lo].a);
-                uint32_t* gdst = reinterpret_cast<uint32_t*>(&sg);
-                for (int w = tid; w < int(sizeof(GmmArgs) / 4); w += 32 * TY) gdst[w] = gsrc[w];
-            }
-            __syncthreads();
-            cur = lo;
-        }
-        const int local = it - E[lo].tile_off, tx = E[lo].tiles_x;
+        const PbasBatchEntry& E = T.e[lo];
+        const int local = it - E.tile_off, tx = E.tiles_x;
         const int x0 = (local % tx) * Geo<PX, TY>::TW, y0 = (local / tx) * TY;
-        if (E[lo].init) init_tile<NT, PX, TY, KR, KD>(sa, &sg, x0, y0, S.sm);
-        else classify_tile<NT, PX, TY, KR, KD>(sa, &sg, x0, y0, S, fresh);
+        if (E.init) init_tile<NT, PX, TY, KR, KD>(E.a, &T.g[lo], x0, y0, S.sm);
+        else classify_tile<NT, PX, TY, KR, KD>(E.a, &T.g[lo], x0, y0, S, true);
         __syncthreads();
     }
 }
@@ -510,24 +491,23 @@ LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStre
 }
 
 template <int NT, int KR>
-bool batch_shape(const PbasBatchEntry* E, const GmmBatchEntry* G, int* hdr, int blocks, int px,
-                 int ty, cudaStream_t s)
+bool batch_shape(const PbasBatchTable& t, int blocks, int px, int ty, cudaStream_t s)
 {
-    if (px == 2 && ty == 8) pbas_batch_kernel<NT, 2, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
-    else if (px == 2 && ty == 4) pbas_batch_kernel<NT, 2, 4, KR><<<blocks, dim3(32, 4), 0, s>>>(E, G, hdr);
-    else if (px == 4 && ty == 4) pbas_batch_kernel<NT, 4, 4, KR><<<blocks, dim3(32, 4), 0, s>>>(E, G, hdr);
-    else if (px == 4 && ty == 8) pbas_batch_kernel<NT, 4, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
-    else if (px == 1 && ty == 8) pbas_batch_kernel<NT, 1, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(E, G, hdr);
+    if (px == 2 && ty == 8) pbas_batch_kernel<NT, 2, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(t);
+    else if (px == 2 && ty == 4) pbas_batch_kernel<NT, 2, 4, KR><<<blocks, dim3(32, 4), 0, s>>>(t);
+    else if (px == 4 && ty == 4) pbas_batch_kernel<NT, 4, 4, KR><<<blocks, dim3(32, 4), 0, s>>>(t);
+    else if (px == 4 && ty == 8) pbas_batch_kernel<NT, 4, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(t);
+    else if (px == 1 && ty == 8) pbas_batch_kernel<NT, 1, 8, KR><<<blocks, dim3(32, 8), 0, s>>>(t);
     else return false;
     return true;
 }
 
-LaunchResult launch_pbas_batch(const PbasBatchEntry* E, const GmmBatchEntry* G, int* hdr,
-                               int blocks, int N, int px, int ty, cudaStream_t s)
+LaunchResult launch_pbas_batch(const PbasBatchTable& t, bool fused, int blocks, int N, int px, int ty,
+                               cudaStream_t s)
 {
     bool ok;
-    if (G) ok = N == 20 ? batch_shape<20, 3>(E, G, hdr, blocks, px, ty, s) : batch_shape<0, 3>(E, G, hdr, blocks, px, ty, s);
-    else ok = N == 20 ? batch_shape<20, 0>(E, G, hdr, blocks, px, ty, s) : batch_shape<0, 0>(E, G, hdr, blocks, px, ty, s);
+    if (fused) ok = N == 20 ? batch_shape<20, 3>(t, blocks, px, ty, s) : batch_shape<0, 3>(t, blocks, px, ty, s);
+    else ok = N == 20 ? batch_shape<20, 0>(t, blocks, px, ty, s) : batch_shape<0, 0>(t, blocks, px, ty, s);
     if (!ok) return kLaunchUnsupported;
     return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
 }
