@@ -488,13 +488,16 @@ typedef struct fos_softgmm_params {
     int32_t K_rgb, K_d;                         /* must be 3 and 3 */
     int32_t ckpt_every;                         /* frames between checkpoints, 1..16 */
     uint32_t depth_full_scale_mm;
+    int32_t fp64;                               /* 0: FP32 state and adjoint (fast);
+                                                   1: FP64 throughout (checkpoints 8 B) */
 } fos_softgmm_params;
 
 typedef struct fos_softgmm fos_softgmm;
 
 void fos_softgmm_default_params(fos_softgmm_params* p);
 /* Workspace for `batch` sequences of `frames` frames of width x height:
- * checkpoints of the model every ckpt_every frames (24 floats per pixel each). */
+ * checkpoints of the model every ckpt_every frames (24 values per pixel each,
+ * 4 or 8 bytes by params->fp64). */
 fos_softgmm* fos_softgmm_create(int32_t width, int32_t height, int32_t batch, int32_t frames,
                                 const fos_softgmm_params* params);
 void fos_softgmm_destroy(fos_softgmm* g);
@@ -502,6 +505,9 @@ const char* fos_softgmm_last_error(const fos_softgmm* g);
 /* Replaces theta (alpha, lambda2, w_depth, v_init_rgb); the next backward
  * needs a forward with the new values. */
 fos_status fos_softgmm_set_theta(fos_softgmm* g, const float theta[4]);
+/* The same with double values: with fp64 = 1 the kernels use them unrounded
+ * (finite differences of the loss need steps below float resolution). */
+fos_status fos_softgmm_set_theta64(fos_softgmm* g, const double theta[4]);
 /*
  * Forward over device sequences rgb [batch][frames][H][W][3] u8,
  * depth [batch][frames][H][W] u16 (mm, 0 invalid), gt [batch][frames][H][W]

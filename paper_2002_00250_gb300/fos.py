@@ -78,7 +78,7 @@ class SoftParams(ctypes.Structure):
                 ("v_min_rgb", ctypes.c_float), ("v_min_d", ctypes.c_float),
                 ("v_init_d_ratio", ctypes.c_float), ("K_rgb", ctypes.c_int32),
                 ("K_d", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
-                ("depth_full_scale_mm", ctypes.c_uint32)]
+                ("depth_full_scale_mm", ctypes.c_uint32), ("fp64", ctypes.c_int32)]
 
 
 class ServerResult(ctypes.Structure):
@@ -151,6 +151,7 @@ SIGNATURES = {
     "fos_softgmm_destroy": (None, [_vp]),
     "fos_softgmm_last_error": (ctypes.c_char_p, [_vp]),
     "fos_softgmm_set_theta": (_st, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "fos_softgmm_set_theta64": (_st, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "fos_softgmm_forward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "fos_softgmm_backward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
 }

@@ -22,7 +22,8 @@ def default_params(**overrides) -> fos.SoftParams:
 
 
 class SoftGMM:
-    """Workspace for B sequences of T frames of W x H (checkpoints live here)."""
+    """Workspace for B sequences of T frames of W x H (checkpoints live here).
+    fp64=1 (a params field) runs the recurrence and the adjoint in double."""
 
     def __init__(self, width: int, height: int, batch: int, frames: int, params=None, **overrides):
         self.lib = fos.load()
@@ -48,8 +49,10 @@ class SoftGMM:
             raise fos.FosError(st, self.lib.fos_softgmm_last_error(self.h).decode())
 
     def set_theta(self, theta) -> None:
-        arr = (ctypes.c_float * 4)(*[float(v) for v in theta])
-        self._check(self.lib.fos_softgmm_set_theta(self.h, arr))
+        """theta = (alpha, lambda^2, w_depth, v_init_rgb); kept in double (the
+        FP32 kernels round it to float, the FP64 ones use it as given)."""
+        arr = (ctypes.c_double * 4)(*[float(v) for v in theta])
+        self._check(self.lib.fos_softgmm_set_theta64(self.h, arr))
 
     def forward(self, rgb, depth, gt, stream=None) -> float:
         out = ctypes.c_double()

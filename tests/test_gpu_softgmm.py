@@ -98,3 +98,62 @@ def test_autograd_function_and_descent():
         th1 = theta * torch.exp(1e-4 * d / d.abs().max())
     l1 = softgmm.SoftGMMLoss.apply(th1, ws, *data)
     assert float(l1.detach()) < float(loss.detach())
+
+
+def _gpu64(rgb, depth, gt, theta, pixel=False):
+    import torch
+    from paper_2002_00250_gb300 import softgmm
+    B, T, H, W = rgb.shape[:4]
+    ws = softgmm.SoftGMM(W, H, B, T, fp64=1)
+    ws.set_theta(theta)
+    d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (rgb, depth, gt)]
+    loss = ws.forward(*d)
+    pg = torch.zeros((B, H * W, 4), dtype=torch.float32, device="cuda") if pixel else None
+    g = np.array(ws.backward(*d, pixel_grad=pg))
+    ws.close()
+    return loss, g, (pg.cpu().numpy().astype(np.float64) if pixel else None)
+
+
+@pytest.mark.parametrize("seed", [80, 81])
+def test_fp64_adjoint_matches_finite_differences_and_oracle(seed):
+    """FP64 kernels on 32x32 crops (2 sequences, 12 frames): the hand-written
+    adjoint agrees with central finite differences of the GPU's own forward
+    and with the FP64 oracle's autograd adjoint, both to 1e-5 relative; the
+    loss agrees with the oracle to 1e-10.  The step is h = 1e-4 |theta_i|
+    (every hard decision of the forward the same at theta +/- h): on these
+    crops the difference quotient's round-off grows as 1/h and is already
+    3e-4 relative at h = 1e-6 |theta| for the oracle's own forward, while the
+    truncation error at 1e-4 is of order 1e-8."""
+    from oracle import softgmm as osg
+    rgb, depth, gt = _data(2, 32, 32, 12, seed=seed)
+    l_g, g_g, pg = _gpu64(rgb, depth, gt, THETA, pixel=True)
+    # the library's fixed parameters are floats: give the oracle the same values
+    kw = dict(T_bg=float(np.float32(0.7)), v_init_d_ratio=float(np.float32(4.0 / 36.0)))
+    l_o, g_o = osg.loss_and_grad(rgb, depth, gt, THETA, **kw)
+    assert l_g == pytest.approx(l_o, rel=1e-10)
+    scale = np.abs(g_o * np.array(THETA)).max() / np.abs(np.array(THETA))
+    np.testing.assert_array_less(np.abs(g_g - g_o), 1e-5 * np.maximum(np.abs(g_o), 1e-3 * scale))
+    # per-pixel contributions sum to the total (float output, 1e-6)
+    np.testing.assert_allclose(pg.sum(axis=(0, 1)), g_g, rtol=1e-5, atol=1e-9 * np.abs(g_g).max())
+    fp0 = osg.fingerprint(rgb, depth, gt, THETA, **kw)
+    checked = 0
+    for i in range(4):
+        h = 1e-4 * abs(THETA[i])
+        tp = list(THETA); tp[i] += h
+        tm = list(THETA); tm[i] -= h
+        if not (osg.fingerprint(rgb, depth, gt, tp, **kw) == fp0 == osg.fingerprint(rgb, depth, gt, tm, **kw)):
+            continue
+        lp = _gpu64(rgb, depth, gt, tp)[0]
+        lm = _gpu64(rgb, depth, gt, tm)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g_g[i]) <= 1e-5 * max(abs(g_g[i]), 1e-3 * scale[i]), (i, fd, g_g[i])
+        checked += 1
+    assert checked >= 3
+
+
+def test_fp64_and_fp32_agree_to_fp32_accuracy():
+    rgb, depth, gt = _data(1, 24, 16, 10, seed=90)
+    l32, g32, _ = _run_gpu(rgb, depth, gt, THETA, pixel=False)
+    l64, g64, _ = _gpu64(rgb, depth, gt, THETA)
+    assert l32 == pytest.approx(l64, rel=1e-4)
+    np.testing.assert_allclose(g32, g64, rtol=5e-2, atol=1e-3 * np.abs(g64).max())
