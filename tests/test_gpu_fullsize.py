@@ -4,9 +4,11 @@ The 1280x720 benchmark sequence (camouflage, illumination ramp, shadows),
 generated on the device as the benchmark does, both methods in one context
 through the device API on a side stream (the fused kernel the benchmark
 times): PBAS masks bit-exact at every frame and its whole model bit-exact at
-the end; GMM masks equal except at pixels whose oracle margin ever came
-within 1e-5 of a threshold, and the GMM model within the FP32 tolerance
-elsewhere.  The first frames of the sequence keep the oracle's run short.
+the end of every 100-frame chunk; GMM masks equal except at pixels whose
+oracle margin ever came within 1e-5 of a threshold, and the GMM model within
+the FP32 tolerance elsewhere.  All 300 frames: the bootstrap, the objects'
+passes, the 0.6 -> 1.2 illumination ramp of frames 100-200 and the long-run
+R, T, D dynamics.
 """
 import numpy as np
 import pytest
@@ -22,31 +24,38 @@ MARGIN = 1e-5
 def test_1280x720_benchmark_configuration(orc):
     import torch
     from paper_2002_00250_gb300 import fos, synth
-    n = 12
+    n, chunk = 300, 100
     sc = synth.RGBDScene(synth.config_720p(seed=0), device="cuda")
-    d_rgb, d_dep, _ = sc.sequence(0, n)
     W, H = 1280, 720
     seg = fos.Segmenter(W, H)
-    mg = torch.empty((n, H, W), dtype=torch.uint8, device="cuda")
-    mp = torch.empty_like(mg)
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        seg.process_device(d_rgb, d_dep, mg, mp, stream=stream)
-    torch.cuda.synchronize()
-    rgb, depth = synth.to_numpy(d_rgb), synth.to_numpy(d_dep)
     g = orc.GMM(W, H, **oracle_gmm_params(seg.params))
     p = orc.PBAS(W, H, **oracle_pbas_params(seg.params))
-    mg_h, mp_h = mg.cpu().numpy(), mp.cpu().numpy()
+    stream = torch.cuda.Stream()
     bad = np.zeros(W * H, bool)
-    for t in range(n):
-        np.testing.assert_array_equal(mp_h[t], p.step(rgb[t], depth[t]), err_msg=f"PBAS frame {t}")
-        mo, margin = g.step(rgb[t], depth[t], want_margin=True)
-        bad |= (margin < MARGIN).ravel()
-        np.testing.assert_array_equal(mg_h[t].ravel()[~bad], mo.ravel()[~bad], err_msg=f"GMM frame {t}")
-    st = seg.decode_state()
-    assert_same(st.pbas, p, n - 1)
-    for name in ("w_rgb", "mu_rgb", "v_rgb", "w_d", "mu_d", "v_d"):
-        good = close(st.gmm[name], getattr(g, name)).reshape(W * H, -1).all(axis=1)
-        assert good[~bad].all(), name
-    assert bad.mean() < 0.01
-    assert mp_h[1:].any() and mg_h[1:].any()
+    fg_g = fg_p = 0
+    for c0 in range(0, n, chunk):
+        d_rgb, d_dep, _ = sc.sequence(c0, chunk)
+        mg = torch.empty((chunk, H, W), dtype=torch.uint8, device="cuda")
+        mp = torch.empty_like(mg)
+        with torch.cuda.stream(stream):
+            seg.process_device(d_rgb, d_dep, mg, mp, stream=stream)
+        torch.cuda.synchronize()
+        rgb, depth = synth.to_numpy(d_rgb), synth.to_numpy(d_dep)
+        mg_h, mp_h = mg.cpu().numpy(), mp.cpu().numpy()
+        for k in range(chunk):
+            t = c0 + k
+            np.testing.assert_array_equal(mp_h[k], p.step(rgb[k], depth[k]), err_msg=f"PBAS frame {t}")
+            mo, margin = g.step(rgb[k], depth[k], want_margin=True)
+            bad |= (margin < MARGIN).ravel()
+            np.testing.assert_array_equal(mg_h[k].ravel()[~bad], mo.ravel()[~bad], err_msg=f"GMM frame {t}")
+        fg_g += int(mg_h.astype(bool).sum())
+        fg_p += int(mp_h.astype(bool).sum())
+        st = seg.decode_state()
+        assert_same(st.pbas, p, c0 + chunk - 1)
+        for name in ("w_rgb", "mu_rgb", "v_rgb", "w_d", "mu_d", "v_d"):
+            good = close(st.gmm[name], getattr(g, name)).reshape(W * H, -1).all(axis=1)
+            assert good[~bad].all(), (c0 + chunk - 1, name)
+    # over 300 frames about 3 % of the pixels come within 1e-5 of a GMM
+    # threshold at some frame (the illumination ramp moves every pixel)
+    assert bad.mean() < 0.05
+    assert fg_g > 0 and fg_p > 0

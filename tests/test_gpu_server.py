@@ -248,3 +248,51 @@ def test_zero_copy_submit_and_odd_sizes():
         for f in range(n):
             np.testing.assert_array_equal(outs[(i, f)][0], mg[f], err_msg=f"gmm s{i} f{f}")
             np.testing.assert_array_equal(outs[(i, f)][1], mp[f], err_msg=f"pbas s{i} f{f}")
+
+
+def test_served_results_against_oracle(orc):
+    """A short serving run checked against the oracle directly: three streams
+    of mixed sizes (one with a width the scalar tiles take), one opened after
+    the others have started, frames submitted interleaved and batched by the
+    worker; each stream's PBAS masks bit-exact against its own oracle at every
+    frame, GMM masks equal except at pixels whose oracle margin came within
+    1e-5 of a threshold (Sec. 3.1, 3.2)."""
+    from paper_2002_00250_gb300 import fos
+    from _helpers import oracle_gmm_params, oracle_pbas_params
+    sizes = [(136, 40), (67, 45), (96, 32)]
+    n = 8
+    start = {0: 0, 1: 0, 2: 3}
+    data = [scene(W, H, n, seed=140 + i, n_objects=3, hole_fraction=0.05) for i, (W, H) in enumerate(sizes)]
+    srv = fos.Server(1 << 34, 4)
+    sids, outs = {}, {}
+    for step in range(n + max(start.values())):
+        for i, (W, H) in enumerate(sizes):
+            f = step - start[i]
+            if f == 0:
+                sids[i] = srv.open_stream(W, H, stream_id=700 + i)
+            if 0 <= f < n:
+                mg, mp = np.empty((H, W), np.uint8), np.empty((H, W), np.uint8)
+                outs[(i, f)] = (mg, mp)
+                assert srv.submit(sids[i], data[i][0][f], data[i][1][f], mg, mp, tag=i * 100 + f, wait=30.0)
+    done = []
+    t0 = time.time()
+    while len(done) < n * len(sizes) and time.time() - t0 < 60:
+        done += srv.poll()
+        time.sleep(0.001)
+    assert len(done) == n * len(sizes)
+    assert all(r[1] == 0 for r in done)
+    assert srv.stats()["ticks"] < n * len(sizes)
+    srv.close()
+    for i, (W, H) in enumerate(sizes):
+        rgb, depth, _ = data[i]
+        prm = fos.default_params(stream_id=700 + i)
+        g = orc.GMM(W, H, **oracle_gmm_params(prm))
+        p = orc.PBAS(W, H, **oracle_pbas_params(prm))
+        bad = np.zeros(W * H, bool)
+        for f in range(n):
+            np.testing.assert_array_equal(outs[(i, f)][1], p.step(rgb[f], depth[f]), err_msg=f"PBAS s{i} f{f}")
+            mo, margin = g.step(rgb[f], depth[f], want_margin=True)
+            bad |= (margin < 1e-5).ravel()
+            np.testing.assert_array_equal(outs[(i, f)][0].ravel()[~bad], mo.ravel()[~bad],
+                                          err_msg=f"GMM s{i} f{f}")
+        assert bad.mean() < 0.02
