@@ -527,6 +527,36 @@ fos_status fos_softgmm_backward(fos_softgmm* g, const uint8_t* d_rgb, const uint
                                 void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Range-checked builds.  The paper has no counterpart: this is a testing aid.
+ * The library built with FOS_DEBUG_BOUNDS defined (libfos_bounds.so; the
+ * build script makes it on request) checks every global and shared-memory
+ * index of the GMM, PBAS (per-channel), fused, batched, frame-0 and flush
+ * kernels against the extent of its buffer before the access.  A violation
+ * does not fault or trap: it is counted in the context's device-side record,
+ * the first one's site code and index are kept, and the access goes to a
+ * scratch word instead (its result is then meaningless).  Other kernels
+ * (joint-channel PBAS, literal GMM, soft GMM, quality counts, resampling,
+ * the no-allocation entry point) are not instrumented.
+ *
+ * fos_bounds_checked: 1 in a range-checked build, else 0.
+ * fos_bounds_status: waits for the device, writes the context's violation
+ *     count (and, if the pointers are non-NULL, the first violation's site
+ *     code and element index) and clears the record.  FOS_ERR_UNSUPPORTED in
+ *     a release build (*violations set to 0).
+ * fos_bounds_selftest: exercises the check itself: a one-thread kernel reads
+ *     element 12 of a 64-element buffer through the checked accessor told
+ *     that the buffer has 8 elements; the check must record one violation
+ *     (site 99, index 12) and send the read to the scratch word, so nothing
+ *     outside the declared range is touched.  Allocates and frees its own
+ *     buffer (error text from fos_last_error(NULL)); FOS_ERR_UNSUPPORTED in a
+ *     release build.
+ * ------------------------------------------------------------------------- */
+int32_t fos_bounds_checked(void);
+fos_status fos_bounds_status(fos_ctx* ctx, uint32_t* violations, uint32_t* first_site,
+                             int64_t* first_index);
+fos_status fos_bounds_selftest(uint32_t* violations, uint32_t* first_site, int64_t* first_index);
+
+/* ---------------------------------------------------------------------------
  * One PBAS frame step that allocates nothing.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 SO = os.path.join(PKG, "libfos.so")
+# the range-checked variant (every kernel index checked, violations recorded)
+BUILD_BOUNDS = os.path.join(PKG, "_build_bounds")
+SO_BOUNDS = os.path.join(PKG, "libfos_bounds.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -50,12 +53,14 @@ def _stale(obj: str, src: str) -> bool:
     return os.path.getmtime(src) > t or any(os.path.getmtime(h) > t for h in _headers())
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src: str, verbose: bool, bounds: bool = False) -> str:
+    obj = os.path.join(BUILD_BOUNDS if bounds else BUILD, os.path.splitext(src)[0] + ".o")
     path = os.path.join(CSRC, src)
     if not _stale(obj, path):
         return obj
     cmd = [nvcc(), "-c", path, "-o", obj + ".tmp"] + COMMON + PER_FILE.get(src, [])
+    if bounds:
+        cmd.append("-DFOS_DEBUG_BOUNDS")
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,25 +72,27 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libfos.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
+    """Compile and link libfos.so (bounds: the range-checked libfos_bounds.so);
+    returns its path."""
+    bdir, so = (BUILD_BOUNDS, SO_BOUNDS) if bounds else (BUILD, SO)
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
+        for f in os.listdir(bdir):
+            os.remove(os.path.join(bdir, f))
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    if (not os.path.exists(SO) or force or
-            any(os.path.getmtime(o) > os.path.getmtime(SO) for o in objs)):
+    with cf.ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, len(srcs))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose, bounds), srcs))
+    if (not os.path.exists(so) or force or
+            any(os.path.getmtime(o) > os.path.getmtime(so) for o in objs)):
         # -ldl: the NVTX ranges look their collector up with dlopen
-        cmd = [nvcc(), "-shared", "-o", SO + ".tmp"] + ARCH + objs + ["-Xcompiler", "-fPIC", "-ldl"]
+        cmd = [nvcc(), "-shared", "-o", so + ".tmp"] + ARCH + objs + ["-Xcompiler", "-fPIC", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(SO + ".tmp", SO)
-    return SO
+        os.replace(so + ".tmp", so)
+    return so
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds="--bounds" in sys.argv))

@@ -28,6 +28,19 @@ thread_local fos_status g_create_status = FOS_OK;
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+constexpr int kAuxWords = 32;  // aux: gsum[3][4], counters[3], ..., OobWord at word 16
+
+// The context's violation record in range-checked builds (none otherwise).
+fos::OobWord* oob_of(fos_ctx* c)
+{
+#ifdef FOS_DEBUG_BOUNDS
+    return reinterpret_cast<fos::OobWord*>(c->aux + 16);
+#else
+    (void)c;
+    return nullptr;
+#endif
+}
+
 }  // namespace
 
 
@@ -197,6 +210,7 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     a.px = c->opt[FOS_OPT_PBAS_PX];
     a.ty = c->opt[FOS_OPT_PBAS_TY];
     a.mask_vec = aligned(mask, uintptr_t(a.px)) ? 1 : 0;
+    a.oob = oob_of(c);
     return a;
 }
 
@@ -216,6 +230,7 @@ GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t*
     a.vec_ok = aligned(rgb, 4) && aligned(depth, 8) && aligned(mg, 4) && c->Wd == c->W && c->Hd == c->H;
     a.px = c->opt[FOS_OPT_GMM_PX];
     a.tpb = c->opt[FOS_OPT_GMM_TPB];
+    a.oob = oob_of(c);
     return a;
 }
 
@@ -510,8 +525,9 @@ fos_ctx* fos_create_rgbd(int32_t width, int32_t height, int32_t depth_width, int
         const size_t prev_bytes = params->pbas_propagate ? pp * (2 * 8 + 4) : pp * 8;
         if ((e = dev_alloc(reinterpret_cast<void**>(&c->prev), prev_bytes)) != cudaSuccess) return bail("cudaMalloc(prev)", e);
     }
-    if ((e = dev_alloc(reinterpret_cast<void**>(&c->aux), 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
-    if ((e = cudaMemset(c->aux, 0, 16 * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
+    // gradient sums, counters, and at word 16 the range-checked build's OobWord
+    if ((e = dev_alloc(reinterpret_cast<void**>(&c->aux), kAuxWords * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMalloc(aux)", e);
+    if ((e = cudaMemset(c->aux, 0, kAuxWords * sizeof(unsigned long long))) != cudaSuccess) return bail("cudaMemset(aux)", e);
     return c;
 }
 
@@ -830,3 +846,76 @@ fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4])
 }
 
 }  // extern "C"
+
+extern "C" int32_t fos_bounds_checked(void)
+{
+#ifdef FOS_DEBUG_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" fos_status fos_bounds_status(fos_ctx* ctx, uint32_t* violations, uint32_t* first_site,
+                                        int64_t* first_index)
+{
+    if (!ctx || !violations) return FOS_ERR_INVALID_ARG;
+#ifdef FOS_DEBUG_BOUNDS
+    FOS_TRY(ctx, cudaSetDevice(ctx->device));
+    FOS_TRY(ctx, cudaDeviceSynchronize());
+    fos::OobWord w{};
+    FOS_TRY(ctx, cudaMemcpy(&w, oob_of(ctx), sizeof w, cudaMemcpyDeviceToHost));
+    FOS_TRY(ctx, cudaMemset(oob_of(ctx), 0, sizeof w));
+    *violations = w.count;
+    if (first_site) *first_site = w.site;
+    if (first_index) *first_index = w.index;
+    return FOS_OK;
+#else
+    *violations = 0;
+    return fail(ctx, FOS_ERR_UNSUPPORTED, "fos_bounds_status: not a range-checked build (FOS_DEBUG_BOUNDS)");
+#endif
+}
+
+#ifdef FOS_DEBUG_BOUNDS
+namespace {
+// Reads element i of a 16-element buffer through the checked accessor with a
+// declared extent of n: for i >= n the check records the violation and the
+// read goes to the sink, so the buffer is never accessed out of its range.
+__global__ void bounds_selftest_kernel(const uint32_t* buf, int64_t i, int64_t n, fos::OobWord* w, uint32_t* out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) out[0] = fos::at(buf, i, n, 99, w);
+}
+}  // namespace
+#endif
+
+extern "C" fos_status fos_bounds_selftest(uint32_t* violations, uint32_t* first_site, int64_t* first_index)
+{
+    if (!violations) return FOS_ERR_INVALID_ARG;
+    *violations = 0;
+#ifdef FOS_DEBUG_BOUNDS
+    uint32_t* buf = nullptr;
+    fos::OobWord w{};
+    cudaError_t e = cudaMalloc(&buf, 64 * sizeof(uint32_t) + sizeof(fos::OobWord));
+    fos::OobWord* dw = reinterpret_cast<fos::OobWord*>(buf + 32);
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, 64 * sizeof(uint32_t) + sizeof(fos::OobWord));
+    if (e == cudaSuccess) {
+        bounds_selftest_kernel<<<1, 32>>>(buf, 12, 8, dw, buf + 16);  // element 12 is in the buffer, above 8
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&w, dw, sizeof w, cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        set_thread_error(cudaGetErrorString(e));
+        return FOS_ERR_CUDA;
+    }
+    *violations = w.count;
+    if (first_site) *first_site = w.site;
+    if (first_index) *first_index = w.index;
+    return FOS_OK;
+#else
+    (void)first_site;
+    (void)first_index;
+    set_thread_error("fos_bounds_selftest: not a range-checked build (FOS_DEBUG_BOUNDS)");
+    return FOS_ERR_UNSUPPORTED;
+#endif
+}

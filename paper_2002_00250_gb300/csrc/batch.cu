@@ -3,12 +3,13 @@
 // A batch owns up to max_streams stream contexts (ordinary fos_ctx objects,
 // so every single-stream call -- state export, reset, options -- works on
 // them).  One frame step of up to kBatchLaunchMax streams is one replay of a
-// CUDA graph holding one persistent kernel (GMM and PBAS of every tile, or
-// one per method when they do not run together) that walks the (stream, tile)
-// work of the step round-robin.  The per-stream arguments of the step form a
-// table that rides in the kernel node's parameters (updated in the
-// instantiated graph before each replay), so the kernels read them from the
-// constant bank; larger steps take one replay per kBatchLaunchMax streams.
+// CUDA graph holding one kernel launch (GMM and PBAS of every tile, or one
+// per method when they do not run together) with one block per tile of every
+// stream (the GMM-only kernel: a persistent grid over the streams' blocks).
+// The per-stream arguments of the step form a table that rides in the kernel
+// node's parameters, updated in the instantiated graph together with the
+// grid size before each replay, so the kernels read them from the constant
+// bank; larger steps take one replay per kBatchLaunchMax streams.
 // Results are bit-identical to processing each stream alone: every pixel runs
 // the same code on the same data.
 #include <algorithm>
@@ -102,8 +103,9 @@ fos_status ensure_graph(fos_batch* b, int pbas_px)
     drop_graph(b);
     const bool fz = fused(b);
     b->blocks[0] = b->blocks[1] = 0;
-    if (gmm_on(b) && !fz) b->blocks[0] = b->sms * std::max(1, gmm_batch_blocks_per_sm(b->prm.K_rgb, b->prm.K_d, b->gmm_px));
-    if (pbas_on(b)) b->blocks[1] = b->sms * std::max(1, pbas_batch_blocks_per_sm(b->prm.N, pbas_px, b->pbas_ty, fz));
+    // one block per tile / per block of pixels: the grid is set at each replay
+    if (gmm_on(b) && !fz) b->blocks[0] = 1;
+    if (pbas_on(b)) b->blocks[1] = 1;
     b->gt.n = b->gt.total = 0;
     b->pt.n = b->pt.total = 0;
     FOS_BTRY(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
@@ -157,12 +159,14 @@ fos_status replay(fos_batch* b, cudaStream_t s)
         cudaKernelNodeParams p = b->kp[0];
         p.kernelParams = gargs;
         p.extra = nullptr;
+        p.gridDim = dim3(unsigned(std::max(1, b->gt.total)));
         FOS_BTRY(b, cudaGraphExecKernelNodeSetParams(b->graph, b->node[0], &p));
     }
     if (b->node[1]) {
         cudaKernelNodeParams p = b->kp[1];
         p.kernelParams = pargs;
         p.extra = nullptr;
+        p.gridDim = dim3(unsigned(std::max(1, b->pt.total)));  // one block per tile
         FOS_BTRY(b, cudaGraphExecKernelNodeSetParams(b->graph, b->node[1], &p));
     }
     FOS_BTRY(b, cudaGraphLaunch(b->graph, s));

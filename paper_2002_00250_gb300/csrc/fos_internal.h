@@ -11,6 +11,57 @@ namespace fos {
 // Launch status of an internal launcher.
 enum LaunchResult { kLaunchOk = 0, kLaunchUnsupported = 1, kLaunchCudaError = 2 };
 
+// Range-checked builds.  Compiled with -DFOS_DEBUG_BOUNDS (libfos_bounds.so),
+// every global and shared-memory index of the GMM and PBAS kernels is checked
+// against the extent of its buffer before the access.  A violation is counted
+// in the context's OobWord (the first one's site and index are kept) and the
+// access goes to a scratch sink instead, so the kernel neither faults nor
+// traps; fos_bounds_status reads the word back.  In release builds at()
+// and vat() are plain indexing.
+struct OobWord {
+    unsigned int count;  // violations since the last read
+    unsigned int site;   // site code of the first one
+    long long index;     // its index (elements) or, for a vector access, its start
+};
+
+#ifdef FOS_DEBUG_BOUNDS
+__device__ __align__(16) static unsigned long long g_oob_sink[2];
+__device__ __forceinline__ void oob_record(OobWord* w, int site, int64_t i)
+{
+    if (w && atomicAdd(&w->count, 1u) == 0u) {
+        w->site = unsigned(site);
+        w->index = i;
+    }
+}
+template <class T>
+__device__ __forceinline__ T& at(T* base, int64_t i, int64_t n, int site, OobWord* w)
+{
+    if (i >= 0 && i < n) return base[i];
+    oob_record(w, site, i);
+    return *reinterpret_cast<T*>(g_oob_sink);
+}
+// element i..i+width-1 of base as one vector V (also checks V's alignment)
+template <class V, class T>
+__device__ __forceinline__ V& vat(T* base, int64_t i, int width, int64_t n, int site, OobWord* w)
+{
+    V* p = reinterpret_cast<V*>(base + i);
+    if (i >= 0 && i + width <= n && (reinterpret_cast<uintptr_t>(p) % sizeof(V)) == 0) return *p;
+    oob_record(w, site, i);
+    return *reinterpret_cast<V*>(g_oob_sink);
+}
+#else
+template <class T>
+__device__ __forceinline__ T& at(T* base, int64_t i, int64_t, int, OobWord*)
+{
+    return base[i];
+}
+template <class V, class T>
+__device__ __forceinline__ V& vat(T* base, int64_t i, int, int64_t, int, OobWord*)
+{
+    return *reinterpret_cast<V*>(base + i);
+}
+#endif
+
 // Index of the depth reading used for colour pixel (x, y) of a W x H frame
 // when depth frames are Wd x Hd: the same pixel at equal sizes, else the
 // nearest-neighbour source with floor mapping (Sec. 4.3; the resampling that
@@ -42,6 +93,7 @@ struct GmmArgs {
     int px;             // pixels per thread: 1, 2 or 4
     int tpb;            // threads per block: 64, 128 or 256
     int W, H, Wd, Hd;   // colour frame; depth frame (resampled on read when it differs)
+    OobWord* oob;       // range-checked builds: the context's violation record
 };
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);
@@ -85,12 +137,12 @@ struct GmmBatchTable {
     int pad[2];
     GmmBatchEntry e[kBatchLaunchMax];
 };
-// Persistent batched GMM launch over t.n entries and t.total blocks; every
-// stream uses the same (Kr, Kd) and pixels per thread.
+// Batched GMM launch over t.n entries and t.total blocks of kGmmBatchThreads
+// threads (`blocks` >= t.total); every stream uses the same (Kr, Kd) and
+// pixels per thread.
 constexpr int kGmmBatchThreads = 128;
 LaunchResult launch_gmm_batch(const GmmBatchTable& t, int blocks, int Kr, int Kd, int px, cudaStream_t s);
 int gmm_batch_px(int Kr, int Kd, int px);
-int gmm_batch_blocks_per_sm(int Kr, int Kd, int px);
 
 // PBAS device state.  Frames are cut into row segments of kSeg = 128 pixels
 // (spr = ceil(W / 128) segments per row, nseg = H * spr).  Samples and D are
@@ -144,7 +196,13 @@ struct PbasArgs {
                                  // requesters' (propagate; a second plane) or prev itself
     uint32_t* own;               // [plane] propagate only: byte c = slot of the pixel's own
                                  // update in channel c of the last frame (0x1F none)
+    OobWord* oob;                // range-checked builds: the context's violation record
 };
+
+// Extents (elements) of the PBAS buffers, for the range-checked build.
+__host__ __device__ inline int64_t samp_extent(const PbasArgs& a) { return 4 * a.nseg * a.N * kSeg; }
+__host__ __device__ inline int64_t rts_extent(const PbasArgs& a) { return 4 * a.plane; }
+__host__ __device__ inline int64_t depth_extent(const PbasArgs& a) { return int64_t(a.Wd) * a.Hd; }
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
@@ -169,12 +227,11 @@ struct PbasBatchTable {
     PbasBatchEntry e[kBatchLaunchMax];
     GmmArgs g[kBatchLaunchMax];  // fused launches: the GMM arguments of entry i
 };
-// Persistent batched PBAS launch over t.n entries and t.total tiles (blocks
-// take tiles round-robin).  fused (3+3-component GMM): each tile also runs the
+// Batched PBAS launch over t.n entries and t.total tiles, one block per tile
+// (`blocks` >= t.total).  fused (3+3-component GMM): each tile also runs the
 // GMM of its pixels.
 LaunchResult launch_pbas_batch(const PbasBatchTable& t, bool fused, int blocks, int N, int px, int ty,
                                cudaStream_t s);
-int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused);
 
 // Depth frame sw x sh resampled onto dw x dh (nearest, floor mapping).
 LaunchResult launch_depth_resample(const uint16_t* src, int sw, int sh, uint16_t* dst, int dw, int dh,

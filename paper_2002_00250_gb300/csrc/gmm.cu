@@ -21,9 +21,10 @@ using namespace gmmdev;
 __device__ __forceinline__ uint32_t depth_at(const GmmArgs& a, int64_t p)
 {
     const uint16_t* d = a.depth;
-    if (a.Wd == a.W && a.Hd == a.H) return d[p];
+    const int64_t nd = int64_t(a.Wd) * a.Hd;
+    if (a.Wd == a.W && a.Hd == a.H) return at(d, p, nd, 44, a.oob);
     const int y = int(uint32_t(p) / uint32_t(a.W)), x = int(p) - y * a.W;  // P < 2^28
-    return d[depth_index(x, y, a.W, a.H, a.Wd, a.Hd)];
+    return at(d, depth_index(x, y, a.W, a.H, a.Wd, a.Hd), nd, 44, a.oob);
 }
 
 // PX consecutive pixels per thread starting at pixel p0 of one stream.
@@ -31,25 +32,28 @@ template <int KR, int KD, int PX>
 __device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
 {
     if (p0 >= a.P) return;
+    const int64_t ne = int64_t(5 * KR + 3 * KD) * a.plane;  // state extent (range-checked builds)
     // PX = 4 reads the inputs as 32/64-bit words: needs aligned frame buffers
     if (PX > 1 && (PX != 4 || a.vec_ok) && p0 + PX <= a.P) {
         Mix<KR, 3> mr[PX];
         Mix<KD, 1> md[PX];
-        if (!a.init) move_state<KR, KD, PX, false>(a.state, a.plane, p0, mr, md);
+        if (!a.init) move_state<KR, KD, PX, false>(a.state, a.plane, p0, mr, md, ne, a.oob);
         uint32_t rgbw[3 * PX / 4 > 0 ? 3 * PX / 4 : 1];
         uint16_t dv[PX];
         uint8_t rgbb[3 * PX];
         if constexpr (PX == 4) {
             const uint32_t* src = reinterpret_cast<const uint32_t*>(a.rgb + 3 * p0);
-            rgbw[0] = src[0]; rgbw[1] = src[1]; rgbw[2] = src[2];
+            rgbw[0] = at(src, 0, 3 * (a.P - p0) / 4, 45, a.oob);
+            rgbw[1] = at(src, 1, 3 * (a.P - p0) / 4, 45, a.oob);
+            rgbw[2] = at(src, 2, 3 * (a.P - p0) / 4, 45, a.oob);
 #pragma unroll
             for (int j = 0; j < 12; ++j) rgbb[j] = uint8_t(rgbw[j >> 2] >> (8 * (j & 3)));
-            const uint2 dd = *reinterpret_cast<const uint2*>(a.depth + p0);
+            const uint2 dd = vat<const uint2>(a.depth, p0, 4, a.P, 46, a.oob);
             dv[0] = uint16_t(dd.x); dv[1] = uint16_t(dd.x >> 16);
             dv[2] = uint16_t(dd.y); dv[3] = uint16_t(dd.y >> 16);
         } else {
 #pragma unroll
-            for (int j = 0; j < 3 * PX; ++j) rgbb[j] = a.rgb[3 * p0 + j];
+            for (int j = 0; j < 3 * PX; ++j) rgbb[j] = at(a.rgb, 3 * p0 + j, 3 * a.P, 47, a.oob);
 #pragma unroll
             for (int i = 0; i < PX; ++i) dv[i] = uint16_t(depth_at(a, p0 + i));
         }
@@ -58,13 +62,13 @@ __device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
         for (int i = 0; i < PX; ++i)
             m[i] = gmm_pixel<KR, KD>(mr[i], md[i], rgbb[3 * i], rgbb[3 * i + 1], rgbb[3 * i + 2],
                                      dv[i], a);
-        move_state<KR, KD, PX, true>(a.state, a.plane, p0, mr, md);
+        move_state<KR, KD, PX, true>(a.state, a.plane, p0, mr, md, ne, a.oob);
         if constexpr (PX == 4) {
-            *reinterpret_cast<uint32_t*>(a.mask + p0) =
+            vat<uint32_t>(a.mask, p0, 4, a.P, 48, a.oob) =
                 uint32_t(m[0]) | (uint32_t(m[1]) << 8) | (uint32_t(m[2]) << 16) | (uint32_t(m[3]) << 24);
         } else {
 #pragma unroll
-            for (int i = 0; i < PX; ++i) a.mask[p0 + i] = m[i];
+            for (int i = 0; i < PX; ++i) at(a.mask, p0 + i, a.P, 48, a.oob) = m[i];
         }
         return;
     }
@@ -72,11 +76,12 @@ __device__ __forceinline__ void gmm_pixels(const GmmArgs& a, int64_t p0)
     for (int64_t p = p0; p < p0 + PX && p < a.P; ++p) {
         Mix<KR, 3> mr[1];
         Mix<KD, 1> md[1];
-        if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md);
-        const uint8_t m = gmm_pixel<KR, KD>(mr[0], md[0], a.rgb[3 * p], a.rgb[3 * p + 1],
-                                            a.rgb[3 * p + 2], depth_at(a, p), a);
-        move_state<KR, KD, 1, true>(a.state, a.plane, p, mr, md);
-        a.mask[p] = m;
+        if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md, ne, a.oob);
+        const uint8_t m = gmm_pixel<KR, KD>(mr[0], md[0], at(a.rgb, 3 * p, 3 * a.P, 49, a.oob),
+                                            at(a.rgb, 3 * p + 1, 3 * a.P, 49, a.oob),
+                                            at(a.rgb, 3 * p + 2, 3 * a.P, 49, a.oob), depth_at(a, p), a);
+        move_state<KR, KD, 1, true>(a.state, a.plane, p, mr, md, ne, a.oob);
+        at(a.mask, p, a.P, 50, a.oob) = m;
     }
 }
 
@@ -86,22 +91,21 @@ __global__ void __launch_bounds__(256) gmm_kernel(const GmmArgs a)
     gmm_pixels<KR, KD, PX>(a, (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * PX);
 }
 
-// Many streams in one persistent launch: entry i of the table (a
-// __grid_constant__ parameter, read from the constant bank) holds stream i's
-// arguments and its first block in the launch; blocks take the launch's
-// blocks round-robin.
+// Many streams in one launch: entry i of the table (a __grid_constant__
+// parameter, read from the constant bank) holds stream i's arguments and its
+// first block in the launch; one block per block of pixels of every stream.
 template <int KR, int KD, int PX>
 __global__ void __launch_bounds__(kGmmBatchThreads) gmm_batch_kernel(const __grid_constant__ GmmBatchTable T)
 {
-    for (int it = blockIdx.x; it < T.total; it += gridDim.x) {
-        int lo = 0, hi = T.n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (T.e[mid].block_off <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        gmm_pixels<KR, KD, PX>(T.e[lo].a, (int64_t(it - T.e[lo].block_off) * blockDim.x + threadIdx.x) * PX);
+    const int it = int(blockIdx.x);
+    if (it >= T.total) return;
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.e[mid].block_off <= it) lo = mid;
+        else hi = mid - 1;
     }
+    gmm_pixels<KR, KD, PX>(T.e[lo].a, (int64_t(it - T.e[lo].block_off) * blockDim.x + threadIdx.x) * PX);
 }
 
 template <int KR, int KD, int PX>
@@ -162,20 +166,6 @@ LaunchResult launch_gmm_batch(const GmmBatchTable& t, int blocks, int Kr, int Kd
     return kLaunchUnsupported;
 }
 
-int gmm_batch_blocks_per_sm(int Kr, int Kd, int px)
-{
-    const int p = gmm_batch_px(Kr, Kd, px);
-    int nb = 0;
-    cudaError_t e = cudaErrorInvalidValue;
-#define FOS_O(R, D, PX)                                                                    \
-    if (Kr == R && Kd == D && p == PX)                                                     \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gmm_batch_kernel<R, D, PX>, \
-                                                          kGmmBatchThreads, 0);
-    FOS_GMM_BATCH_CASES(FOS_O)
-#undef FOS_O
-    return e == cudaSuccess ? nb : 0;
-}
-
 #undef FOS_GMM_BATCH_CASES
 
 namespace {
@@ -196,23 +186,29 @@ __global__ void __launch_bounds__(kFramesThreads) gmm_frames_kernel(const GmmArg
     if (p >= a.P) return;
     Mix<KR, 3> mr[1];
     Mix<KD, 1> md[1];
-    if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md);
+    const int64_t ne = int64_t(5 * KR + 3 * KD) * a.plane;  // state extent (range-checked builds)
+    if (!a.init) move_state<KR, KD, 1, false>(a.state, a.plane, p, mr, md, ne, a.oob);
     GmmArgs b = a;
     // the pixel's depth reading (the same index in every frame) and the depth frame stride
     const int y = int(uint32_t(p) / uint32_t(a.W)), x = int(p) - y * a.W;
     const int64_t pd = depth_index(x, y, a.W, a.H, a.Wd, a.Hd), Pd = int64_t(a.Wd) * a.Hd;
-    uint32_t r = a.rgb[3 * p], g = a.rgb[3 * p + 1], bl = a.rgb[3 * p + 2], d = a.depth[pd];
+    const int64_t nrgb = 3 * a.P * n, nd = Pd * n, nm = a.P * n;
+    uint32_t r = at(a.rgb, 3 * p, nrgb, 51, a.oob), g = at(a.rgb, 3 * p + 1, nrgb, 51, a.oob);
+    uint32_t bl = at(a.rgb, 3 * p + 2, nrgb, 51, a.oob), d = at(a.depth, pd, nd, 52, a.oob);
     for (int f = 0; f < n; ++f) {
         uint32_t r1 = 0, g1 = 0, b1 = 0, d1 = 0;
         if (f + 1 < n) {
             const int64_t q = int64_t(f + 1) * a.P + p;
-            r1 = a.rgb[3 * q]; g1 = a.rgb[3 * q + 1]; b1 = a.rgb[3 * q + 2]; d1 = a.depth[int64_t(f + 1) * Pd + pd];
+            r1 = at(a.rgb, 3 * q, nrgb, 51, a.oob);
+            g1 = at(a.rgb, 3 * q + 1, nrgb, 51, a.oob);
+            b1 = at(a.rgb, 3 * q + 2, nrgb, 51, a.oob);
+            d1 = at(a.depth, int64_t(f + 1) * Pd + pd, nd, 52, a.oob);
         }
         b.init = (f == 0) ? a.init : 0;
-        a.mask[int64_t(f) * a.P + p] = gmm_pixel<KR, KD>(mr[0], md[0], r, g, bl, d, b);
+        at(a.mask, int64_t(f) * a.P + p, nm, 53, a.oob) = gmm_pixel<KR, KD>(mr[0], md[0], r, g, bl, d, b);
         r = r1; g = g1; bl = b1; d = d1;
     }
-    move_state<KR, KD, 1, true>(a.state, a.plane, p, mr, md);
+    move_state<KR, KD, 1, true>(a.state, a.plane, p, mr, md, ne, a.oob);
 }
 
 }  // namespace

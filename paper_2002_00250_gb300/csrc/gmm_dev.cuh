@@ -138,46 +138,49 @@ __device__ __forceinline__ float mix_step(Mix<K, C>& m, const float (&x)[C], flo
     return dB;
 }
 
+// PX floats of a state plane from element i (extent n: range-checked builds).
 template <int PX>
-__device__ __forceinline__ void ldv(const float* p, float (&o)[PX])
+__device__ __forceinline__ void ldv(const float* st, int64_t i, int64_t n, OobWord* w, float (&o)[PX])
 {
     if constexpr (PX == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
+        const float4 v = vat<const float4>(st, i, 4, n, 40, w);
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     } else if constexpr (PX == 2) {
-        const float2 v = *reinterpret_cast<const float2*>(p);
+        const float2 v = vat<const float2>(st, i, 2, n, 40, w);
         o[0] = v.x; o[1] = v.y;
     } else {
-        o[0] = *p;
+        o[0] = at(st, i, n, 40, w);
     }
 }
 
 template <int PX>
-__device__ __forceinline__ void stv(float* p, const float (&o)[PX])
+__device__ __forceinline__ void stv(float* st, int64_t i, int64_t n, OobWord* w, const float (&o)[PX])
 {
     if constexpr (PX == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+        vat<float4>(st, i, 4, n, 41, w) = make_float4(o[0], o[1], o[2], o[3]);
     } else if constexpr (PX == 2) {
-        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
+        vat<float2>(st, i, 2, n, 41, w) = make_float2(o[0], o[1]);
     } else {
-        *p = o[0];
+        at(st, i, n, 41, w) = o[0];
     }
 }
 
-// Per-plane load/store of PX pixels of one parameter into the mixtures.
+// Per-plane load/store of PX pixels of one parameter into the mixtures
+// (n: elements of the whole state, for range-checked builds).
 template <int KR, int KD, int PX, bool STORE>
 __device__ __forceinline__ void move_state(float* st, int64_t plane, int64_t p0,
-                                           Mix<KR, 3> (&mr)[PX], Mix<KD, 1> (&md)[PX])
+                                           Mix<KR, 3> (&mr)[PX], Mix<KD, 1> (&md)[PX],
+                                           int64_t n = int64_t(1) << 62, OobWord* w = nullptr)
 {
     float tmp[PX];
 #define FOS_MOVE(QIDX, FIELD_I)                                            \
     {                                                                      \
-        float* ptr = st + (int64_t)(QIDX) * plane + p0;                    \
+        const int64_t idx = (int64_t)(QIDX) * plane + p0;                  \
         if (STORE) {                                                       \
             _Pragma("unroll") for (int i = 0; i < PX; ++i) tmp[i] = FIELD_I; \
-            stv<PX>(ptr, tmp);                                             \
+            stv<PX>(st, idx, n, w, tmp);                                   \
         } else {                                                           \
-            ldv<PX>(ptr, tmp);                                             \
+            ldv<PX>(st, idx, n, w, tmp);                                   \
             _Pragma("unroll") for (int i = 0; i < PX; ++i) FIELD_I = tmp[i]; \
         }                                                                  \
     }
@@ -224,19 +227,20 @@ __device__ __forceinline__ uint8_t gmm_pixel_d8(Mix<KR, 3>& mr, Mix<KD, 1>& md, 
 // One mixture of one pixel moved between registers and its planes
 // (first plane index q0: colour model 0, depth model 5*Kr).
 template <int K, int C, bool STORE>
-__device__ __forceinline__ void move_mix(float* st, int64_t plane, int64_t p, int q0, Mix<K, C>& m)
+__device__ __forceinline__ void move_mix(float* st, int64_t plane, int64_t p, int q0, Mix<K, C>& m,
+                                         int64_t n = int64_t(1) << 62, OobWord* ob = nullptr)
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float* w = st + int64_t(q0 + k) * plane + p;
-        float* v = st + int64_t(q0 + (1 + C) * K + k) * plane + p;
-        if (STORE) { *w = m.w[k]; *v = m.v[k]; }
-        else { m.w[k] = *w; m.v[k] = *v; }
+        float& w = at(st, int64_t(q0 + k) * plane + p, n, 42, ob);
+        float& v = at(st, int64_t(q0 + (1 + C) * K + k) * plane + p, n, 42, ob);
+        if (STORE) { w = m.w[k]; v = m.v[k]; }
+        else { m.w[k] = w; m.v[k] = v; }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            float* mu = st + int64_t(q0 + (1 + c) * K + k) * plane + p;
-            if (STORE) *mu = m.mu[c][k];
-            else m.mu[c][k] = *mu;
+            float& mu = at(st, int64_t(q0 + (1 + c) * K + k) * plane + p, n, 42, ob);
+            if (STORE) mu = m.mu[c][k];
+            else m.mu[c][k] = mu;
         }
     }
 }
@@ -244,14 +248,15 @@ __device__ __forceinline__ void move_mix(float* st, int64_t plane, int64_t p, in
 // One mixture of two adjacent pixels (p even, plane 8-byte aligned) moved
 // between registers and its planes with one 8-byte access per parameter.
 template <int K, int C, bool STORE>
-__device__ __forceinline__ void move_mix2(float* st, int64_t plane, int64_t p, int q0, Mix<K, C> (&m)[2])
+__device__ __forceinline__ void move_mix2(float* st, int64_t plane, int64_t p, int q0, Mix<K, C> (&m)[2],
+                                          int64_t n = int64_t(1) << 62, OobWord* ob = nullptr)
 {
     auto mv = [&](int q, float& a0, float& a1) {
-        float2* ptr = reinterpret_cast<float2*>(st + int64_t(q) * plane + p);
+        float2& ref = vat<float2>(st, int64_t(q) * plane + p, 2, n, 43, ob);
         if (STORE) {
-            *ptr = make_float2(a0, a1);
+            ref = make_float2(a0, a1);
         } else {
-            const float2 v = *ptr;
+            const float2 v = ref;
             a0 = v.x;
             a1 = v.y;
         }
@@ -275,20 +280,21 @@ __device__ __forceinline__ uint32_t gmm_pair(const GmmArgs& a, int64_t p, const 
                                              const uint32_t (&g)[2], const uint32_t (&b)[2],
                                              const uint32_t (&d8)[2])
 {
+    const int64_t ne = int64_t(5 * KR + 3 * KD) * a.plane;
     float Q[2];
     {
         Mix<KR, 3> mr[2];
-        move_mix2<KR, 3, false>(a.state, a.plane, p, 0, mr);
+        move_mix2<KR, 3, false>(a.state, a.plane, p, 0, mr, ne, a.oob);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             const float xr[3] = {float(r[i]), float(g[i]), float(b[i])};
             Q[i] = mix_step(mr[i], xr, a.alpha, a.lam2, a.T_bg, a.v_init_rgb, a.v_min_rgb);
         }
-        move_mix2<KR, 3, true>(a.state, a.plane, p, 0, mr);
+        move_mix2<KR, 3, true>(a.state, a.plane, p, 0, mr, ne, a.oob);
     }
     if (d8[0] | d8[1]) {
         Mix<KD, 1> md[2];
-        move_mix2<KD, 1, false>(a.state, a.plane, p, 5 * KR, md);
+        move_mix2<KD, 1, false>(a.state, a.plane, p, 5 * KR, md, ne, a.oob);
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
             if (d8[i] != 0) {
@@ -297,7 +303,7 @@ __device__ __forceinline__ uint32_t gmm_pair(const GmmArgs& a, int64_t p, const 
                 Q[i] = __fmaf_rn(a.w_depth, dB_d, __fmul_rn(__fsub_rn(1.f, a.w_depth), Q[i]));
             }
         }
-        move_mix2<KD, 1, true>(a.state, a.plane, p, 5 * KR, md);
+        move_mix2<KD, 1, true>(a.state, a.plane, p, 5 * KR, md, ne, a.oob);
     }
     return (Q[0] >= a.lam2 ? 0xFFu : 0u) | (Q[1] >= a.lam2 ? 0xFF00u : 0u);
 }
@@ -308,6 +314,7 @@ template <int KR, int KD>
 __device__ __forceinline__ uint8_t gmm_pixel_lowreg(const GmmArgs& a, int64_t p, uint32_t r,
                                                     uint32_t g, uint32_t b, uint32_t d8)
 {
+    const int64_t ne = int64_t(5 * KR + 3 * KD) * a.plane;
     float dB_rgb;
     {
         Mix<KR, 3> mr;
@@ -316,10 +323,10 @@ __device__ __forceinline__ uint8_t gmm_pixel_lowreg(const GmmArgs& a, int64_t p,
             mix_init(mr, xr, a.v_init_rgb);
             dB_rgb = 0.f;
         } else {
-            move_mix<KR, 3, false>(a.state, a.plane, p, 0, mr);
+            move_mix<KR, 3, false>(a.state, a.plane, p, 0, mr, ne, a.oob);
             dB_rgb = mix_step(mr, xr, a.alpha, a.lam2, a.T_bg, a.v_init_rgb, a.v_min_rgb);
         }
-        move_mix<KR, 3, true>(a.state, a.plane, p, 0, mr);
+        move_mix<KR, 3, true>(a.state, a.plane, p, 0, mr, ne, a.oob);
     }
     float Q = dB_rgb;
     {
@@ -327,11 +334,11 @@ __device__ __forceinline__ uint8_t gmm_pixel_lowreg(const GmmArgs& a, int64_t p,
         const float xd[1] = {float(d8)};
         if (a.init) {
             mix_init(md, xd, a.v_init_d);
-            move_mix<KD, 1, true>(a.state, a.plane, p, 5 * KR, md);
+            move_mix<KD, 1, true>(a.state, a.plane, p, 5 * KR, md, ne, a.oob);
         } else if (d8 != 0) {
-            move_mix<KD, 1, false>(a.state, a.plane, p, 5 * KR, md);
+            move_mix<KD, 1, false>(a.state, a.plane, p, 5 * KR, md, ne, a.oob);
             const float dB_d = mix_step(md, xd, a.alpha, a.lam2, a.T_bg, a.v_init_d, a.v_min_d);
-            move_mix<KD, 1, true>(a.state, a.plane, p, 5 * KR, md);
+            move_mix<KD, 1, true>(a.state, a.plane, p, 5 * KR, md, ne, a.oob);
             Q = __fmaf_rn(a.w_depth, dB_d, __fmul_rn(__fsub_rn(1.f, a.w_depth), dB_rgb));
         }
     }

@@ -81,25 +81,26 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         uint64_t pw[PX];
         if (vec) {
             if constexpr (PX == 4) {
-                const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(a.prev + q0);
-                const ulonglong2 u1 = *reinterpret_cast<const ulonglong2*>(a.prev + q0 + 2);
+                const ulonglong2 u0 = vat<const ulonglong2>(a.prev, q0, 2, a.plane, 24, a.oob);
+                const ulonglong2 u1 = vat<const ulonglong2>(a.prev, q0 + 2, 2, a.plane, 24, a.oob);
                 pw[0] = u0.x; pw[1] = u0.y; pw[2] = u1.x; pw[3] = u1.y;
             } else if constexpr (PX == 2) {
-                const ulonglong2 u0 = *reinterpret_cast<const ulonglong2*>(a.prev + q0);
+                const ulonglong2 u0 = vat<const ulonglong2>(a.prev, q0, 2, a.plane, 24, a.oob);
                 pw[0] = u0.x; pw[1] = u0.y;
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < PX; ++i) pw[i] = inb[i] ? a.prev[q0 + i] : 0ull;
+            for (int i = 0; i < PX; ++i) pw[i] = inb[i] ? at(a.prev, q0 + i, a.plane, 24, a.oob) : 0ull;
         }
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
-            const uint32_t mm = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1) : 0u;
+            const uint32_t mm = inb[i] ? request_matches<G::SW>(sreq, ly, lx0 + i + 1, G::SH * G::SW, a.oob) : 0u;
             if (a.propagate) {
                 cnt7[5] += apply_propagated<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm,
-                                                   mm ? a.own[q0 + i] : kReqNone4);
+                                                   mm ? at(a.own, q0 + i, a.plane, 25, a.oob) : kReqNone4,
+                                                   G::SH * G::SW);
             } else {
-                cnt7[5] += apply_own_value<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm, pw[i]);
+                cnt7[5] += apply_own_value<G::SW>(a, N, sreq, ly, lx0 + i + 1, x + i, y, mm, pw[i], G::SH * G::SW);
             }
         }
     }
@@ -120,10 +121,10 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             const int col = lx0 + i + 1;
-            const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
-            const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
+            const uint32_t v = at(sm, c * G::CH + (ly + 1) * G::SWP + col, 4 * G::CH, 26, a.oob);
+            const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col, G::CH, a.oob);
             pv[i] = v | (g << 8);
-            act[i] = inb[i] && (c < 3 || sm[3 * G::CH + (ly + 1) * G::SWP + col] != 0);
+            act[i] = inb[i] && (c < 3 || at(sm, 3 * G::CH + (ly + 1) * G::SWP + col, 4 * G::CH, 26, a.oob) != 0);
             if (inb[i]) gsc += g;
             any |= act[i];
         }
@@ -140,16 +141,17 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
 
         float Rv[PX], Tv[PX];
         uint32_t Sv[PX];
+        const int64_t ne = rts_extent(a);
         if (vec) {
-            ldf<PX>(a.R + pc, Rv);
-            ldf<PX>(a.T + pc, Tv);
-            ldu<PX>(a.S + pc, Sv);
+            ldf<PX>(a.R, pc, ne, 16, a.oob, Rv);
+            ldf<PX>(a.T, pc, ne, 17, a.oob, Tv);
+            ldu<PX>(a.S, pc, ne, 18, a.oob, Sv);
         } else {
 #pragma unroll
             for (int i = 0; i < PX; ++i) {
-                Rv[i] = inb[i] ? a.R[pc + i] : 0.f;
-                Tv[i] = inb[i] ? a.T[pc + i] : 1.f;
-                Sv[i] = inb[i] ? a.S[pc + i] : 0u;
+                Rv[i] = inb[i] ? at(a.R, pc + i, ne, 16, a.oob) : 0.f;
+                Tv[i] = inb[i] ? at(a.T, pc + i, ne, 17, a.oob) : 1.f;
+                Sv[i] = inb[i] ? at(a.S, pc + i, ne, 18, a.oob) : 0u;
             }
         }
         if (c < 3 && inb[0]) prefetch_channel<NT>(a, N, c + 1, x, y, q0);
@@ -171,9 +173,9 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         for (int k = 0; k < N; ++k) {
             uint32_t s[NW];
             if (vec) {
-                ldw<PX>(a.samp + sb + int64_t(k) * kSeg, s);
+                ldw<PX>(a.samp, sb + int64_t(k) * kSeg, samp_extent(a), 23, a.oob, s);
             } else {
-                s[0] = inb[0] ? a.samp[sidx(a, N, c, k, x, y)] : 0u;
+                s[0] = inb[0] ? at(a.samp, sidx(a, N, c, k, x, y), samp_extent(a), 23, a.oob) : 0u;
             }
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
@@ -219,15 +221,15 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         // own updates: all D reads first (independent), then the writes
         uint32_t dold[PX];
 #pragma unroll
-        for (int i = 0; i < PX; ++i) dold[i] = slot[i] >= 0 ? uint32_t(a.Dq[oidx[i]]) : 0u;
+        for (int i = 0; i < PX; ++i) dold[i] = slot[i] >= 0 ? uint32_t(at(a.Dq, oidx[i], samp_extent(a), 27, a.oob)) : 0u;
 #pragma unroll
         for (int i = 0; i < PX; ++i) {
             if (slot[i] < 0) continue;
-            a.samp[oidx[i]] = uint16_t(pv[i]);
+            at(a.samp, oidx[i], samp_extent(a), 28, a.oob) = uint16_t(pv[i]);
             const float q16 = __fmul_rn(dmin[i], 16.0f);
             const uint32_t q = q16 >= 65535.0f ? 65535u : __float2uint_rn(q16);
             Sv[i] = Sv[i] + q - dold[i];
-            a.Dq[oidx[i]] = uint16_t(q);
+            at(a.Dq, oidx[i], samp_extent(a), 29, a.oob) = uint16_t(q);
             cnt7[4] += 1;
         }
         if (a.propagate) put_own_slots<PX>(a, q0, c, inb, slot);
@@ -248,27 +250,31 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
             Tv[i] = Tn > a.T_upper ? a.T_upper : Tn;
         }
         if (vec) {
-            stf<PX>(a.R + pc, Rv);
-            stf<PX>(a.T + pc, Tv);
-            stu<PX>(a.S + pc, Sv);
+            stf<PX>(a.R, pc, ne, 19, a.oob, Rv);
+            stf<PX>(a.T, pc, ne, 20, a.oob, Tv);
+            stu<PX>(a.S, pc, ne, 21, a.oob, Sv);
         } else {
 #pragma unroll
             for (int i = 0; i < PX; ++i)
-                if (inb[i]) { a.R[pc + i] = Rv[i]; a.T[pc + i] = Tv[i]; a.S[pc + i] = Sv[i]; }
+                if (inb[i]) {
+                    at(a.R, pc + i, ne, 19, a.oob) = Rv[i];
+                    at(a.T, pc + i, ne, 20, a.oob) = Tv[i];
+                    at(a.S, pc + i, ne, 21, a.oob) = Sv[i];
+                }
         }
     }
 
     if (vec) {
         if constexpr (PX == 4) {
-            *reinterpret_cast<ulonglong2*>(a.prev + q0) = make_ulonglong2(pnew[0], pnew[1]);
-            *reinterpret_cast<ulonglong2*>(a.prev + q0 + 2) = make_ulonglong2(pnew[2], pnew[3]);
+            vat<ulonglong2>(a.prev, q0, 2, a.plane, 30, a.oob) = make_ulonglong2(pnew[0], pnew[1]);
+            vat<ulonglong2>(a.prev, q0 + 2, 2, a.plane, 30, a.oob) = make_ulonglong2(pnew[2], pnew[3]);
         } else if constexpr (PX == 2) {
-            *reinterpret_cast<ulonglong2*>(a.prev + q0) = make_ulonglong2(pnew[0], pnew[1]);
+            vat<ulonglong2>(a.prev, q0, 2, a.plane, 30, a.oob) = make_ulonglong2(pnew[0], pnew[1]);
         }
     } else {
 #pragma unroll
         for (int i = 0; i < PX; ++i)
-            if (inb[i]) a.prev[q0 + i] = pnew[i];
+            if (inb[i]) at(a.prev, q0 + i, a.plane, 30, a.oob) = pnew[i];
     }
 
     const int64_t p0 = int64_t(y) * a.W + x;  // mask index (unpadded frame)
@@ -276,21 +282,19 @@ __device__ __forceinline__ void classify_tile(const PbasArgs& a, const GmmArgs* 
         uint32_t m = 0;
 #pragma unroll
         for (int i = 0; i < PX; ++i) m |= (anyfg[i] ? 255u : 0u) << (8 * i);
-        if constexpr (PX == 4) *reinterpret_cast<uint32_t*>(a.mask + p0) = m;
-        else *reinterpret_cast<uint16_t*>(a.mask + p0) = uint16_t(m);
+        if constexpr (PX == 4) vat<uint32_t>(a.mask, p0, 4, a.P, 31, a.oob) = m;
+        else vat<uint16_t>(a.mask, p0, 2, a.P, 31, a.oob) = uint16_t(m);
     } else {
 #pragma unroll
         for (int i = 0; i < PX; ++i)
-            if (inb[i]) a.mask[p0 + i] = anyfg[i] ? 255 : 0;
+            if (inb[i]) at(a.mask, p0 + i, a.P, 31, a.oob) = anyfg[i] ? 255 : 0;
     }
     if (vec) {
-        stu<PX>(a.req_cur + q0, reqw);
+        stu<PX>(a.req_cur, q0, a.plane, 32, a.oob, reqw);
     } else {
 #pragma unroll
         for (int i = 0; i < PX; ++i)
-            if (inb[i]) {
-                a.req_cur[q0 + i] = reqw[i];
-            }
+            if (inb[i]) at(a.req_cur, q0 + i, a.plane, 32, a.oob) = reqw[i];
     }
 
     block_add<TY, 7>(cnt7, [&](int q) {
@@ -331,12 +335,13 @@ __global__ void __launch_bounds__(32 * TY) pbas_flush_kernel(const PbasArgs a)
     uint32_t applied[1] = {0};
     if (x < a.W && y < a.H) {
         const int64_t q = int64_t(y) * a.Wp + x;
-        const uint32_t mm = request_matches<G::SW>(sreq, threadIdx.y, threadIdx.x + 1);
+        const uint32_t mm = request_matches<G::SW>(sreq, threadIdx.y, threadIdx.x + 1, G::SH * G::SW, a.oob);
         if (a.propagate)
             applied[0] = apply_propagated<G::SW>(a, N, sreq, threadIdx.y, threadIdx.x + 1, x, y, mm,
-                                                 mm ? a.own[q] : kReqNone4);
+                                                 mm ? at(a.own, q, a.plane, 33, a.oob) : kReqNone4, G::SH * G::SW);
         else
-            applied[0] = apply_own_value<G::SW>(a, N, sreq, threadIdx.y, threadIdx.x + 1, x, y, mm, a.prev_src[q]);
+            applied[0] = apply_own_value<G::SW>(a, N, sreq, threadIdx.y, threadIdx.x + 1, x, y, mm,
+                                                at(a.prev_src, q, a.plane, 33, a.oob), G::SH * G::SW);
     }
     block_add<TY, 1>(applied, [&](int) { return a.counters + 1; });
 }
@@ -361,25 +366,25 @@ __device__ __forceinline__ void init_tile(const PbasArgs& a, const GmmArgs* gm, 
         const int col = lx0 + i + 1;
         const int64_t q = int64_t(y) * a.Wp + x + i;
         uint64_t pw = 0ull;
-        if (a.propagate) a.own[q] = kReqNone4;
+        if (a.propagate) at(a.own, q, a.plane, 34, a.oob) = kReqNone4;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const uint32_t v = sm[c * G::CH + (ly + 1) * G::SWP + col];
-            const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col);
+            const uint32_t v = at(sm, c * G::CH + (ly + 1) * G::SWP + col, 4 * G::CH, 35, a.oob);
+            const uint32_t g = sobel(sm + c * G::CH, G::SWP, ly + 1, col, G::CH, a.oob);
             gs[c] += g;
             const uint16_t sv = uint16_t(v | (g << 8));
             const int64_t b = sidx(a, N, c, 0, x + i, y);
             for (int k = 0; k < N; ++k) {
-                a.samp[b + int64_t(k) * kSeg] = sv;
-                a.Dq[b + int64_t(k) * kSeg] = 0;
+                at(a.samp, b + int64_t(k) * kSeg, samp_extent(a), 36, a.oob) = sv;
+                at(a.Dq, b + int64_t(k) * kSeg, samp_extent(a), 36, a.oob) = 0;
             }
-            a.R[int64_t(c) * a.plane + q] = c < 3 ? a.R_lower_rgb : a.R_lower_d;
-            a.T[int64_t(c) * a.plane + q] = a.T_lower;
-            a.S[int64_t(c) * a.plane + q] = 0u;
+            at(a.R, int64_t(c) * a.plane + q, rts_extent(a), 37, a.oob) = c < 3 ? a.R_lower_rgb : a.R_lower_d;
+            at(a.T, int64_t(c) * a.plane + q, rts_extent(a), 37, a.oob) = a.T_lower;
+            at(a.S, int64_t(c) * a.plane + q, rts_extent(a), 37, a.oob) = 0u;
             pw |= uint64_t(sv) << (16 * c);
         }
-        a.prev[q] = pw;
-        a.mask[int64_t(y) * a.W + x + i] = 0;
+        at(a.prev, q, a.plane, 38, a.oob) = pw;
+        at(a.mask, int64_t(y) * a.W + x + i, a.P, 39, a.oob) = 0;
     }
     block_add<TY, 4>(gs, [&](int q) { return a.gsum_cur + q; });
 }
@@ -391,34 +396,33 @@ __global__ void __launch_bounds__(32 * TY) pbas_init_kernel(const PbasArgs a)
     init_tile<NT, PX, TY>(a, nullptr, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, sm);
 }
 
-// Many streams in one persistent launch.  Entry i of the table holds stream
-// i's arguments, whether it is at frame 0, its first tile in the launch
-// (prefix sum) and its tiles per row; the table is a __grid_constant__
-// parameter, so the arguments are read from the constant bank (one copy per
-// launch, shared by every block).  Blocks take tiles round-robin: tiles of
-// one stream cost alike, and consecutive tiles of a block come from streams
-// spread over the launch, so the blocks finish together without a work
-// counter.
+// Many streams in one launch.  Entry i of the table holds stream i's
+// arguments, whether it is at frame 0, its first tile in the launch (prefix
+// sum) and its tiles per row; the table is a __grid_constant__ parameter, so
+// the arguments are read from the constant bank (one copy per launch, shared
+// by every block).  One block per tile, in the order of the streams and of
+// their tiles, as the single-stream launch orders them: tiles that share
+// sample rows and halo rows run at about the same time (a persistent grid
+// that took tiles round-robin ran 23 % slower on one 1280x720 stream).
 template <int NT, int PX, int TY, int KR>
 __global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
 pbas_batch_kernel(const __grid_constant__ PbasBatchTable T)
 {
     constexpr int KD = KR;
     __shared__ ClassifySmem<PX, TY> S;
-    for (int it = blockIdx.x; it < T.total; it += gridDim.x) {
-        int lo = 0, hi = T.n - 1;  // entry whose tile range holds `it`
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (T.e[mid].tile_off <= it) lo = mid;
-            else hi = mid - 1;
-        }
-        const PbasBatchEntry& E = T.e[lo];
-        const int local = it - E.tile_off, tx = E.tiles_x;
-        const int x0 = (local % tx) * Geo<PX, TY>::TW, y0 = (local / tx) * TY;
-        if (E.init) init_tile<NT, PX, TY, KR, KD>(E.a, &T.g[lo], x0, y0, S.sm);
-        else classify_tile<NT, PX, TY, KR, KD>(E.a, &T.g[lo], x0, y0, S, true);
-        __syncthreads();
+    const int it = int(blockIdx.x);
+    if (it >= T.total) return;
+    int lo = 0, hi = T.n - 1;  // entry whose tile range holds `it`
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.e[mid].tile_off <= it) lo = mid;
+        else hi = mid - 1;
     }
+    const PbasBatchEntry& E = T.e[lo];
+    const int local = it - E.tile_off, tx = E.tiles_x;
+    const int x0 = (local % tx) * Geo<PX, TY>::TW, y0 = (local / tx) * TY;
+    if (E.init) init_tile<NT, PX, TY, KR, KD>(E.a, &T.g[lo], x0, y0, S.sm);
+    else classify_tile<NT, PX, TY, KR, KD>(E.a, &T.g[lo], x0, y0, S, true);
 }
 
 template <int PX, int TY>
@@ -510,26 +514,6 @@ LaunchResult launch_pbas_batch(const PbasBatchTable& t, bool fused, int blocks, 
     else ok = N == 20 ? batch_shape<20, 0>(t, blocks, px, ty, s) : batch_shape<0, 0>(t, blocks, px, ty, s);
     if (!ok) return kLaunchUnsupported;
     return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
-}
-
-template <int NT, int P, int T>
-int occ_of(int threads, bool fused)
-{
-    int nb = 0;
-    const cudaError_t e = fused
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<NT, P, T, 3>, threads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pbas_batch_kernel<NT, P, T, 0>, threads, 0);
-    return e == cudaSuccess ? nb : 0;
-}
-
-int pbas_batch_blocks_per_sm(int N, int px, int ty, bool fused)
-{
-    const int threads = 32 * ty;
-#define FOS_OCC(P, T) \
-    if (px == P && ty == T) return N == 20 ? occ_of<20, P, T>(threads, fused) : occ_of<0, P, T>(threads, fused);
-    FOS_OCC(2, 8) FOS_OCC(2, 4) FOS_OCC(4, 4) FOS_OCC(4, 8) FOS_OCC(1, 8)
-#undef FOS_OCC
-    return 0;
 }
 
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s)

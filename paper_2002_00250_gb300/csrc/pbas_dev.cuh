@@ -50,13 +50,14 @@ __device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, u
         const int gy = min(max(y0 - 1 + r, 0), a.H - 1);
         const int64_t p = int64_t(gy) * a.W + gx;
         const int o = r * G::SWP + col;
-        sm[o] = a.rgb[3 * p];
-        sm[G::CH + o] = a.rgb[3 * p + 1];
-        sm[2 * G::CH + o] = a.rgb[3 * p + 2];
+        constexpr int n = 4 * G::CH;
+        at(sm, o, n, 1, a.oob) = at(a.rgb, 3 * p, 3 * a.P, 2, a.oob);
+        at(sm, G::CH + o, n, 1, a.oob) = at(a.rgb, 3 * p + 1, 3 * a.P, 2, a.oob);
+        at(sm, 2 * G::CH + o, n, 1, a.oob) = at(a.rgb, 3 * p + 2, 3 * a.P, 2, a.oob);
         const int64_t pd = mapped ? int64_t(uint32_t(gy * a.Hd) / uint32_t(a.H)) * a.Wd +
                                         int64_t(uint32_t(gx * a.Wd) / uint32_t(a.W))
                                   : p;
-        sm[3 * G::CH + o] = uint8_t(depth_to_u8(a.depth[pd], a.depth_fs));
+        at(sm, 3 * G::CH + o, n, 1, a.oob) = uint8_t(depth_to_u8(at(a.depth, pd, depth_extent(a), 3, a.oob), a.depth_fs));
     }
 }
 
@@ -71,16 +72,19 @@ __device__ __forceinline__ void stage_requests(const PbasArgs& a, int x0, int y0
         const int r = idx / G::SW, col = idx - r * G::SW;
         const int gx = x0 - 1 + col, gy = y0 - 1 + r;
         const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
-        sreq[idx] = in ? a.req_prev[int64_t(gy) * a.Wp + gx] : kReqNone4;
+        at(sreq, idx, G::SH * G::SW, 4, a.oob) = in ? at(a.req_prev, int64_t(gy) * a.Wp + gx, a.plane, 5, a.oob) : kReqNone4;
     }
 }
 
-// Gradient magnitude: 3x3 Sobel, |gx| + |gy|, >> 3, clamped to 255.
-__device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int c)
+// Gradient magnitude: 3x3 Sobel, |gx| + |gy|, >> 3, clamped to 255 (s: one
+// staged channel of ch bytes).
+__device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int c, int ch = 1 << 30,
+                                          OobWord* w = nullptr)
 {
-    const int a00 = s[(r - 1) * swp + c - 1], a01 = s[(r - 1) * swp + c], a02 = s[(r - 1) * swp + c + 1];
-    const int a10 = s[r * swp + c - 1], a12 = s[r * swp + c + 1];
-    const int a20 = s[(r + 1) * swp + c - 1], a21 = s[(r + 1) * swp + c], a22 = s[(r + 1) * swp + c + 1];
+    auto px = [&](int i) { return int(at(s, i, ch, 6, w)); };
+    const int a00 = px((r - 1) * swp + c - 1), a01 = px((r - 1) * swp + c), a02 = px((r - 1) * swp + c + 1);
+    const int a10 = px(r * swp + c - 1), a12 = px(r * swp + c + 1);
+    const int a20 = px((r + 1) * swp + c - 1), a21 = px((r + 1) * swp + c), a22 = px((r + 1) * swp + c + 1);
     const int gx = (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
     const int gy = (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
     const int m = (abs(gx) + abs(gy)) >> 3;
@@ -92,12 +96,13 @@ __device__ __forceinline__ uint32_t sobel(const uint8_t* s, int swp, int r, int 
 // asked, for channel c, to write into this pixel (its request byte for c is
 // (j << 5) | slot; 0x1F means no request).
 template <int SW>
-__device__ __forceinline__ uint32_t request_matches(const uint32_t* sreq, int ly, int col)
+__device__ __forceinline__ uint32_t request_matches(const uint32_t* sreq, int ly, int col, int n = 1 << 30,
+                                                    OobWord* w = nullptr)
 {
     uint32_t mm = 0u;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-        const uint32_t r = sreq[(ly + 1 - dir_dy(j)) * SW + (col - dir_dx(j))];
+        const uint32_t r = at(sreq, (ly + 1 - dir_dy(j)) * SW + (col - dir_dx(j)), n, 7, w);
         const uint32_t dir_ok = __vcmpeq4(r & 0xE0E0E0E0u, uint32_t(j << 5) * 0x01010101u);
         const uint32_t has = __vcmpne4(r & 0x1F1F1F1Fu, 0x1F1F1F1Fu);
         const uint32_t m = dir_ok & has & 0x08040201u;  // bit c of byte c
@@ -108,11 +113,12 @@ __device__ __forceinline__ uint32_t request_matches(const uint32_t* sreq, int ly
 
 // Slot requested by the neighbour at -dir(j) for channel c (a match exists).
 template <int SW>
-__device__ __forceinline__ int request_slot(const uint32_t* sreq, int ly, int col, int j, int c)
+__device__ __forceinline__ int request_slot(const uint32_t* sreq, int ly, int col, int j, int c,
+                                            int n = 1 << 30, OobWord* w = nullptr)
 {
     const int dy = (j == 2 || j == 6) ? 0 : ((j < 2 || j == 7) ? -1 : 1);
     const int dx = (j == 0 || j == 4) ? 0 : (j < 4 ? 1 : -1);
-    return int((sreq[(ly + 1 - dy) * SW + (col - dx)] >> (8 * c)) & 31u);
+    return int((at(sreq, (ly + 1 - dy) * SW + (col - dx), n, 8, w) >> (8 * c)) & 31u);
 }
 
 // PX pixels of uint16 / float / uint32 planes; PX = 4 uses one vector access.
@@ -201,6 +207,75 @@ __device__ __forceinline__ void stu(uint32_t* p, const uint32_t (&o)[PX])
     else *p = o[0];
 }
 
+// Range-checked forms of the plane accesses above: PX elements of `base`
+// from element i (extent n, site code for the violation record).
+template <int PX>
+__device__ __forceinline__ void ldw(const uint16_t* base, int64_t i, int64_t n, int site, OobWord* w,
+                                    uint32_t (&o)[SWords<PX>::NW])
+{
+    if constexpr (PX == 4) {
+        const uint2 v = vat<const uint2>(base, i, 4, n, site, w);
+        o[0] = v.x; o[1] = v.y;
+    } else if constexpr (PX == 2) {
+        o[0] = vat<const uint32_t>(base, i, 2, n, site, w);
+    } else {
+        o[0] = at(base, i, n, site, w);
+    }
+}
+
+template <int PX, class T, class V2, class V4>
+__device__ __forceinline__ void ldv_c(const T* base, int64_t i, int64_t n, int site, OobWord* w, T (&o)[PX])
+{
+    if constexpr (PX == 4) {
+        const V4 v = vat<const V4>(base, i, 4, n, site, w);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else if constexpr (PX == 2) {
+        const V2 v = vat<const V2>(base, i, 2, n, site, w);
+        o[0] = v.x; o[1] = v.y;
+    } else {
+        o[0] = at(base, i, n, site, w);
+    }
+}
+
+template <int PX, class T, class V2, class V4>
+__device__ __forceinline__ void stv_c(T* base, int64_t i, int64_t n, int site, OobWord* w, const T (&o)[PX])
+{
+    if constexpr (PX == 4) {
+        V4 v;
+        v.x = o[0]; v.y = o[1]; v.z = o[2]; v.w = o[3];
+        vat<V4>(base, i, 4, n, site, w) = v;
+    } else if constexpr (PX == 2) {
+        V2 v;
+        v.x = o[0]; v.y = o[1];
+        vat<V2>(base, i, 2, n, site, w) = v;
+    } else {
+        at(base, i, n, site, w) = o[0];
+    }
+}
+
+template <int PX>
+__device__ __forceinline__ void ldf(const float* b, int64_t i, int64_t n, int site, OobWord* w, float (&o)[PX])
+{
+    ldv_c<PX, float, float2, float4>(b, i, n, site, w, o);
+}
+template <int PX>
+__device__ __forceinline__ void stf(float* b, int64_t i, int64_t n, int site, OobWord* w, const float (&o)[PX])
+{
+    stv_c<PX, float, float2, float4>(b, i, n, site, w, o);
+}
+template <int PX>
+__device__ __forceinline__ void ldu(const uint32_t* b, int64_t i, int64_t n, int site, OobWord* w,
+                                    uint32_t (&o)[PX])
+{
+    ldv_c<PX, uint32_t, uint2, uint4>(b, i, n, site, w, o);
+}
+template <int PX>
+__device__ __forceinline__ void stu(uint32_t* b, int64_t i, int64_t n, int site, OobWord* w,
+                                    const uint32_t (&o)[PX])
+{
+    stv_c<PX, uint32_t, uint2, uint4>(b, i, n, site, w, o);
+}
+
 // Block-wide sums of per-thread counters: v[q] is added to dst(q) with one
 // atomicAdd per counter per block (dst maps a counter index to its address).
 template <int TY, int NV, class Dst>
@@ -235,7 +310,8 @@ __device__ __forceinline__ int64_t sidx(const PbasArgs& a, int N, int c, int k, 
 // the same value, so the order does not matter.  Returns the writes made.
 template <int SW>
 __device__ __forceinline__ uint32_t apply_own_value(const PbasArgs& a, int N, const uint32_t* sreq, int ly,
-                                                    int col, int x, int y, uint32_t mm, uint64_t pw)
+                                                    int col, int x, int y, uint32_t mm, uint64_t pw,
+                                                    int nreq = 1 << 30)
 {
     if (((pw >> 48) & 0xFFu) == 0u) mm &= 0x77777777u;
     uint32_t n = 0;
@@ -243,8 +319,8 @@ __device__ __forceinline__ uint32_t apply_own_value(const PbasArgs& a, int N, co
         const int b = __ffs(mm) - 1;
         mm &= mm - 1u;
         const int j = b >> 2, c = b & 3;
-        const int k = request_slot<SW>(sreq, ly, col, j, c);
-        a.samp[sidx(a, N, c, k, x, y)] = uint16_t(pw >> (16 * c));
+        const int k = request_slot<SW>(sreq, ly, col, j, c, nreq, a.oob);
+        at(a.samp, sidx(a, N, c, k, x, y), samp_extent(a), 9, a.oob) = uint16_t(pw >> (16 * c));
         ++n;
     }
     return n;
@@ -259,7 +335,8 @@ __device__ __forceinline__ uint32_t apply_own_value(const PbasArgs& a, int N, co
 // winner last.  Returns the writes made.
 template <int SW>
 __device__ __forceinline__ uint32_t apply_propagated(const PbasArgs& a, int N, const uint32_t* sreq, int ly,
-                                                     int col, int x, int y, uint32_t mm, uint32_t own)
+                                                     int col, int x, int y, uint32_t mm, uint32_t own,
+                                                     int nreq = 1 << 30)
 {
     mm = __byte_perm(mm, 0u, 0x1032);
     uint32_t n = 0;
@@ -267,10 +344,10 @@ __device__ __forceinline__ uint32_t apply_propagated(const PbasArgs& a, int N, c
         const int b = 31 - __clz(mm);
         mm &= ~(1u << b);
         const int j = (b >> 2) ^ 4, c = b & 3;
-        const int k = request_slot<SW>(sreq, ly, col, j, c);
+        const int k = request_slot<SW>(sreq, ly, col, j, c, nreq, a.oob);
         if (uint32_t(k) == ((own >> (8 * c)) & 0xFFu)) continue;
-        const uint64_t src = a.prev_src[int64_t(y - dir_dy(j)) * a.Wp + (x - dir_dx(j))];
-        a.samp[sidx(a, N, c, k, x, y)] = uint16_t(src >> (16 * c));
+        const uint64_t src = at(a.prev_src, int64_t(y - dir_dy(j)) * a.Wp + (x - dir_dx(j)), a.plane, 10, a.oob);
+        at(a.samp, sidx(a, N, c, k, x, y), samp_extent(a), 11, a.oob) = uint16_t(src >> (16 * c));
         ++n;
     }
     return n;
@@ -285,7 +362,8 @@ __device__ __forceinline__ void put_own_slots(const PbasArgs& a, int64_t q0, int
 #pragma unroll
     for (int i = 0; i < PX; ++i)
         if (inb[i])
-            reinterpret_cast<uint8_t*>(a.own + q0 + i)[c] = uint8_t(slot && slot[i] >= 0 ? slot[i] : 0x1F);
+            at(reinterpret_cast<uint8_t*>(a.own), 4 * (q0 + i) + c, 4 * a.plane, 12, a.oob) =
+                uint8_t(slot && slot[i] >= 0 ? slot[i] : 0x1F);
 }
 
 struct Draws {
@@ -339,18 +417,20 @@ __device__ __forceinline__ void gmm_tile_part(const GmmArgs& g, const PbasArgs& 
     if (y >= a.H || x >= a.W) return;
     const int64_t p0 = int64_t(y) * a.W + x;
     const int o = (ly + 1) * G::SWP + lx0 + 1;
+    constexpr int n = 4 * G::CH;
+    auto st = [&](int i) { return uint32_t(at(sm, i, n, 13, a.oob)); };
     if constexpr (PX == 2 && PAIR) {
         // W is even on this path: both pixels in the frame, 8-byte state accesses
-        const uint32_t r[2] = {sm[o], sm[o + 1]}, gg[2] = {sm[G::CH + o], sm[G::CH + o + 1]};
-        const uint32_t b[2] = {sm[2 * G::CH + o], sm[2 * G::CH + o + 1]};
-        const uint32_t d8[2] = {sm[3 * G::CH + o], sm[3 * G::CH + o + 1]};
+        const uint32_t r[2] = {st(o), st(o + 1)}, gg[2] = {st(G::CH + o), st(G::CH + o + 1)};
+        const uint32_t b[2] = {st(2 * G::CH + o), st(2 * G::CH + o + 1)};
+        const uint32_t d8[2] = {st(3 * G::CH + o), st(3 * G::CH + o + 1)};
         if (!g.init) {
             const uint32_t m = gmmdev::gmm_pair<KR, KD>(g, p0, r, gg, b, d8);
             if ((reinterpret_cast<uintptr_t>(g.mask) & 1u) == 0) {  // p0 is even
-                *reinterpret_cast<uint16_t*>(g.mask + p0) = uint16_t(m);
+                vat<uint16_t>(g.mask, p0, 2, g.P, 14, g.oob) = uint16_t(m);
             } else {
-                g.mask[p0] = uint8_t(m);
-                g.mask[p0 + 1] = uint8_t(m >> 8);
+                at(g.mask, p0, g.P, 14, g.oob) = uint8_t(m);
+                at(g.mask, p0 + 1, g.P, 14, g.oob) = uint8_t(m >> 8);
             }
             return;
         }
@@ -358,8 +438,9 @@ __device__ __forceinline__ void gmm_tile_part(const GmmArgs& g, const PbasArgs& 
 #pragma unroll 1
     for (int i = 0; i < PX; ++i) {
         if (x + i >= a.W) break;
-        g.mask[p0 + i] = gmmdev::gmm_pixel_lowreg<KR, KD>(g, p0 + i, sm[o + i], sm[G::CH + o + i],
-                                                          sm[2 * G::CH + o + i], sm[3 * G::CH + o + i]);
+        at(g.mask, p0 + i, g.P, 14, g.oob) =
+            gmmdev::gmm_pixel_lowreg<KR, KD>(g, p0 + i, st(o + i), st(G::CH + o + i), st(2 * G::CH + o + i),
+                                             st(3 * G::CH + o + i));
     }
 }
 
@@ -377,13 +458,13 @@ __device__ __forceinline__ void prefetch_l1(const void* p)
 template <int NT>
 __device__ __forceinline__ void prefetch_channel(const PbasArgs& a, int N, int c, int x, int y, int64_t q0)
 {
-    const uint16_t* sb = a.samp + sidx(a, N, c, 0, x, y);
+    const int64_t s0 = sidx(a, N, c, 0, x, y);
 #pragma unroll(NT > 0 ? NT : 4)
-    for (int k = 0; k < N; ++k) prefetch_l1(sb + int64_t(k) * kSeg);
+    for (int k = 0; k < N; ++k) prefetch_l1(&at(a.samp, s0 + int64_t(k) * kSeg, samp_extent(a), 15, a.oob));
     const int64_t pc = int64_t(c) * a.plane + q0;
-    prefetch_l1(a.R + pc);
-    prefetch_l1(a.T + pc);
-    prefetch_l1(a.S + pc);
+    prefetch_l1(&at(a.R, pc, rts_extent(a), 15, a.oob));
+    prefetch_l1(&at(a.T, pc, rts_extent(a), 15, a.oob));
+    prefetch_l1(&at(a.S, pc, rts_extent(a), 15, a.oob));
 }
 
 // fl(S / d) for an integer 0 <= S < 2^24 and an integer divisor 1 <= d < 2^23,

@@ -16,6 +16,7 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfos.so")
+BOUNDS_LIB_PATH = os.path.join(_PKG, "libfos_bounds.so")  # range-checked build (build.build(bounds=True))
 
 METHOD_GMM = 1
 METHOD_PBAS = 2
@@ -127,6 +128,9 @@ SIGNATURES = {
     "fos_quality_counts_device": (_st, [_vp, _vp, _i64, _vp, _vp]),
     "fos_quality_metrics": (None, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
     "fos_pbas_step_noalloc": (_st, [_i32, _i32, ctypes.POINTER(Params), _i64, _vp, _vp, _vp, _vp, _vp]),
+    "fos_bounds_checked": (_i32, []),
+    "fos_bounds_status": (_st, [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_i64)]),
+    "fos_bounds_selftest": (_st, [ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_i64)]),
     "fos_stream_device_bytes": (ctypes.c_size_t, [_i32, _i32, ctypes.POINTER(Params)]),
     "fos_batch_create": (_vp, [_i32, ctypes.POINTER(Params)]),
     "fos_batch_destroy": (None, [_vp]),
@@ -361,6 +365,13 @@ class Segmenter:
 
     def get_option(self, option: int) -> int:
         return int(self.lib.fos_get_option(self.h, option))
+
+    def bounds_status(self):
+        """(violations, first site code, first index) of a range-checked build;
+        raises FosError in a release build."""
+        n, site, idx = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+        self._check(self.lib.fos_bounds_status(self.h, ctypes.byref(n), ctypes.byref(site), ctypes.byref(idx)))
+        return n.value, site.value, idx.value
 
     def get_counters(self) -> dict:
         arr = (ctypes.c_uint64 * 4)()
