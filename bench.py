@@ -226,6 +226,13 @@ def run_ours(args):
     if args.pbas_joint:  # profiler captures of the joint-channel PBAS kernel alone
         seg = fos.Segmenter(W, H, stream_id=rank, methods=fos.METHOD_PBAS, pbas_joint=1)
         mg = None
+    elif args.methods != "both":  # profiler captures of one method's kernel alone
+        seg = fos.Segmenter(W, H, stream_id=rank,
+                            methods=fos.METHOD_GMM if args.methods == "gmm" else fos.METHOD_PBAS)
+        if args.methods == "gmm":
+            mp = None
+        else:
+            mg = None
     else:
         seg = fos.Segmenter(W, H, stream_id=rank)
     stream = torch.cuda.Stream(device=dev)
@@ -905,7 +912,8 @@ def run_serve32(args):
                                "max": round(float(np.max(lat)) / 1e3, 3)},
                 "queue_ms_p50": round(float(np.percentile(queue, 50)) / 1e3, 3),
                 "ticks": st["ticks"], "frames_per_tick": round(st["frames_done"] / max(1, st["ticks"]), 2),
-                "gpu_busy_s": round(st["busy_us"] / 1e6, 3)}
+                "gpu_busy_s": round(st["busy_us"] / 1e6, 3),
+                "housekeeping_s": round(st["housekeeping_us"] / 1e6, 3)}
 
     paced = run(True)
     saturated = run(False)
@@ -933,11 +941,13 @@ def main():
                     help="run the device-resident steps only (for profiler captures)")
     ap.add_argument("--pbas-joint", action="store_true",
                     help="with --kernels-only: the joint-channel PBAS variant alone (profiler captures)")
+    ap.add_argument("--methods", default="both", choices=["both", "gmm", "pbas"],
+                    help="with --kernels-only: one method's kernel alone (profiler captures)")
     ap.add_argument("--workload", default="720p", choices=["720p", "batch16", "softgmm", "serve32", "table"],
                     help="720p: the headline single-stream sequence; batch16: 16 mixed streams")
     args = ap.parse_args()
-    if args.pbas_joint and not args.kernels_only:
-        ap.error("--pbas-joint is for --kernels-only profiler captures")
+    if (args.pbas_joint or args.methods != "both") and not args.kernels_only:
+        ap.error("--pbas-joint and --methods are for --kernels-only profiler captures")
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch16":

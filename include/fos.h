@@ -405,9 +405,12 @@ fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
  * by a device-memory budget: each needs fos_stream_device_bytes plus three
  * input and three mask buffers (3 * 7 bytes per pixel, plus up to 15 bytes of
  * alignment per input buffer); a stream that does not fit, or finds no free
- * slot, waits in FIFO order until others close.  fos_server_submit copies a
- * frame into one of the stream's queue_depth pinned input slots (allocated at
- * admission) and returns at once.  Each worker tick takes
+ * slot, waits in FIFO order until others close.  A housekeeping thread
+ * allocates an admitted stream's memory and frees that of streams that left,
+ * so the worker's ticks never wait on an allocation or a free.
+ * fos_server_submit copies a frame into one of the stream's queue_depth
+ * pinned input slots (allocated by its first copying submit) and returns at
+ * once.  Each worker tick takes
  * the oldest pending frame of every admitted stream (frames of one stream run
  * in order), runs them as one batched launch, and writes the masks into the
  * caller's buffers given at submit time; three ticks are in flight (the
@@ -430,6 +433,8 @@ typedef struct fos_server_stats_t {
     size_t device_bytes_used;
     int32_t streams_active, streams_waiting;
     double busy_us;      /* sum over ticks of launch -> completion */
+    double housekeeping_us;  /* time the housekeeping thread spent allocating
+                                and freeing streams' memory */
 } fos_server_stats_t;
 
 /* Server over one device-memory budget (bytes), at most max_streams admitted
@@ -447,7 +452,10 @@ int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uin
 fos_status fos_server_close_stream(fos_server* s, int32_t stream);
 /* Queues one host frame of the stream (copied before returning).  The masks
  * (either may be NULL) are written when the frame completes: keep those
- * buffers valid until fos_server_poll reports the tag.  The frame is not
+ * buffers valid until fos_server_poll reports the tag.  Pinned mask buffers
+ * are written by DMA; pageable ones through the stream's pinned staging.
+ * The stream's first submit that needs its pinned input slots or its mask
+ * staging allocates them (FOS_ERR_OOM if pinned memory is exhausted).  The frame is not
  * taken (drop it or retry) with FOS_ERR_BUDGET while the stream still waits
  * for admission, and with FOS_ERR_BUSY while it has queue_depth frames queued
  * or running. */

@@ -175,6 +175,29 @@ fos_status replay(fos_batch* b, cudaStream_t s)
 
 }  // namespace
 
+namespace fos {
+
+int32_t batch_attach(fos_batch* b, fos_ctx* c)
+{
+    if (!b || !c) return -1;
+    for (int i = 0; i < b->max_streams; ++i)
+        if (!b->slot[i]) {
+            b->slot[i] = c;
+            return i;
+        }
+    return -1;
+}
+
+fos_ctx* batch_detach(fos_batch* b, int32_t slot)
+{
+    if (!b || slot < 0 || slot >= b->max_streams) return nullptr;
+    fos_ctx* c = b->slot[slot];
+    b->slot[slot] = nullptr;
+    return c;
+}
+
+}  // namespace fos
+
 extern "C" {
 
 size_t fos_stream_device_bytes(int32_t width, int32_t height, const fos_params* p)
@@ -271,6 +294,7 @@ fos_status fos_batch_remove_stream(fos_batch* b, int32_t slot)
     b->slot[slot] = nullptr;
     return FOS_OK;
 }
+
 
 fos_ctx* fos_batch_stream(fos_batch* b, int32_t slot)
 {

@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+struct fos_batch;
+struct fos_ctx;
+
 namespace fos {
 
 // Launch status of an internal launcher.
@@ -255,5 +258,12 @@ cudaError_t dev_alloc(void** p, size_t bytes);
 
 // Sets the text fos_last_error(NULL) returns on the calling thread.
 void set_thread_error(const char* msg);
+
+// Puts an existing context (same parameters as the batch) into a free slot of
+// the batch without allocating; returns the slot, or -1 if none is free.
+int32_t batch_attach(fos_batch* b, fos_ctx* c);
+// Takes the context out of the slot without freeing it (NULL if empty).  The
+// caller guarantees that no step still in flight uses it.
+fos_ctx* batch_detach(fos_batch* b, int32_t slot);
 
 }  // namespace fos

@@ -4,15 +4,24 @@
 // an HBM budget: a stream needs its device-resident models plus three input
 // and three mask buffers; a stream that does not fit waits (FIFO) until others
 // leave.  fos_server_submit copies a frame into one of the stream's pinned
-// input slots (allocated once, at admission) and returns at once; with no
-// free slot, or before admission, it refuses the frame (backpressure).  A worker thread runs ticks: each tick takes the oldest
-// pending frame of every admitted stream (at most one per stream, so every
-// stream's frames run in order), copies them to the device, runs ONE batched
-// launch over all of them (fos_batch), and copies the masks back.  Three
-// ticks are in flight, on three CUDA streams (input copies, kernels, mask
-// copies): frames that arrive while a tick runs are admitted into the next
-// one.  Completed frames are delivered into the caller's mask buffers
-// and reported by fos_server_poll with their latency.
+// input slots and returns at once; with no free slot, or before admission,
+// it refuses the frame (backpressure).  A worker thread runs ticks: each tick
+// takes the oldest pending frame of every admitted stream (at most one per
+// stream, so every stream's frames run in order), copies them to the device,
+// runs ONE batched launch over all of them (fos_batch), and copies the masks
+// back.  Three ticks are in flight, on three CUDA streams (input copies,
+// kernels, mask copies): frames that arrive while a tick runs are admitted
+// into the next one.  Completed frames are delivered into the caller's mask
+// buffers and reported by fos_server_poll with their latency.
+//
+// No allocation or free runs on the worker thread.  A housekeeping thread
+// creates an admitted stream's context and device buffers and hands them to
+// the worker, which only puts them into a batch slot between ticks; when a
+// stream leaves, the worker takes it out of its slot and the housekeeper
+// frees its memory (cudaFree waits for the device, which would otherwise
+// drain the pipeline).  Pinned host staging (the input slots of copying
+// submits, the mask staging for pageable mask buffers) is allocated by the
+// first submit of the stream that needs it, on the submitting thread.
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -50,9 +59,11 @@ struct Frame {
     double t_submit;
 };
 
+size_t round16(size_t n) { return (n + 15) / 16 * 16; }
+
 // Byte offset of the depth plane in an input buffer (host slot or device):
 // 16-byte aligned whatever the pixel count.
-size_t depth_offset(size_t P) { return (P * 3 + 15) / 16 * 16; }
+size_t depth_offset(size_t P) { return round16(P * 3); }
 
 // Ticks in flight: the input copies of one tick, the kernels of another and
 // the mask copies of a third run at the same time.
@@ -71,6 +82,8 @@ bool host_pinned(const void* p)
     return a.type == cudaMemoryTypeHost;
 }
 size_t input_bytes(size_t P) { return depth_offset(P) + P * 2; }
+// One mask buffer: P bytes and 16 of slack, 16-byte aligned.
+size_t mask_bytes(size_t P) { return round16(P + 16); }
 
 struct Stream {
     int id;              // server handle
@@ -78,20 +91,25 @@ struct Stream {
     uint32_t stream_id;
     size_t bytes = 0;    // device bytes charged against the budget
     int slot = -1;       // batch slot once admitted
+    bool admitting = false;  // the housekeeper is allocating its memory
     bool closing = false;
+    fos_ctx* ctx = nullptr;  // its models, from the housekeeper
     std::deque<Frame> pending;
     int inflight = 0;    // frames of this stream in ticks not yet completed
     // by frame number mod kTicks: a stream has at most one frame in each of
     // the kTicks ticks in flight
+    uint8_t* dbuf = nullptr;                   // the device buffers below, one allocation
     uint8_t* d_in[kTicks] = {};                // device rgb+depth
     uint8_t* d_mg[kTicks] = {};
     uint8_t* d_mp[kTicks] = {};
-    uint8_t* h_mg[kTicks] = {};                // pinned mask staging
+    uint8_t* hstage = nullptr;                 // pinned mask staging, on first need
+    uint8_t* h_mg[kTicks] = {};
     uint8_t* h_mp[kTicks] = {};
     int64_t nframes = 0;
-    uint8_t* arena = nullptr;                    // pinned input slots, allocated at admission
-    int copying = 0;                             // submits writing into a slot right now
-    std::vector<uint8_t*> free_in;               // free slots of the arena
+    uint8_t* arena = nullptr;                  // pinned input slots, on the first copying submit
+    bool host_alloc = false;                   // a submit is allocating arena or staging now
+    int copying = 0;                           // submits writing into a slot (or allocating) now
+    std::vector<uint8_t*> free_in;             // free slots of the arena
 };
 
 struct TickItem {
@@ -108,21 +126,13 @@ struct Tick {
     double t_launch = 0.0;
 };
 
-void destroy_events(Tick& t)
-{
-    for (cudaEvent_t* e : {&t.in, &t.k, &t.done})
-        if (*e) {
-            cudaEventDestroy(*e);
-            *e = nullptr;
-        }
-}
-
 }  // namespace
 
 struct fos_server {
     fos_params prm{};
-    size_t budget = 0, used = 0;
+    size_t budget = 0, used = 0;      // used: device bytes held, freed ones excluded
     int max_streams = 0;
+    int resident = 0;                 // streams holding (or being given) a batch slot
     int queue_depth = 16;             // pinned input slots per stream
     fos_batch* batch = nullptr;
     cudaStream_t cs = nullptr;        // batched kernels
@@ -130,15 +140,20 @@ struct fos_server {
     cudaStream_t cout = nullptr;      // mask copies
     int device = 0;
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;       // wakes the worker (and waiting submitters)
+    std::condition_variable hcv;      // wakes the housekeeper
     std::vector<Stream*> streams;     // by handle (nullptr once gone)
     std::deque<int> waiting;          // handles waiting for admission
+    std::vector<int> ready;           // handles whose memory is ready for a slot
+    std::deque<Stream*> dead;         // left their slot; memory to be freed
+    bool admit_blocked = false;       // an allocation failed: retry once memory comes back
     std::deque<fos_server_result> results;
-    std::thread worker;
+    std::thread worker, housekeeper;
     bool stop = false;
     std::string err;
     int64_t ticks = 0, frames_done = 0;
-    double busy_us = 0.0;
+    double busy_us = 0.0, house_us = 0.0;
+    std::vector<cudaEvent_t> events;  // free tick events (created once, reused)
 };
 
 namespace {
@@ -149,57 +164,141 @@ size_t stream_bytes(const fos_server* s, int32_t W, int32_t H)
     return fos_stream_device_bytes(W, H, &s->prm) + kTicks * (input_bytes(P) + 2 * P);
 }
 
-void free_stream_buffers(Stream* st)
+size_t slot_bytes(size_t P) { return round16(input_bytes(P)); }
+
+// Context and device buffers of an admitted stream (housekeeper thread, no lock).
+bool allocate_stream(fos_server* s, Stream* st, std::string& why)
 {
-    cudaFreeHost(st->arena);
-    st->arena = nullptr;
-    st->free_in.clear();
+    fos_params p = s->prm;
+    p.stream_id = st->stream_id;
+    st->ctx = fos_create(st->W, st->H, &p);
+    if (!st->ctx) {
+        why = std::string("admission: ") + fos_last_error(nullptr);
+        return false;
+    }
+    const size_t P = size_t(st->W) * size_t(st->H);
+    const size_t per = slot_bytes(P) + 2 * mask_bytes(P);
+    if (dev_alloc(reinterpret_cast<void**>(&st->dbuf), kTicks * per) != cudaSuccess) {
+        cudaGetLastError();
+        fos_destroy(st->ctx);
+        st->ctx = nullptr;
+        st->dbuf = nullptr;
+        why = "admission: device memory exhausted (frame buffers)";
+        return false;
+    }
     for (int k = 0; k < kTicks; ++k) {
-        cudaFree(st->d_in[k]);
-        cudaFree(st->d_mg[k]);
-        cudaFree(st->d_mp[k]);
-        cudaFreeHost(st->h_mg[k]);
-        cudaFreeHost(st->h_mp[k]);
-        st->d_in[k] = st->d_mg[k] = st->d_mp[k] = st->h_mg[k] = st->h_mp[k] = nullptr;
+        uint8_t* b = st->dbuf + size_t(k) * per;
+        st->d_in[k] = b;
+        st->d_mg[k] = b + slot_bytes(P);
+        st->d_mp[k] = b + slot_bytes(P) + mask_bytes(P);
+    }
+    return true;
+}
+
+// Everything a stream holds, device and host (housekeeper or destroy; no lock).
+void release_stream(Stream* st)
+{
+    if (st->ctx) fos_destroy(st->ctx);
+    st->ctx = nullptr;
+    cudaFree(st->dbuf);
+    cudaFreeHost(st->arena);
+    cudaFreeHost(st->hstage);
+    st->dbuf = st->arena = st->hstage = nullptr;
+    st->free_in.clear();
+}
+
+// Frees what streams that left held and allocates the memory of waiting
+// streams, FIFO, while they fit the budget and a batch slot is free.
+void housekeeper_main(fos_server* s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        if (!s->dead.empty()) {
+            Stream* st = s->dead.front();
+            s->dead.pop_front();
+            lk.unlock();
+            const double t0 = now_us();
+            release_stream(st);
+            const double dt = now_us() - t0;
+            lk.lock();
+            s->used -= st->bytes;
+            s->house_us += dt;
+            s->admit_blocked = false;  // memory came back: a failed admission may fit now
+            delete st;
+            continue;
+        }
+        if (s->stop) break;
+        Stream* next = nullptr;
+        while (!s->waiting.empty() && !(next = s->streams[s->waiting.front()])) s->waiting.pop_front();
+        if (next && !s->admit_blocked && s->resident < s->max_streams && s->used + next->bytes <= s->budget) {
+            s->waiting.pop_front();
+            s->used += next->bytes;
+            s->resident += 1;
+            next->admitting = true;
+            lk.unlock();
+            const double t0 = now_us();
+            std::string why;
+            const bool ok = allocate_stream(s, next, why);
+            const double dt = now_us() - t0;
+            lk.lock();
+            s->house_us += dt;
+            next->admitting = false;
+            if (ok) {
+                s->ready.push_back(next->id);
+                s->cv.notify_all();
+            } else {
+                s->used -= next->bytes;
+                s->resident -= 1;
+                s->waiting.push_front(next->id);
+                s->err = why;
+                s->admit_blocked = true;
+            }
+            continue;
+        }
+        s->hcv.wait(lk);
     }
 }
 
-// Admits waiting streams in FIFO order while they fit (worker thread, lock held).
-void admit(fos_server* s)
+// Streams whose memory is ready take a batch slot (worker thread, lock held).
+void attach_ready(fos_server* s)
 {
-    while (!s->waiting.empty()) {
-        Stream* st = s->streams[s->waiting.front()];
-        if (!st) {
-            s->waiting.pop_front();
+    for (int h : s->ready) {
+        Stream* st = s->streams[h];
+        const int slot = batch_attach(s->batch, st->ctx);
+        if (slot < 0) {  // cannot happen: resident streams never exceed the slots
+            s->err = "admission: no free batch slot";
+            s->resident -= 1;
+            s->streams[h] = nullptr;
+            s->dead.push_back(st);
+            s->hcv.notify_all();
             continue;
         }
-        if (s->used + st->bytes > s->budget) break;
-        const int slot = fos_batch_add_stream(s->batch, st->W, st->H, st->stream_id);
-        if (slot < 0) break;  // no free slot yet
-        const size_t P = size_t(st->W) * size_t(st->H);
-        bool ok = true;
-        const size_t slot_bytes = (input_bytes(P) + 15) / 16 * 16;
-        ok = cudaMallocHost(&st->arena, size_t(s->queue_depth) * slot_bytes) == cudaSuccess;
-        if (ok) {
-            st->free_in.clear();
-            for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(st->arena + size_t(q) * slot_bytes);
-        }
-        for (int k = 0; k < kTicks && ok; ++k) {
-            ok = cudaMalloc(&st->d_in[k], input_bytes(P)) == cudaSuccess &&
-                 cudaMalloc(&st->d_mg[k], P + 16) == cudaSuccess &&
-                 cudaMalloc(&st->d_mp[k], P + 16) == cudaSuccess &&
-                 cudaMallocHost(&st->h_mg[k], P + 16) == cudaSuccess &&
-                 cudaMallocHost(&st->h_mp[k], P + 16) == cudaSuccess;
-        }
-        if (!ok) {
-            free_stream_buffers(st);
-            fos_batch_remove_stream(s->batch, slot);
-            s->err = "admission: device or pinned memory exhausted";
-            break;
-        }
         st->slot = slot;
-        s->used += st->bytes;
-        s->waiting.pop_front();
+    }
+    s->ready.clear();
+}
+
+// Streams that asked to close and have nothing left leave their slot; the
+// housekeeper frees their memory (worker thread, lock held).
+void retire(fos_server* s)
+{
+    for (size_t h = 0; h < s->streams.size(); ++h) {
+        Stream* st = s->streams[h];
+        if (!st || !st->closing || !st->pending.empty() || st->inflight > 0 || st->copying > 0 ||
+            st->admitting || (st->ctx && st->slot < 0))
+            continue;
+        s->streams[h] = nullptr;
+        if (st->slot >= 0) {
+            // all of its ticks have completed, so no step in flight uses it
+            batch_detach(s->batch, st->slot);
+            st->slot = -1;
+            s->resident -= 1;
+            s->dead.push_back(st);
+            s->hcv.notify_all();
+        } else {
+            delete st;  // never admitted: holds nothing
+        }
     }
 }
 
@@ -224,23 +323,24 @@ void publish(fos_server* s, Tick& t)
         st->inflight -= 1;
         s->frames_done += 1;
     }
-    destroy_events(t);
+    for (cudaEvent_t* e : {&t.in, &t.k, &t.done})
+        if (*e) {
+            s->events.push_back(*e);
+            *e = nullptr;
+        }
 }
 
-// Streams that asked to close and have nothing left leave; their memory is freed.
-void retire(fos_server* s)
+cudaError_t take_event(fos_server* s, cudaEvent_t* e)
 {
-    for (size_t h = 0; h < s->streams.size(); ++h) {
-        Stream* st = s->streams[h];
-        if (!st || !st->closing || !st->pending.empty() || st->inflight > 0 || st->copying > 0) continue;
-        if (st->slot >= 0) {
-            fos_batch_remove_stream(s->batch, st->slot);
-            s->used -= st->bytes;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->events.empty()) {
+            *e = s->events.back();
+            s->events.pop_back();
+            return cudaSuccess;
         }
-        free_stream_buffers(st);
-        delete st;
-        s->streams[h] = nullptr;
     }
+    return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
 }
 
 void worker_main(fos_server* s)
@@ -255,19 +355,19 @@ void worker_main(fos_server* s)
         Tick t;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            attach_ready(s);
             retire(s);
-            admit(s);
             auto ready = [&] {
-                if (s->stop) return true;
+                if (s->stop || !s->ready.empty()) return true;
                 for (Stream* st : s->streams)
-                    if (st && st->slot >= 0 && !st->pending.empty()) return true;
+                    if (st && st->slot >= 0 && (!st->pending.empty() || st->closing)) return true;
                 return false;
             };
-            // idle: sleep until a frame arrives (or re-check admission and
-            // closing streams every millisecond)
+            // idle: sleep until a frame arrives, memory is ready for a stream,
+            // or a stream asks to close (or re-check every millisecond)
             if (inflight.empty()) s->cv.wait_for(lk, std::chrono::milliseconds(1), ready);
             if (s->stop && inflight.empty()) break;
-            if (!ready() && inflight.empty()) continue;
+            attach_ready(s);
             // continuous batching: the oldest frame of every admitted stream
             // whose previous frame is not still using this parity's buffers
             for (size_t h = 0; h < s->streams.size(); ++h) {
@@ -308,9 +408,9 @@ void worker_main(fos_server* s)
             // the input copies of this tick overlap the previous tick's kernels,
             // its mask copies the next tick's (at most kTicks ticks in flight,
             // and a stream's frames in them use different buffers)
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.in, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.k, cudaEventDisableTiming);
-            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = take_event(s, &t.in);
+            if (e == cudaSuccess) e = take_event(s, &t.k);
+            if (e == cudaSuccess) e = take_event(s, &t.done);
             if (e == cudaSuccess) e = cudaEventRecord(t.in, s->cin);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, t.in, 0);
             t.t_launch = now_us();
@@ -344,7 +444,9 @@ void worker_main(fos_server* s)
                     s->streams[it.stream]->inflight -= 1;
                     if (it.f.host_in) s->streams[it.stream]->free_in.push_back(it.f.host_in);
                 }
-                destroy_events(t);
+                for (cudaEvent_t ev : {t.in, t.k, t.done})
+                    if (ev) s->events.push_back(ev);
+                s->hcv.notify_all();
                 break;
             }
             inflight.push_back(std::move(t));
@@ -372,6 +474,73 @@ void worker_main(fos_server* s)
         std::lock_guard<std::mutex> lk(s->mu);
         publish(s, t);
     }
+}
+
+Stream* live_stream(fos_server* s, int32_t stream)
+{
+    if (stream < 0 || stream >= int32_t(s->streams.size())) return nullptr;
+    Stream* st = s->streams[stream];
+    return st && !st->closing ? st : nullptr;
+}
+
+// Allocates, on first need, a stream's pinned input slots (copying submits)
+// and its pinned mask staging (masks bound for pageable buffers), on the
+// calling thread without the lock held.  FOS_ERR_BUSY while another submit of
+// the stream is allocating them.
+fos_status ensure_host_memory(fos_server* s, int32_t stream, bool arena, bool stage)
+{
+    size_t P;
+    bool need_arena, need_stage;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        Stream* st = live_stream(s, stream);
+        if (!st) return FOS_ERR_INVALID_ARG;
+        if (s->stop) return FOS_ERR_STATE;
+        if (st->slot < 0) return FOS_ERR_BUDGET;  // still waiting for admission
+        need_arena = arena && !st->arena;
+        need_stage = stage && !st->hstage;
+        if (!need_arena && !need_stage) return FOS_OK;
+        if (st->host_alloc) return FOS_ERR_BUSY;
+        st->host_alloc = true;
+        st->copying += 1;  // keeps the stream from leaving meanwhile
+        P = size_t(st->W) * size_t(st->H);
+    }
+    uint8_t* a = nullptr;
+    uint8_t* g = nullptr;
+    bool ok = true;
+    if (need_arena)
+        ok = cudaHostAlloc(reinterpret_cast<void**>(&a), size_t(s->queue_depth) * slot_bytes(P),
+                           cudaHostAllocDefault) == cudaSuccess;
+    if (ok && need_stage)
+        ok = cudaHostAlloc(reinterpret_cast<void**>(&g), kTicks * 2 * mask_bytes(P), cudaHostAllocDefault) ==
+             cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFreeHost(a);
+        a = nullptr;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    Stream* st = s->streams[stream];
+    st->host_alloc = false;
+    st->copying -= 1;
+    if (!ok) {
+        s->err = "submit: pinned host memory exhausted";
+        set_thread_error(s->err.c_str());
+        return FOS_ERR_OOM;
+    }
+    if (a) {
+        st->arena = a;
+        st->free_in.clear();
+        for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(a + size_t(q) * slot_bytes(P));
+    }
+    if (g) {
+        st->hstage = g;
+        for (int k = 0; k < kTicks; ++k) {
+            st->h_mg[k] = g + size_t(2 * k) * mask_bytes(P);
+            st->h_mp[k] = g + size_t(2 * k + 1) * mask_bytes(P);
+        }
+    }
+    return FOS_OK;
 }
 
 }  // namespace
@@ -404,6 +573,7 @@ fos_server* fos_server_create(const fos_params* params, size_t hbm_budget_bytes,
         return nullptr;
     }
     s->worker = std::thread(worker_main, s);
+    s->housekeeper = std::thread(housekeeper_main, s);
     return s;
 }
 
@@ -415,13 +585,23 @@ void fos_server_destroy(fos_server* s)
         s->stop = true;
     }
     s->cv.notify_all();
+    s->hcv.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    if (s->housekeeper.joinable()) s->housekeeper.join();
+    // the worker has finished every tick: take the streams out of their slots
+    // (the batch would otherwise free their contexts) and free them here
+    for (Stream* st : s->dead) {
+        release_stream(st);
+        delete st;
+    }
     for (Stream* st : s->streams) {
         if (!st) continue;
-        free_stream_buffers(st);
+        if (st->slot >= 0) batch_detach(s->batch, st->slot);
+        release_stream(st);
         delete st;
     }
     fos_batch_destroy(s->batch);
+    for (cudaEvent_t e : s->events) cudaEventDestroy(e);
     cudaStreamDestroy(s->cs);
     cudaStreamDestroy(s->cin);
     cudaStreamDestroy(s->cout);
@@ -447,7 +627,7 @@ int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uin
     st->id = int(s->streams.size());
     s->streams.push_back(st);
     s->waiting.push_back(st->id);
-    s->cv.notify_all();
+    s->hcv.notify_all();
     return st->id;
 }
 
@@ -469,14 +649,15 @@ fos_status fos_server_submit(fos_server* s, int32_t stream, const uint8_t* rgb, 
     f.tag = tag;
     f.out_gmm = mask_gmm;
     f.out_pbas = mask_pbas;
+    f.direct_out = host_pinned(mask_gmm) && host_pinned(mask_pbas);
+    const fos_status hs = ensure_host_memory(s, stream, true, !f.direct_out);
+    if (hs != FOS_OK) return hs;
     size_t P;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream] || s->streams[stream]->closing)
-            return FOS_ERR_INVALID_ARG;
+        Stream* st = live_stream(s, stream);
+        if (!st) return FOS_ERR_INVALID_ARG;
         if (s->stop) return FOS_ERR_STATE;
-        Stream* st = s->streams[stream];
-        if (st->slot < 0) return FOS_ERR_BUDGET;        // still waiting for admission
         if (int(st->pending.size()) + st->inflight + st->copying >= s->queue_depth || st->free_in.empty())
             return FOS_ERR_BUSY;  // queue full
         f.host_in = st->free_in.back();
@@ -508,13 +689,13 @@ fos_status fos_server_submit_nocopy(fos_server* s, int32_t stream, const uint8_t
     f.out_gmm = mask_gmm;
     f.out_pbas = mask_pbas;
     f.direct_out = host_pinned(mask_gmm) && host_pinned(mask_pbas);
+    const fos_status hs = ensure_host_memory(s, stream, false, !f.direct_out);
+    if (hs != FOS_OK) return hs;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (stream < 0 || stream >= int32_t(s->streams.size()) || !s->streams[stream] || s->streams[stream]->closing)
-            return FOS_ERR_INVALID_ARG;
+        Stream* st = live_stream(s, stream);
+        if (!st) return FOS_ERR_INVALID_ARG;
         if (s->stop) return FOS_ERR_STATE;
-        Stream* st = s->streams[stream];
-        if (st->slot < 0) return FOS_ERR_BUDGET;  // still waiting for admission
         if (int(st->pending.size()) + st->inflight + st->copying >= s->queue_depth) return FOS_ERR_BUSY;
         f.t_submit = now_us();
         st->pending.push_back(f);
@@ -548,6 +729,7 @@ fos_status fos_server_stats(fos_server* s, fos_server_stats_t* out)
     out->streams_active = active;
     out->streams_waiting = waiting;
     out->busy_us = s->busy_us;
+    out->housekeeping_us = s->house_us;
     return s->stop && !s->err.empty() ? FOS_ERR_CUDA : FOS_OK;
 }
 

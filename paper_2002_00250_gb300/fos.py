@@ -90,7 +90,8 @@ class ServerResult(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("ticks", ctypes.c_int64), ("frames_done", ctypes.c_int64),
                 ("device_bytes_used", ctypes.c_size_t), ("streams_active", ctypes.c_int32),
-                ("streams_waiting", ctypes.c_int32), ("busy_us", ctypes.c_double)]
+                ("streams_waiting", ctypes.c_int32), ("busy_us", ctypes.c_double),
+                ("housekeeping_us", ctypes.c_double)]
 
 
 class KernelTiming(ctypes.Structure):
