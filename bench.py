@@ -36,6 +36,8 @@ ALGO_BYTES = {
     "gmm_step": 198.0,        # 96 B state read + 96 B written + 5 B input + 1 B mask
     "pbas_classify": 246.0,   # 160 B samples + 48 B R,T,S read + 32 B R,T written + 5 in + 1 mask
     "fused_classify": 439.0,  # both of the above, the 5 B input read once
+    "fused_sequence": 439.0,  # the same per frame, several frames per launch (its
+                              # gradient-sum pre-pass re-reads the input: not counted)
 }
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e nominal, for context beside the measured peak
 SPARSE_OWN = 10.0   # per own update: 2 B sample + 2 B D read + 2 B D write + 4 B S write
@@ -128,23 +130,28 @@ def _dist():
     return ws, rank, int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def _traffic_for(kernel: str, pixels: int):
-    """DRAM bytes per launch from the committed ncu summary, if it still
-    describes the current kernel source; else None."""
+def _traffic_for(kernel: str, pixels: int):  # pixels: pixel-frames of one launch
+    """(DRAM bytes per launch, where they come from) from the committed ncu
+    summary, if it still describes the current kernel source; else (None,
+    why not).  The capture is one cold-cache launch (serialised, caches
+    flushed by ncu); its bytes per pixel are scaled to this frame size."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_1280x720.md")
     files = {"gmm_step": ["gmm.cu", "gmm_dev.cuh"], "pbas_classify": ["pbas.cu", "pbas_dev.cuh"],
              # the fused kernel also compiles the GMM device code
-             "fused_classify": ["pbas.cu", "pbas_dev.cuh", "gmm_dev.cuh"]}.get(kernel, [])
+             "fused_classify": ["pbas.cu", "pbas_dev.cuh", "gmm_dev.cuh"],
+             "fused_sequence": ["pbas.cu", "pbas_dev.cuh", "gmm_dev.cuh"]}.get(kernel, [])
     srcs = [os.path.join(ROOT, "paper_2002_00250_gb300", "csrc", f) for f in files]
     try:
         txt = open(path).read()
         sha = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         fields = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("traffic_bytes_per_pixel:", "source_sha:")))
         if fields.get("source_sha", "").strip() != sha:
-            return None
-        return float(fields["traffic_bytes_per_pixel"]) * pixels
+            return None, f"profiles/{kernel}_1280x720.md predates the current kernel source"
+        return (float(fields["traffic_bytes_per_pixel"]) * pixels,
+                f"profiles/{kernel}_1280x720.md: ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                f"launch, {float(fields['traffic_bytes_per_pixel']):.1f} B/pixel scaled to {pixels} pixels")
     except Exception:
-        return None
+        return None, f"no ncu summary for {kernel}"
 
 
 def cpu_oracle_sample(n_steps: int = 3, nthreads: int = 0, frames=None):
@@ -235,6 +242,9 @@ def run_ours(args):
             mg = None
     else:
         seg = fos.Segmenter(W, H, stream_id=rank)
+    if args.per_frame:
+        seg.set_option(fos.OPT_SEQUENCE, 0)
+    seq = seg.get_option(fos.OPT_SEQUENCE) == 1 and not args.pbas_joint and args.methods == "both"
     stream = torch.cuda.Stream(device=dev)
 
     def step():
@@ -251,7 +261,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     seg.get_timing()
     seg.get_counters()
-    seg.set_timing(0b10011)  # time every GMM, PBAS-classify and fused launch
+    # time every GMM, PBAS-classify, fused and fused-sequence launch
+    seg.set_timing((1 << fos.KERNEL_GMM) | (1 << fos.KERNEL_PBAS_CLASSIFY) | (1 << fos.KERNEL_FUSED) |
+                   (1 << fos.KERNEL_FUSED_SEQUENCE))
 
     clocks = ClockSampler(local)
     barrier()
@@ -279,30 +291,37 @@ def run_ours(args):
     peak, peak_src = _peaks()
     frames_timed = counters["frames"]
     kern = {}
-    for name, (n, tot) in timing.items():
+    for name, (n, tot, nfr) in timing.items():
         if name not in ALGO_BYTES or n == 0:
             continue
+        # algorithmic bytes per launch: dense bytes of each frame it ran, plus
+        # the sparse own/neighbour updates the kernel counted (only one
+        # classify-type kernel runs in the timed region)
         # the joint-channel PBAS kernel reports as pbas_classify: 186 B dense
-        bytes_px = (186.0 if args.pbas_joint and name == "pbas_classify" else ALGO_BYTES[name]) * P
-        if name in ("pbas_classify", "fused_classify"):
-            bytes_px += (SPARSE_OWN * counters["own_updates"] +
-                         SPARSE_NEIGH * counters["neighbour_writes"]) / max(1, n)
+        dense = 186.0 if args.pbas_joint and name == "pbas_classify" else ALGO_BYTES[name]
+        bytes_launch = dense * P * nfr / n
+        if name in ("pbas_classify", "fused_classify", "fused_sequence"):
+            bytes_launch += (SPARSE_OWN * counters["own_updates"] +
+                             SPARSE_NEIGH * counters["neighbour_writes"]) / n
         avg_s = tot / n / 1e3
         kern[name] = {"launches": n, "avg_us": round(avg_s * 1e6, 2),
-                      "share": None, "algo_bytes": bytes_px,
-                      "gbs": bytes_px / avg_s / 1e9}
+                      "frames_per_launch": round(nfr / n, 2),
+                      "us_per_frame": round(tot / nfr * 1e3, 2),
+                      "share": None, "algo_bytes": bytes_launch,
+                      "gbs": bytes_launch / avg_s / 1e9}
     total = sum(v["avg_us"] * v["launches"] for v in kern.values())
     for v in kern.values():
         v["share"] = round(v["avg_us"] * v["launches"] / total, 3)
     dom = max(kern, key=lambda k: kern[k]["avg_us"] * kern[k]["launches"])
     d = kern[dom]
-    tr = _traffic_for(dom, P)
+    tr, tr_src = _traffic_for(dom, int(round(P * d["frames_per_launch"])))  # pixel-frames per launch
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
                 "peak": peak, "unit": "GB/s", "frac": round(d["gbs"] / peak, 3),
-                "peak_source": peak_src, "traffic": tr,
+                "peak_source": peak_src, "traffic": tr, "traffic_source": tr_src,
                 "frac_of_nominal": round(d["gbs"] / NOMINAL_HBM_GBS, 3),
                 "algo_bytes_per_launch": round(d["algo_bytes"]),
-                "kernels": {k: {"avg_us": v["avg_us"], "GBps": round(v["gbs"], 1),
+                "kernels": {k: {"avg_us": v["avg_us"], "frames_per_launch": v["frames_per_launch"],
+                                "us_per_frame": v["us_per_frame"], "GBps": round(v["gbs"], 1),
                                 "share": v["share"]} for k, v in kern.items()}}
 
     if args.kernels_only:
@@ -353,7 +372,9 @@ def run_ours(args):
             nf = min(args.cpu_frames + 1, NFRAMES)
             host = [(_s.to_numpy(h_rgb[f]), _s.to_numpy(h_dep[f])) for f in range(nf)]
             cb = cpu_oracle_sample(args.cpu_frames, frames=host)
-        launches_per_step = 2 + (NFRAMES - 1)  # frame 0: 2 init kernels; then one fused launch per frame
+        # frame 0: 2 init kernels; then one fused launch per frame, or the
+        # gradient-sum pre-pass and one sequence launch for all of them
+        launches_per_step = 2 + (2 if seq else NFRAMES - 1)
         out = {"metric": METRIC, "value": round(value, 1), "unit": "Mpixel-frames/s",
                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
@@ -913,7 +934,8 @@ def run_serve32(args):
                 "queue_ms_p50": round(float(np.percentile(queue, 50)) / 1e3, 3),
                 "ticks": st["ticks"], "frames_per_tick": round(st["frames_done"] / max(1, st["ticks"]), 2),
                 "gpu_busy_s": round(st["busy_us"] / 1e6, 3),
-                "housekeeping_s": round(st["housekeeping_us"] / 1e6, 3)}
+                "housekeeping_s": round(st["housekeeping_us"] / 1e6, 3),
+                "gpu_kernel_s": round(st["kernel_us"] / 1e6, 3)}
 
     paced = run(True)
     saturated = run(False)
@@ -941,6 +963,8 @@ def main():
                     help="run the device-resident steps only (for profiler captures)")
     ap.add_argument("--pbas-joint", action="store_true",
                     help="with --kernels-only: the joint-channel PBAS variant alone (profiler captures)")
+    ap.add_argument("--per-frame", action="store_true",
+                    help="one fused launch per frame instead of one sequence launch (comparison, captures)")
     ap.add_argument("--methods", default="both", choices=["both", "gmm", "pbas"],
                     help="with --kernels-only: one method's kernel alone (profiler captures)")
     ap.add_argument("--workload", default="720p", choices=["720p", "batch16", "softgmm", "serve32", "table"],

@@ -269,11 +269,15 @@ fos_status fos_set_state(fos_ctx* ctx, const void* host_buf, size_t bytes);
                                     outside a frame (before a state export) */
 #define FOS_KERNEL_INIT 3       /* frame-0 initialisation */
 #define FOS_KERNEL_FUSED 4      /* GMM and PBAS of a frame in one launch */
-#define FOS_KERNEL_COUNT 5
+#define FOS_KERNEL_FUSED_SEQUENCE 5 /* GMM and PBAS of several frames in one
+                                       persistent launch (with the gradient-sum
+                                       pre-pass it needs) */
+#define FOS_KERNEL_COUNT 6
 
 typedef struct fos_kernel_timing {
     int64_t launches;
     double total_ms;  /* sum of CUDA-event durations on the launch stream */
+    int64_t frames;   /* frames those launches processed */
 } fos_kernel_timing;
 
 /* Bit k of mask enables CUDA-event timing around every launch of kernel k. */
@@ -297,7 +301,12 @@ fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
                               or 7+3, equal colour/depth size) runs all its frames in one launch,
                               each pixel's mixtures kept in registers; 0: one launch per frame.
                               Same bits either way. */
-#define FOS_OPT_COUNT 7
+#define FOS_OPT_SEQUENCE 7 /* 1 (default): fos_process_frames_device / _host with both methods
+                              fused (FOS_OPT_FUSE, K = 3+3) run the frames after the first of a
+                              call in one persistent launch, in which a tile of frame t+1 starts
+                              as soon as the 3x3 tiles around it have finished frame t; 0: one
+                              launch per frame.  Same bits either way. */
+#define FOS_OPT_COUNT 8
 
 /* Sets a kernel-shape option; FOS_ERR_INVALID_ARG for unknown options or
  * values, FOS_ERR_UNSUPPORTED for shapes not compiled in. */
@@ -435,6 +444,7 @@ typedef struct fos_server_stats_t {
     double busy_us;      /* sum over ticks of launch -> completion */
     double housekeeping_us;  /* time the housekeeping thread spent allocating
                                 and freeing streams' memory */
+    double kernel_us;    /* sum over ticks of the batched kernels' device time */
 } fos_server_stats_t;
 
 /* Server over one device-memory budget (bytes), at most max_streams admitted

@@ -71,6 +71,12 @@ fos_status cuda_fail(fos_ctx* c, const char* what, cudaError_t e)
         if (e_ != cudaSuccess) return cuda_fail(ctx, #call, e_); \
     } while (0)
 
+#define FOS_TRY_ST(call)                      \
+    do {                                      \
+        const fos_status st_ = (call);        \
+        if (st_ != FOS_OK) return st_;        \
+    } while (0)
+
 bool gmm_on(const fos_ctx* c) { return c->prm.methods & FOS_METHOD_GMM; }
 bool pbas_on(const fos_ctx* c) { return c->prm.methods & FOS_METHOD_PBAS; }
 
@@ -145,10 +151,11 @@ struct TimedScope {
     cudaStream_t s;
     TimedLaunch tl{};
     bool on;
-    TimedScope(fos_ctx* c_, int kind, cudaStream_t s_) : c(c_), s(s_), on(false)
+    TimedScope(fos_ctx* c_, int kind, cudaStream_t s_, int64_t frames = 1) : c(c_), s(s_), on(false)
     {
         if (c->timing_mask & (1u << kind)) {
             tl.kind = kind;
+            tl.frames = frames;
             tl.start = pool_event(c);
             tl.stop = pool_event(c);
             if (tl.start && tl.stop) {
@@ -300,6 +307,124 @@ fos_status process_device(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth,
     return FOS_OK;
 }
 
+// --- several frames in one persistent launch ---------------------------------
+
+constexpr size_t kSeqHeader = 256;  // tile counter, error word; scratch sums at byte 64
+
+bool seq_on(const fos_ctx* c) { return ctx_fused(c) && c->opt[FOS_OPT_SEQUENCE] != 0; }
+
+// Buffers of the sequence launch for n frames and `tiles` tiles (grown on
+// demand; an earlier launch using them has been ordered before on the stream
+// or synchronised).
+fos_status ensure_seq(fos_ctx* c, int n, int tiles)
+{
+    if (c->seq && c->seq_frames >= n && c->seq_tiles >= tiles) return FOS_OK;
+    const int nf = std::max(n, c->seq_frames), nt = std::max(tiles, c->seq_tiles);
+    FOS_TRY(c, cudaDeviceSynchronize());  // an earlier launch may still use the old buffers
+    cudaFree(c->seq);
+    c->seq = nullptr;
+    c->seq_frames = c->seq_tiles = 0;
+    const size_t bytes = kSeqHeader + size_t(nf + 1) * 32 + size_t(nt) * 4;
+    FOS_TRY(c, dev_alloc(reinterpret_cast<void**>(&c->seq), bytes));
+    FOS_TRY(c, cudaMemset(c->seq, 0, kSeqHeader));
+    c->seq_frames = nf;
+    c->seq_tiles = nt;
+    return FOS_OK;
+}
+
+// Frames t .. t+n-1 (t >= 1) of a fused context in one persistent launch:
+// frame f's inputs at rgb + f*rgb_stride bytes and depth + f*depth_stride
+// elements, its masks at f*mask_stride bytes.  Same bits as n process_device calls.
+fos_status process_device_seq(fos_ctx* c, int32_t n, const uint8_t* rgb, size_t rgb_stride,
+                              const uint16_t* depth, size_t depth_stride, uint8_t* mg, uint8_t* mp,
+                              size_t mask_stride, cudaStream_t s)
+{
+    const PbasArgs a = pbas_args(c, rgb, depth, mp);
+    const GmmArgs g = gmm_args(c, rgb, depth, mg);
+    int tx = 0, ty = 0;
+    fused_sequence_tiles(a, tx, ty);
+    FOS_TRY_ST(ensure_seq(c, n, tx * ty));
+    SeqArgs q{};
+    q.n = n;
+    q.tiles_x = tx;
+    q.tiles_y = ty;
+    q.rgb_stride = int64_t(rgb_stride);
+    q.depth_stride = int64_t(depth_stride);
+    q.mask_stride = int64_t(mask_stride);
+    q.req_base = c->req;
+    q.prev_base = c->prev;
+    q.claim = reinterpret_cast<unsigned int*>(c->seq);
+    q.err = reinterpret_cast<int*>(c->seq + 4);
+    q.gscratch = reinterpret_cast<unsigned long long*>(c->seq + 64);
+    unsigned long long* gprev = reinterpret_cast<unsigned long long*>(c->seq + kSeqHeader);
+    q.gprev = gprev;
+    q.done = reinterpret_cast<int*>(c->seq + kSeqHeader + size_t(c->seq_frames + 1) * 32);
+    const int64_t t0 = c->t;
+    unsigned long long* last = c->aux + ((t0 + n - 1) % 3) * 4;   // read by frame t0+n
+    unsigned long long* next = c->aux + ((t0 + n) % 3) * 4;       // accumulated by frame t0+n
+    {
+        TimedScope ts(c, FOS_KERNEL_FUSED_SEQUENCE, s, n);
+        // gprev[0]: sums of frame t0-1 (from the last launch); gprev[1 + f]:
+        // sums of frame t0+f, f = 0 .. n-1, by the pre-pass
+        FOS_TRY(c, cudaMemsetAsync(c->seq, 0, 8, s));  // tile counter, error word
+        FOS_TRY(c, cudaMemsetAsync(q.done, 0, size_t(tx) * ty * 4, s));
+        FOS_TRY(c, cudaMemcpyAsync(gprev, a.gsum_prev, 32, cudaMemcpyDeviceToDevice, s));
+        FOS_TRY(c, cudaMemsetAsync(gprev + 4, 0, size_t(n) * 32, s));
+        fos_status st = launch_result(c, launch_grad_sums(a, q, gprev + 4, s), "grad_sums");
+        if (st != FOS_OK) return st;
+        st = launch_result(c, launch_fused_sequence(a, g, q, s), "fused_sequence");
+        if (st != FOS_OK) return st;
+    }
+    // where a per-frame launch of frame t0+n expects the gradient sums
+    FOS_TRY(c, cudaMemcpyAsync(last, gprev + 4 * size_t(n), 32, cudaMemcpyDeviceToDevice, s));
+    FOS_TRY(c, cudaMemsetAsync(next, 0, 32, s));
+    c->pending = true;
+    c->t += n;
+    c->frames_since_counters += uint64_t(n);
+    return FOS_OK;
+}
+
+// n frames through the per-frame path, or (fused, option on, n >= 2) the
+// first through it when the context is at frame 0 and the rest in one
+// sequence launch.
+fos_status process_device_frames(fos_ctx* c, int32_t n, const uint8_t* rgb, size_t rgb_stride,
+                                 const uint16_t* depth, size_t depth_stride, uint8_t* mg, uint8_t* mp,
+                                 size_t mask_stride, cudaStream_t s)
+{
+    int32_t f = 0;
+    if (seq_on(c) && n >= 2) {
+        if (!rgb || !depth || !mg || !mp)
+            return fail(c, FOS_ERR_INVALID_ARG, "rgb, depth and both masks must be non-NULL");
+        if (c->t == 0) {
+            FOS_TRY_ST(process_device(c, rgb, depth, mg, mp, s));
+            f = 1;
+        }
+        if (n - f >= 2)
+            return process_device_seq(c, n - f, rgb + size_t(f) * rgb_stride, rgb_stride,
+                                      depth + size_t(f) * depth_stride, depth_stride, mg + size_t(f) * mask_stride,
+                                      mp + size_t(f) * mask_stride, mask_stride, s);
+    }
+    for (; f < n; ++f) {
+        FOS_TRY_ST(process_device(c, rgb + size_t(f) * rgb_stride, depth + size_t(f) * depth_stride,
+                                  mg ? mg + size_t(f) * mask_stride : nullptr,
+                                  mp ? mp + size_t(f) * mask_stride : nullptr, s));
+    }
+    return FOS_OK;
+}
+
+// Error word of the last sequence launch (after a synchronisation).
+fos_status seq_check(fos_ctx* c)
+{
+    if (!c->seq) return FOS_OK;
+    int e = 0;
+    FOS_TRY(c, cudaMemcpy(&e, c->seq + 4, 4, cudaMemcpyDeviceToHost));
+    if (e) {
+        FOS_TRY(c, cudaMemset(c->seq + 4, 0, 4));
+        return fail(c, FOS_ERR_TIMEOUT, "fused_sequence: a tile's wait for its neighbours gave up");
+    }
+    return FOS_OK;
+}
+
 // Staging for `frames` host frames per slot (grown on demand; callers of the
 // host-pointer API have synchronised every earlier use before this runs).
 constexpr int kHostChunk = 8;  // host frames per staging slot
@@ -358,7 +483,7 @@ size_t pbas_bytes(const fos_ctx* c)
 void free_all(fos_ctx* c)
 {
     cudaFree(c->gmm); cudaFree(c->samp); cudaFree(c->Dq); cudaFree(c->R); cudaFree(c->T);
-    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux);
+    cudaFree(c->S); cudaFree(c->req); cudaFree(c->prev); cudaFree(c->aux); cudaFree(c->seq);
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->h_rgb[b]); cudaFree(c->h_depth[b]); cudaFree(c->h_mg[b]); cudaFree(c->h_mp[b]);
         if (c->ev_in[b]) cudaEventDestroy(c->ev_in[b]);
@@ -593,14 +718,8 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
         ctx->frames_since_counters += uint64_t(n_frames);
         return FOS_OK;
     }
-    for (int32_t f = 0; f < n_frames; ++f) {
-        fos_status st = process_device(ctx, d_rgb + f * P * 3, d_depth + f * Pd,
-                                       d_mask_gmm ? d_mask_gmm + f * P : nullptr,
-                                       d_mask_pbas ? d_mask_pbas + f * P : nullptr,
-                                       static_cast<cudaStream_t>(stream));
-        if (st != FOS_OK) return st;
-    }
-    return FOS_OK;
+    return process_device_frames(ctx, n_frames, d_rgb, size_t(P) * 3, d_depth, size_t(Pd), d_mask_gmm, d_mask_pbas,
+                                 size_t(P), static_cast<cudaStream_t>(stream));
 }
 
 fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t* rgb,
@@ -635,12 +754,9 @@ fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_in[b], ctx->copy_stream));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_in[b], 0));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_done[b], 0));
-        for (size_t i = 0; i < m; ++i) {
-            st = process_device(ctx, ctx->h_rgb[b] + i * rp, reinterpret_cast<const uint16_t*>(
-                                    reinterpret_cast<const uint8_t*>(ctx->h_depth[b]) + i * dp),
-                                ctx->h_mg[b] + i * mp, ctx->h_mp[b] + i * mp, ctx->stream);
-            if (st != FOS_OK) return st;
-        }
+        st = process_device_frames(ctx, int32_t(m), ctx->h_rgb[b], rp, ctx->h_depth[b], dp / 2, ctx->h_mg[b],
+                                   ctx->h_mp[b], mp, ctx->stream);
+        if (st != FOS_OK) return st;
         FOS_TRY(ctx, cudaEventRecord(ctx->ev_k[b], ctx->stream));
         FOS_TRY(ctx, cudaStreamWaitEvent(ctx->out_stream, ctx->ev_k[b], 0));
         if (gmm_on(ctx))
@@ -653,7 +769,7 @@ fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t
     }
     FOS_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     FOS_TRY(ctx, cudaStreamSynchronize(ctx->out_stream));
-    return FOS_OK;
+    return seq_check(ctx);
 }
 
 fos_status fos_process_frame2(fos_ctx* ctx, const uint8_t* rgb, const uint16_t* depth,
@@ -791,13 +907,14 @@ fos_status fos_set_timing(fos_ctx* ctx, uint32_t kernel_mask)
 fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
 {
     if (!ctx || !out) return FOS_ERR_INVALID_ARG;
-    for (int k = 0; k < FOS_KERNEL_COUNT; ++k) { out[k].launches = 0; out[k].total_ms = 0.0; }
+    for (int k = 0; k < FOS_KERNEL_COUNT; ++k) { out[k].launches = 0; out[k].total_ms = 0.0; out[k].frames = 0; }
     for (const TimedLaunch& tl : ctx->timed) {
         FOS_TRY(ctx, cudaEventSynchronize(tl.stop));
         float ms = 0.f;
         FOS_TRY(ctx, cudaEventElapsedTime(&ms, tl.start, tl.stop));
         out[tl.kind].launches += 1;
         out[tl.kind].total_ms += ms;
+        out[tl.kind].frames += tl.frames;
     }
     ctx->timed.clear();
     ctx->ev_used = 0;
@@ -815,6 +932,7 @@ fos_status fos_set_option(fos_ctx* ctx, int32_t option, int32_t value)
     case FOS_OPT_PBAS_TY: ok = value == 2 || value == 4 || value == 8; break;
     case FOS_OPT_FUSE: ok = value == 0 || value == 1; break;
     case FOS_OPT_TEMPORAL: ok = value == 0 || value == 1; break;
+    case FOS_OPT_SEQUENCE: ok = value == 0 || value == 1; break;
     default: return fail(ctx, FOS_ERR_INVALID_ARG, "unknown option");
     }
     if (!ok) return fail(ctx, FOS_ERR_INVALID_ARG, "option value not supported");
@@ -837,6 +955,7 @@ fos_status fos_get_counters(fos_ctx* ctx, uint64_t out[4])
 {
     if (!ctx || !out) return FOS_ERR_INVALID_ARG;
     FOS_TRY(ctx, cudaDeviceSynchronize());
+    FOS_TRY_ST(seq_check(ctx));
     unsigned long long c[4];
     FOS_TRY(ctx, cudaMemcpy(c, ctx->aux + 12, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = ctx->frames_since_counters;

@@ -10,6 +10,7 @@
 namespace fos {
 struct TimedLaunch {
     int kind;
+    int64_t frames;  // frames the launch processed
     cudaEvent_t start, stop;
 };
 }  // namespace fos
@@ -36,8 +37,13 @@ struct fos_ctx {
     uint32_t* req = nullptr;            // [2][pplane] requests of even / odd frames
     uint64_t* prev = nullptr;           // [pplane]
     bool pending = false;               // requests of the last frame not yet applied
-    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1, 1};  // kernel shapes (fos_set_option)
+    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1, 1, 1};  // kernel shapes (fos_set_option)
     unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
+    // several frames in one launch (grown on demand): a 256-byte header (tile
+    // counter, error word, 8 scratch sums), gradient sums [frames + 1][4],
+    // tile completion words [tiles]
+    uint8_t* seq = nullptr;
+    int seq_frames = 0, seq_tiles = 0;
     // device staging for host frames: two slots of stage_frames frames each,
     // frame pitches rounded up to 256 bytes
     int stage_frames = 0;

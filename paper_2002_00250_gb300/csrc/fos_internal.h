@@ -207,6 +207,37 @@ __host__ __device__ inline int64_t samp_extent(const PbasArgs& a) { return 4 * a
 __host__ __device__ inline int64_t rts_extent(const PbasArgs& a) { return 4 * a.plane; }
 __host__ __device__ inline int64_t depth_extent(const PbasArgs& a) { return int64_t(a.Wd) * a.Hd; }
 
+// Frames t0 .. t0+n-1 (t0 = a0.t >= 1) of one fused (3+3 GMM + PBAS) context
+// in one persistent launch.  Tiles are claimed in frame-major order from a
+// counter; a tile of frame t0+i (i >= 1) starts once its 3x3 neighbourhood of
+// tiles has finished frame t0+i-1 (per-tile completion words), so the next
+// frame's tiles fill the SMs that the end of the previous frame leaves idle.
+// Every cross-tile read of a tile is of the input (read-only), of the request
+// planes of frame t-1 or, with propagation, of the value planes of frame t-1
+// (both double-buffered by frame parity): the 3x3 dependency covers them.
+// The gradient sums that weight frame t0+i come from a pre-pass (gprev).
+struct SeqArgs {
+    int n;                             // frames in the launch
+    int tiles_x, tiles_y;              // tile grid of one frame
+    int64_t rgb_stride;                // bytes between frames
+    int64_t depth_stride;              // elements between frames
+    int64_t mask_stride;               // bytes between frames (both masks)
+    uint32_t* req_base;                // [2][plane] request planes by frame parity
+    uint64_t* prev_base;               // propagation: [2][plane] value planes by frame parity
+    const unsigned long long* gprev;   // [n][4] gradient sums of frame t0+i-1, weighting frame t0+i
+    unsigned long long* gscratch;      // [8] sink for the tiles' own gradient sums
+    unsigned int* claim;               // tile counter, zero on entry
+    int* done;                         // [tiles] frames of this launch each tile has finished, zero on entry
+    int* err;                          // set to 1 if a bounded wait gave up
+};
+LaunchResult launch_fused_sequence(const PbasArgs& a0, const GmmArgs& g0, const SeqArgs& q, cudaStream_t s);
+// The tile grid launch_fused_sequence expects for this context's shape options.
+void fused_sequence_tiles(const PbasArgs& a, int& tiles_x, int& tiles_y);
+// Gradient sums (R, G, B, depth; the Sobel magnitudes the classify pass
+// computes) of the n frames at a0's input pointers with q's strides into
+// out[n][4] (zero on entry).
+LaunchResult launch_grad_sums(const PbasArgs& a0, const SeqArgs& q, unsigned long long* out, cudaStream_t s);
+
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);

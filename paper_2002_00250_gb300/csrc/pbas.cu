@@ -22,6 +22,8 @@
 // Arithmetic is IEEE single precision with every operation rounded once
 // (explicit _rn intrinsics, no contraction), so results are bit-exact against
 // a plain C implementation of the same steps.
+#include <algorithm>
+
 #include "pbas_dev.cuh"
 
 namespace fos {
@@ -320,6 +322,123 @@ fused_classify_kernel(const PbasArgs a, const GmmArgs g)
     classify_tile<NT, PX, TY, 3, 3>(a, &g, blockIdx.x * Geo<PX, TY>::TW, blockIdx.y * TY, S, true);
 }
 
+// --- several frames in one persistent launch ---------------------------------
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Polls before a wait gives up (each poll sleeps 64 ns and reads L2: well
+// over a second in all).  The wait cannot run out: a tile waits only for
+// tiles claimed before it, whose blocks are running.
+constexpr uint32_t kSeqSpinLimit = 1u << 21;
+
+// Waits until tile (tx, ty) has finished `need` frames of the launch (no-op
+// outside the tile grid); on giving up, sets the error word and returns.
+__device__ __forceinline__ void seq_wait(const SeqArgs& q, int tx, int ty, int need)
+{
+    if (tx < 0 || ty < 0 || tx >= q.tiles_x || ty >= q.tiles_y) return;
+    const int* f = q.done + ty * q.tiles_x + tx;
+    for (uint32_t spin = 0; ld_acquire_gpu(f) < need; ++spin) {
+        if (spin >= kSeqSpinLimit || ((spin & 1023u) == 1023u && *(volatile int*)q.err)) {
+            atomicExch(q.err, 1);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
+// The arguments of frame t0+i (inputs, masks, frame index, parity planes).
+template <int PX>
+__device__ __forceinline__ void seq_frame_args(PbasArgs& a, GmmArgs& g, const SeqArgs& q, int i)
+{
+    const int64_t f = i;
+    a.rgb += f * q.rgb_stride;
+    a.depth += f * q.depth_stride;
+    a.mask += f * q.mask_stride;
+    a.t += uint32_t(i);
+    const int64_t pl = a.plane;
+    a.req_cur = q.req_base + int64_t(a.t & 1u) * pl;
+    a.req_prev = q.req_base + int64_t((a.t + 1u) & 1u) * pl;
+    if (a.propagate) {
+        a.prev = q.prev_base + int64_t(a.t & 1u) * pl;
+        a.prev_src = q.prev_base + int64_t((a.t + 1u) & 1u) * pl;
+    }
+    a.gsum_prev = const_cast<unsigned long long*>(q.gprev) + 4 * f;
+    a.gsum_cur = q.gscratch;
+    a.gsum_next = q.gscratch + 4;
+    if (i > 0) a.apply = 1;
+    a.mask_vec = (reinterpret_cast<uintptr_t>(a.mask) % uintptr_t(PX)) == 0 ? 1 : 0;
+    g.rgb = a.rgb;
+    g.depth = a.depth;
+    g.mask += f * q.mask_stride;
+}
+
+// GMM (3+3) and PBAS of q.n frames; one block per SM slot, tiles claimed in
+// frame-major order.  Bits equal to q.n launches of fused_classify_kernel.
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
+fused_sequence_kernel(const PbasArgs a0, const GmmArgs g0, const SeqArgs q)
+{
+    using G = Geo<PX, TY>;
+    __shared__ ClassifySmem<PX, TY> S;
+    __shared__ int s_it;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const int ntiles = q.tiles_x * q.tiles_y;
+    const int total = ntiles * q.n;
+    for (;;) {
+        // s_it is rewritten only after the tile below has passed its own
+        // block barriers, so every thread has read it by then
+        if (tid == 0) s_it = int(atomicAdd(q.claim, 1u));
+        __syncthreads();
+        const int it = s_it;
+        if (it >= total) break;
+        const int i = it / ntiles, j = it - i * ntiles;
+        const int tx = j % q.tiles_x, ty = j / q.tiles_x;
+        // the 3x3 neighbourhood of frame t0+i-1: nine threads wait, one tile each
+        if (i > 0 && tid < 9) seq_wait(q, tx + tid % 3 - 1, ty + tid / 3 - 1, i);
+        __syncthreads();
+        PbasArgs a = a0;
+        GmmArgs g = g0;
+        seq_frame_args<PX>(a, g, q, i);
+        classify_tile<NT, PX, TY, 3, 3>(a, &g, tx * G::TW, ty * TY, S, true);
+        // all of the tile's writes are ordered before the completion word
+        __syncthreads();
+        if (tid == 0) st_release_gpu(q.done + j, i + 1);
+    }
+}
+
+// Gradient sums of frame blockIdx.z (the Sobel magnitudes classify_tile adds
+// to gsum_cur), one tile per block.
+template <int TY>
+__global__ void __launch_bounds__(32 * TY) grad_sums_kernel(const PbasArgs a0, const SeqArgs q,
+                                                            unsigned long long* out)
+{
+    using G = Geo<1, TY>;
+    __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    PbasArgs a = a0;
+    a.rgb += int64_t(blockIdx.z) * q.rgb_stride;
+    a.depth += int64_t(blockIdx.z) * q.depth_stride;
+    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
+    stage_input<1, TY>(a, x0, y0, sm);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    uint32_t v[4] = {0, 0, 0, 0};
+    if (x < a.W && y < a.H) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = sobel(sm + c * G::CH, G::SWP, threadIdx.y + 1, threadIdx.x + 1, G::CH, a.oob);
+    }
+    block_add<TY, 4>(v, [&](int c) { return out + 4 * int64_t(blockIdx.z) + c; });
+}
+
 // Applies the pending neighbour requests of the last frame to the samples
 // without classifying (so that an exported state includes them).
 template <int NT, int TY>
@@ -483,6 +602,75 @@ bool fused_shape(const PbasArgs& a, const GmmArgs& g, cudaStream_t s, int px, in
 
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s) { return init_launch(a, s); }
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s) { return classify_launch(a, s); }
+
+template <int NT, int PX, int TY>
+LaunchResult sequence_go(const PbasArgs& a0, const GmmArgs& g0, const SeqArgs& q, cudaStream_t s)
+{
+    auto k = fused_sequence_kernel<NT, PX, TY>;
+    // one block per SM slot (cached per shape); a cooperative launch, so that
+    // every block is resident while others wait for it
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * TY, 0) != cudaSuccess)
+            return kLaunchCudaError;
+    }
+    const int64_t total = int64_t(q.tiles_x) * q.tiles_y * q.n;
+    const int grid = int(std::min<int64_t>(total, int64_t(per_sm) * sms));
+    if (grid < 1) return kLaunchOk;
+    PbasArgs a = a0;
+    GmmArgs g = g0;
+    SeqArgs qq = q;
+    void* args[] = {&a, &g, &qq};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(unsigned(grid)), dim3(32, TY), args, 0, s) ==
+                   cudaSuccess
+               ? kLaunchOk
+               : kLaunchCudaError;
+}
+
+template <int NT>
+LaunchResult sequence_shape(const PbasArgs& a0, const GmmArgs& g0, const SeqArgs& q, cudaStream_t s, int px, int ty)
+{
+    if (px == 2 && ty == 8) return sequence_go<NT, 2, 8>(a0, g0, q, s);
+    if (px == 2 && ty == 4) return sequence_go<NT, 2, 4>(a0, g0, q, s);
+    if (px == 1) return sequence_go<NT, 1, 8>(a0, g0, q, s);
+    return kLaunchUnsupported;
+}
+
+// Tile shape of the sequence launch for a context's options: 2 px x 8 or 4
+// rows when the width allows; otherwise 1 px x 8 rows.
+static void sequence_tile(const PbasArgs& a, int& px, int& ty)
+{
+    px = (a.px == 2 && a.W % 2 == 0) ? 2 : 1;
+    ty = px == 2 && a.ty == 4 ? 4 : 8;
+}
+
+void fused_sequence_tiles(const PbasArgs& a, int& tiles_x, int& tiles_y)
+{
+    int px, ty;
+    sequence_tile(a, px, ty);
+    tiles_x = (a.W + 32 * px - 1) / (32 * px);
+    tiles_y = (a.H + ty - 1) / ty;
+}
+
+LaunchResult launch_fused_sequence(const PbasArgs& a0, const GmmArgs& g0, const SeqArgs& q, cudaStream_t s)
+{
+    if (a0.P == 0 || q.n == 0) return kLaunchOk;
+    int px, ty;
+    sequence_tile(a0, px, ty);
+    if (q.tiles_x != (a0.W + 32 * px - 1) / (32 * px) || q.tiles_y != (a0.H + ty - 1) / ty) return kLaunchUnsupported;
+    return a0.N == 20 ? sequence_shape<20>(a0, g0, q, s, px, ty) : sequence_shape<0>(a0, g0, q, s, px, ty);
+}
+
+LaunchResult launch_grad_sums(const PbasArgs& a0, const SeqArgs& q, unsigned long long* out, cudaStream_t s)
+{
+    if (a0.P == 0 || q.n == 0) return kLaunchOk;
+    const dim3 grid(unsigned((a0.W + 31) / 32), unsigned((a0.H + 7) / 8), unsigned(q.n));
+    grad_sums_kernel<8><<<grid, dim3(32, 8), 0, s>>>(a0, q, out);
+    return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+}
 
 LaunchResult launch_fused_classify(const PbasArgs& a, const GmmArgs& g, cudaStream_t s)
 {

@@ -121,6 +121,7 @@ struct TickItem {
 struct Tick {
     std::vector<TickItem> items;
     cudaEvent_t in = nullptr;    // inputs on the device (copy-in stream)
+    cudaEvent_t k0 = nullptr;    // kernels start (compute stream, after the input wait)
     cudaEvent_t k = nullptr;     // kernels done (compute stream)
     cudaEvent_t done = nullptr;  // masks in host memory (copy-out stream)
     double t_launch = 0.0;
@@ -152,7 +153,7 @@ struct fos_server {
     bool stop = false;
     std::string err;
     int64_t ticks = 0, frames_done = 0;
-    double busy_us = 0.0, house_us = 0.0;
+    double busy_us = 0.0, house_us = 0.0, kernel_us = 0.0;
     std::vector<cudaEvent_t> events;  // free tick events (created once, reused)
 };
 
@@ -323,7 +324,9 @@ void publish(fos_server* s, Tick& t)
         st->inflight -= 1;
         s->frames_done += 1;
     }
-    for (cudaEvent_t* e : {&t.in, &t.k, &t.done})
+    float ms = 0.f;
+    if (t.k0 && t.k && cudaEventElapsedTime(&ms, t.k0, t.k) == cudaSuccess) s->kernel_us += 1e3 * double(ms);
+    for (cudaEvent_t* e : {&t.in, &t.k0, &t.k, &t.done})
         if (*e) {
             s->events.push_back(*e);
             *e = nullptr;
@@ -340,7 +343,7 @@ cudaError_t take_event(fos_server* s, cudaEvent_t* e)
             return cudaSuccess;
         }
     }
-    return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    return cudaEventCreate(e);  // timing enabled: the kernels of a tick are timed
 }
 
 void worker_main(fos_server* s)
@@ -409,10 +412,12 @@ void worker_main(fos_server* s)
             // its mask copies the next tick's (at most kTicks ticks in flight,
             // and a stream's frames in them use different buffers)
             if (e == cudaSuccess) e = take_event(s, &t.in);
+            if (e == cudaSuccess) e = take_event(s, &t.k0);
             if (e == cudaSuccess) e = take_event(s, &t.k);
             if (e == cudaSuccess) e = take_event(s, &t.done);
             if (e == cudaSuccess) e = cudaEventRecord(t.in, s->cin);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s->cs, t.in, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(t.k0, s->cs);
             t.t_launch = now_us();
             fos_status bst = FOS_OK;
             if (e == cudaSuccess)
@@ -444,7 +449,7 @@ void worker_main(fos_server* s)
                     s->streams[it.stream]->inflight -= 1;
                     if (it.f.host_in) s->streams[it.stream]->free_in.push_back(it.f.host_in);
                 }
-                for (cudaEvent_t ev : {t.in, t.k, t.done})
+                for (cudaEvent_t ev : {t.in, t.k0, t.k, t.done})
                     if (ev) s->events.push_back(ev);
                 s->hcv.notify_all();
                 break;
@@ -730,6 +735,7 @@ fos_status fos_server_stats(fos_server* s, fos_server_stats_t* out)
     out->streams_waiting = waiting;
     out->busy_us = s->busy_us;
     out->housekeeping_us = s->house_us;
+    out->kernel_us = s->kernel_us;
     return s->stop && !s->err.empty() ? FOS_ERR_CUDA : FOS_OK;
 }
 

@@ -20,8 +20,9 @@ BOUNDS_LIB_PATH = os.path.join(_PKG, "libfos_bounds.so")  # range-checked build 
 
 METHOD_GMM = 1
 METHOD_PBAS = 2
-KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_FLUSH, KERNEL_INIT, KERNEL_FUSED = 0, 1, 2, 3, 4
-KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_flush", "init", "fused_classify")
+KERNEL_GMM, KERNEL_PBAS_CLASSIFY, KERNEL_PBAS_FLUSH, KERNEL_INIT, KERNEL_FUSED, KERNEL_FUSED_SEQUENCE = \
+    0, 1, 2, 3, 4, 5
+KERNEL_NAMES = ("gmm_step", "pbas_classify", "pbas_flush", "init", "fused_classify", "fused_sequence")
 STATUS = {0: "FOS_OK", 1: "FOS_ERR_INVALID_ARG", 2: "FOS_ERR_CUDA", 3: "FOS_ERR_OOM",
           4: "FOS_ERR_TIMEOUT", 5: "FOS_ERR_BUDGET", 6: "FOS_ERR_STATE", 7: "FOS_ERR_UNSUPPORTED",
           8: "FOS_ERR_BUSY"}
@@ -91,11 +92,11 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("ticks", ctypes.c_int64), ("frames_done", ctypes.c_int64),
                 ("device_bytes_used", ctypes.c_size_t), ("streams_active", ctypes.c_int32),
                 ("streams_waiting", ctypes.c_int32), ("busy_us", ctypes.c_double),
-                ("housekeeping_us", ctypes.c_double)]
+                ("housekeeping_us", ctypes.c_double), ("kernel_us", ctypes.c_double)]
 
 
 class KernelTiming(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double), ("frames", ctypes.c_int64)]
 
 
 # Every exported function and its ctypes signature (checked against the header
@@ -160,7 +161,7 @@ SIGNATURES = {
     "fos_softgmm_forward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "fos_softgmm_backward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
 }
-OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY, OPT_FUSE, OPT_TEMPORAL = 1, 2, 3, 4, 5, 6
+OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY, OPT_FUSE, OPT_TEMPORAL, OPT_SEQUENCE = 1, 2, 3, 4, 5, 6, 7
 
 _lib = None
 
@@ -359,7 +360,8 @@ class Segmenter:
     def get_timing(self) -> dict:
         arr = (KernelTiming * len(KERNEL_NAMES))()
         self._check(self.lib.fos_get_timing(self.h, arr))
-        return {KERNEL_NAMES[k]: (arr[k].launches, arr[k].total_ms) for k in range(len(KERNEL_NAMES))}
+        """{kernel: (launches, total ms, frames processed)}."""
+        return {KERNEL_NAMES[k]: (arr[k].launches, arr[k].total_ms, arr[k].frames) for k in range(len(KERNEL_NAMES))}
 
     def set_option(self, option: int, value: int) -> None:
         self._check(self.lib.fos_set_option(self.h, option, value))
