@@ -108,6 +108,37 @@ __global__ void __launch_bounds__(kGmmBatchThreads) gmm_batch_kernel(const __gri
     gmm_pixels<KR, KD, PX>(T.e[lo].a, (int64_t(it - T.e[lo].block_off) * blockDim.x + threadIdx.x) * PX);
 }
 
+// Two pixels per thread through gmm_pair (frames >= 1, depth of the colour
+// frame's size): the two colour mixtures, then the two depth mixtures, each
+// parameter plane moved with one 8-byte access; a lower register peak than
+// gmm_pixels (more warps resident to hide the plane loads).  Same arithmetic
+// (mix_step) and bits.
+template <int KR, int KD, int MINB>
+__global__ void __launch_bounds__(256, MINB) gmm_pair_kernel(const GmmArgs a)
+{
+    const int64_t p = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 2;
+    if (p >= a.P) return;
+    if (p + 2 > a.P) {  // odd pixel count: the last pixel alone
+        gmm_pixels<KR, KD, 1>(a, p);
+        return;
+    }
+    uint32_t r[2], g[2], b[2], d8[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        r[i] = at(a.rgb, 3 * (p + i), 3 * a.P, 47, a.oob);
+        g[i] = at(a.rgb, 3 * (p + i) + 1, 3 * a.P, 47, a.oob);
+        b[i] = at(a.rgb, 3 * (p + i) + 2, 3 * a.P, 47, a.oob);
+        d8[i] = depth_to_u8(at(a.depth, p + i, a.P, 46, a.oob), a.depth_fs);
+    }
+    const uint32_t m = gmm_pair<KR, KD>(a, p, r, g, b, d8);
+    if ((reinterpret_cast<uintptr_t>(a.mask) & 1u) == 0) {
+        vat<uint16_t>(a.mask, p, 2, a.P, 48, a.oob) = uint16_t(m);
+    } else {
+        at(a.mask, p, a.P, 48, a.oob) = uint8_t(m);
+        at(a.mask, p + 1, a.P, 48, a.oob) = uint8_t(m >> 8);
+    }
+}
+
 template <int KR, int KD, int PX>
 LaunchResult launch_k(const GmmArgs& a, cudaStream_t s)
 {
@@ -127,7 +158,12 @@ LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s)
     if (a.P == 0) return kLaunchOk;
     if (Kr == 3 && Kd == 3) {
         if (a.px == 1) return launch_k<3, 3, 1>(a, s);
-        if (a.px == 2) return launch_k<3, 3, 2>(a, s);
+        if (a.px == 2) {
+            if (a.init || a.Wd != a.W || a.Hd != a.H) return launch_k<3, 3, 2>(a, s);
+            const int64_t blocks = ((a.P + 1) / 2 + 255) / 256;
+            gmm_pair_kernel<3, 3, 2><<<dim3(unsigned(blocks)), 256, 0, s>>>(a);
+            return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+        }
         return launch_k<3, 3, 4>(a, s);
     }
 #define FOS_CASE(R, D, PX) \

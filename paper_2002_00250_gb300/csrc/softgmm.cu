@@ -75,7 +75,7 @@ struct SFwd {
     R e[K][C], s[K], d[K], m[K], Pp[K + 1], r[K], q, w1[K], rho[K];
     bool clamp[K], unused[K];
     R mu1[K][C], v1[K], w2[K], v2[K], sum, w3[K];
-    int perm[K];
+    int rank[K];  // output position of component k after the re-rank
 };
 
 template <typename R>
@@ -201,27 +201,37 @@ __device__ __forceinline__ void mix_fwd(const SMix<K, C, R>& in, const R (&x)[C]
     for (int k = 0; k < K; ++k) {
         f.w3[k] = f.w2[k] / f.sum;
         key[k] = f.w3[k] / rsqrt_(f.v2[k]);
-        f.perm[k] = k;
     }
-    // stable descending sort of (key, index): adjacent swaps on strictly greater
+    // stable descending order of the keys: component k goes to position
+    // #{j < k: key_j >= key_k} + #{j > k: key_j > key_k}.  Ranks come from
+    // comparisons and the outputs from predicated selects, so that no array
+    // is indexed by a run-time value (which would move the state to local memory).
 #pragma unroll
-    for (int pass = 0; pass < K - 1; ++pass)
+    for (int k = 0; k < K; ++k) {
+        int r = 0;
 #pragma unroll
-        for (int j = 0; j < K - 1 - pass; ++j)
-            if (key[j + 1] > key[j]) {
-                const R tk = key[j]; key[j] = key[j + 1]; key[j + 1] = tk;
-                const int ti = f.perm[j]; f.perm[j] = f.perm[j + 1]; f.perm[j + 1] = ti;
-            }
+        for (int j = 0; j < K; ++j)
+            if (j != k) r += (j < k ? key[j] >= key[k] : key[j] > key[k]) ? 1 : 0;
+        f.rank[k] = r;
+    }
 #pragma unroll
-    for (int i = 0; i < K; ++i)
+    for (int i = 0; i < K; ++i) {
+        R w = f.w3[0], v = f.v2[0], mu[C];
 #pragma unroll
-        for (int kk = 0; kk < K; ++kk)
-            if (f.perm[i] == kk) {
-                out.w[i] = f.w3[kk];
-                out.v[i] = f.v2[kk];
+        for (int c = 0; c < C; ++c) mu[c] = mu2[0][c];
 #pragma unroll
-                for (int c = 0; c < C; ++c) out.mu[i][c] = mu2[kk][c];
-            }
+        for (int kk = 1; kk < K; ++kk) {
+            const bool here = f.rank[kk] == i;
+            w = here ? f.w3[kk] : w;
+            v = here ? f.v2[kk] : v;
+#pragma unroll
+            for (int c = 0; c < C; ++c) mu[c] = here ? mu2[kk][c] : mu[c];
+        }
+        out.w[i] = w;
+        out.v[i] = v;
+#pragma unroll
+        for (int c = 0; c < C; ++c) out.mu[i][c] = mu[c];
+    }
 }
 
 // Adjoint of one model step.  gout: adjoint of the (ranked) output;
@@ -235,15 +245,23 @@ __device__ __forceinline__ void mix_bwd(const SMix<K, C, R>& in, const R (&x)[C]
 {
     R gw3[K], gmu2[K][C], gv2[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i)
+    for (int k = 0; k < K; ++k) {
+        R w = gout.w[0], v = gout.v[0], mu[C];
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-            if (f.perm[i] == k) {
-                gw3[k] = gout.w[i];
-                gv2[k] = gout.v[i];
+        for (int c = 0; c < C; ++c) mu[c] = gout.mu[0][c];
 #pragma unroll
-                for (int c = 0; c < C; ++c) gmu2[k][c] = gout.mu[i][c];
-            }
+        for (int i = 1; i < K; ++i) {
+            const bool here = f.rank[k] == i;
+            w = here ? gout.w[i] : w;
+            v = here ? gout.v[i] : v;
+#pragma unroll
+            for (int c = 0; c < C; ++c) mu[c] = here ? gout.mu[i][c] : mu[c];
+        }
+        gw3[k] = w;
+        gv2[k] = v;
+#pragma unroll
+        for (int c = 0; c < C; ++c) gmu2[k][c] = mu[c];
+    }
     // w3 = w2 / sum
     R dot = R(0);
 #pragma unroll
