@@ -395,6 +395,30 @@ fos_status fos_batch_process_device(fos_batch* b, int32_t n, const int32_t* slot
                                     const uint8_t* const* d_rgb, const uint16_t* const* d_depth,
                                     uint8_t* const* d_mask_gmm, uint8_t* const* d_mask_pbas,
                                     void* stream);
+/*
+ * Several frames of n distinct streams: stream slots[i] processes n_frames[i]
+ * (>= 0) consecutive device frames, frame k at d_rgb[i] + k*W*H*3,
+ * d_depth[i] + k*Wd*Hd, and writes its masks at d_mask_*[i] + k*W*H.  With
+ * both methods and the 3+3 GMM (the fused model): the first frame of streams
+ * at frame 0 runs as one batched step, then all remaining frames of all
+ * streams run in ONE persistent launch (per 48 streams) in which a tile of
+ * frame t+1 of a stream starts as soon as that stream's 3x3 tiles around it
+ * have finished frame t (a bounded wait; the gradient-weight sums of every
+ * frame come from a pre-pass over the inputs).  Otherwise one batched step
+ * per frame slot.  Per-stream results are bit-identical to processing each
+ * stream alone.  Asynchronous on `stream`; the arrays are read before the
+ * call returns.  Errors: FOS_ERR_INVALID_ARG (bad slot, count or pointer;
+ * more than 65535 frames of one stream), FOS_ERR_UNSUPPORTED, FOS_ERR_CUDA,
+ * FOS_ERR_OOM (its scratch is grown on demand; growing synchronises the device).
+ */
+fos_status fos_batch_process_frames_device(fos_batch* b, int32_t n, const int32_t* slots, const int32_t* n_frames,
+                                           const uint8_t* const* d_rgb, const uint16_t* const* d_depth,
+                                           uint8_t* const* d_mask_gmm, uint8_t* const* d_mask_pbas,
+                                           void* stream);
+/* Waits for the device; FOS_ERR_TIMEOUT if a wait of the last persistent
+ * launch of fos_batch_process_frames_device gave up (it cannot while every
+ * block is resident, as the cooperative launch guarantees), else FOS_OK. */
+fos_status fos_batch_sequence_status(fos_batch* b);
 /* Sets the kernel shapes of the batched launch (see fos_batch_tuning). */
 fos_status fos_batch_set_shape(fos_batch* b, int32_t gmm_px, int32_t pbas_px, int32_t pbas_ty);
 /*
@@ -411,17 +435,18 @@ fos_status fos_batch_autotune(fos_batch* b, int32_t n, const int32_t* slots,
  * Serving loop with continuous batching.  No counterpart in the paper.
  *
  * A server owns a batch and a worker thread.  Streams (cameras) are admitted
- * by a device-memory budget: each needs fos_stream_device_bytes plus three
- * input and three mask buffers (3 * 7 bytes per pixel, plus up to 15 bytes of
- * alignment per input buffer); a stream that does not fit, or finds no free
- * slot, waits in FIFO order until others close.  A housekeeping thread
+ * by a device-memory budget: each needs fos_server_stream_bytes (its models
+ * plus a ring of six device frames of inputs and masks, 6 * 7 bytes per pixel
+ * rounded up to 256-byte regions); a stream that does not fit, or finds no
+ * free slot, waits in FIFO order until others close.  A housekeeping thread
  * allocates an admitted stream's memory and frees that of streams that left,
  * so the worker's ticks never wait on an allocation or a free.
  * fos_server_submit copies a frame into one of the stream's queue_depth
  * pinned input slots (allocated by its first copying submit) and returns at
  * once.  Each worker tick takes
- * the oldest pending frame of every admitted stream (frames of one stream run
- * in order), runs them as one batched launch, and writes the masks into the
+ * the oldest pending frames of every admitted stream (up to three per stream,
+ * in order; frames of one stream run in order), runs them as batched graph
+ * steps back to back (one per frame slot), and writes the masks into the
  * caller's buffers given at submit time; three ticks are in flight (the
  * input copies of one, the kernels of another and the mask copies of a third
  * overlap), so frames that arrive while one runs join the next.  Results are identical to
@@ -447,6 +472,9 @@ typedef struct fos_server_stats_t {
     double kernel_us;    /* sum over ticks of the batched kernels' device time */
 } fos_server_stats_t;
 
+/* Device bytes the server charges against its budget for one width x height
+ * stream with these parameters (0 on bad input). */
+size_t fos_server_stream_bytes(int32_t width, int32_t height, const fos_params* params);
 /* Server over one device-memory budget (bytes), at most max_streams admitted
  * streams, and queue_depth (1..1024) queued-or-running frames per stream.
  * NULL on error (fos_last_error(NULL)). */

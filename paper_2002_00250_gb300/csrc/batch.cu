@@ -43,6 +43,12 @@ struct fos_batch {
     int gmm_px = 2, pbas_px = 2, pbas_ty = 8;  // tuned shapes
     GmmBatchTable gt{};
     PbasBatchTable pt{};
+    // several frames per call (fos_batch_process_frames_device): the launch
+    // table and its device scratch (claim counter, error word, scratch sums,
+    // completion words, gradient sums), grown on demand
+    SeqBatchTable qt{};
+    uint8_t* seq = nullptr;
+    size_t seq_bytes = 0;
     std::string err;
 };
 
@@ -61,6 +67,12 @@ fos_status bcuda(fos_batch* b, const char* what, cudaError_t e)
     std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
     return bfail(b, e == cudaErrorMemoryAllocation ? FOS_ERR_OOM : FOS_ERR_CUDA, buf);
 }
+
+#define FOS_BSTEP(call)                \
+    do {                               \
+        const fos_status st_ = (call); \
+        if (st_ != FOS_OK) return st_; \
+    } while (0)
 
 #define FOS_BTRY(b, call)                                  \
     do {                                                   \
@@ -256,6 +268,7 @@ void fos_batch_destroy(fos_batch* b)
     if (b->done && b->used) cudaEventSynchronize(b->done);
     for (fos_ctx* c : b->slot) fos_destroy(c);
     drop_graph(b);
+    cudaFree(b->seq);
     if (b->done) cudaEventDestroy(b->done);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
@@ -367,6 +380,182 @@ fos_status fos_batch_process_device(fos_batch* b, int32_t n, const int32_t* slot
     FOS_BTRY(b, cudaEventRecord(b->done, s));
     b->used = true;
     for (int i = 0; i < n; ++i) ctx_frame_done(b->slot[slots[i]]);
+    return FOS_OK;
+}
+
+fos_status fos_batch_process_frames_device(fos_batch* b, int32_t n, const int32_t* slots, const int32_t* n_frames,
+                                           const uint8_t* const* d_rgb, const uint16_t* const* d_depth,
+                                           uint8_t* const* d_mask_gmm, uint8_t* const* d_mask_pbas, void* stream)
+{
+    NvtxRange nvtx("fos_batch_process_frames_device");
+    if (!b) return FOS_ERR_INVALID_ARG;
+    if (n < 0 || n > b->max_streams) return bfail(b, FOS_ERR_INVALID_ARG, "n out of range");
+    if (n == 0) return FOS_OK;
+    if (!slots || !n_frames || !d_rgb || !d_depth || (gmm_on(b) && !d_mask_gmm) || (pbas_on(b) && !d_mask_pbas))
+        return bfail(b, FOS_ERR_INVALID_ARG, "NULL array argument");
+    int maxf = 0;
+    for (int i = 0; i < n; ++i) {
+        if (n_frames[i] < 0) return bfail(b, FOS_ERR_INVALID_ARG, "negative frame count");
+        maxf = std::max(maxf, int(n_frames[i]));
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int32_t> sl;
+    std::vector<const uint8_t*> r;
+    std::vector<const uint16_t*> d;
+    std::vector<uint8_t*> g, p;
+    // frame k of stream i (k < n_frames[i])
+    auto frame_of = [&](int i, int k) {
+        const fos_ctx* c = b->slot[slots[i]];
+        r.push_back(d_rgb[i] + size_t(k) * size_t(c->P) * 3);
+        d.push_back(d_depth[i] + size_t(k) * size_t(c->Pd));
+        g.push_back(gmm_on(b) ? d_mask_gmm[i] + size_t(k) * size_t(c->P) : nullptr);
+        p.push_back(pbas_on(b) ? d_mask_pbas[i] + size_t(k) * size_t(c->P) : nullptr);
+    };
+    auto step = [&]() -> fos_status {
+        const fos_status st = sl.empty() ? FOS_OK
+                                         : fos_batch_process_device(b, int32_t(sl.size()), sl.data(), r.data(), d.data(),
+                                                                    gmm_on(b) ? g.data() : nullptr,
+                                                                    pbas_on(b) ? p.data() : nullptr, stream);
+        sl.clear(); r.clear(); d.clear(); g.clear(); p.clear();
+        return st;
+    };
+    for (int i = 0; i < n; ++i)  // validates slots and pointers (and runs nothing)
+        if (slots[i] < 0 || slots[i] >= b->max_streams || !b->slot[slots[i]])
+            return bfail(b, FOS_ERR_INVALID_ARG, "bad slot");
+    if (!fused(b)) {  // one batched step per frame slot
+        for (int k = 0; k < maxf; ++k) {
+            for (int i = 0; i < n; ++i)
+                if (n_frames[i] > k) {
+                    sl.push_back(slots[i]);
+                    frame_of(i, k);
+                }
+            FOS_BSTEP(step());
+        }
+        return FOS_OK;
+    }
+    // frame 0 of streams that start here: one batched step
+    std::vector<int> first(size_t(n), 0);
+    for (int i = 0; i < n; ++i)
+        if (n_frames[i] > 0 && b->slot[slots[i]]->t == 0) {
+            sl.push_back(slots[i]);
+            frame_of(i, 0);
+            first[i] = 1;
+        }
+    FOS_BSTEP(step());
+    // the rest: entries sorted by remaining frames (descending), in launches of
+    // at most kSeqBatchMax streams
+    std::vector<int> order;
+    for (int i = 0; i < n; ++i)
+        if (n_frames[i] - first[i] > 0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return n_frames[x] - first[x] > n_frames[y] - first[y]; });
+    int px = b->pbas_px == 2 ? 2 : 1;
+    for (int i : order)
+        if (b->slot[slots[i]]->W % 2 != 0) px = 1;
+    const int ty = px == 2 && b->pbas_ty == 4 ? 4 : 8;
+    for (size_t c0 = 0; c0 < order.size(); c0 += kSeqBatchMax) {
+        const int m = int(std::min(order.size() - c0, size_t(kSeqBatchMax)));
+        SeqBatchTable& T = b->qt;
+        T.n = m;
+        // scratch: header, completion words, gradient sums
+        size_t words = 0, sums = 0;
+        for (int j = 0; j < m; ++j) {
+            const fos_ctx* c = b->slot[slots[order[c0 + j]]];
+            const int tx = (c->W + 32 * px - 1) / (32 * px), tyy = (c->H + ty - 1) / ty;
+            words += size_t(tx) * tyy;
+            sums += size_t(n_frames[order[c0 + j]] - first[order[c0 + j]] + 1) * 4;
+        }
+        const size_t need = 256 + sums * 8 + words * 4;
+        if (need > b->seq_bytes) {
+            FOS_BTRY(b, cudaDeviceSynchronize());  // an earlier launch may still use the old scratch
+            cudaFree(b->seq);
+            b->seq = nullptr;
+            b->seq_bytes = 0;
+            FOS_BTRY(b, dev_alloc(reinterpret_cast<void**>(&b->seq), need));
+            b->seq_bytes = need;
+        }
+        T.claim = reinterpret_cast<unsigned int*>(b->seq);
+        T.err = reinterpret_cast<int*>(b->seq + 4);
+        T.gscratch = reinterpret_cast<unsigned long long*>(b->seq + 64);
+        unsigned long long* gs = reinterpret_cast<unsigned long long*>(b->seq + 256);
+        int* dn = reinterpret_cast<int*>(b->seq + 256 + sums * 8);
+        T.done_all = dn;
+        T.done_words = int(words);
+        int tile_off = 0, gtile_off = 0;
+        for (int j = 0; j < m; ++j) {
+            const int i = order[c0 + j];
+            fos_ctx* c = b->slot[slots[i]];
+            const int nf = n_frames[i] - first[i], f0 = first[i];
+            SeqBatchEntry& E = T.e[j];
+            const uint8_t* rgb = d_rgb[i] + size_t(f0) * size_t(c->P) * 3;
+            const uint16_t* dep = d_depth[i] + size_t(f0) * size_t(c->Pd);
+            uint8_t* mg = d_mask_gmm[i] + size_t(f0) * size_t(c->P);
+            uint8_t* mp = d_mask_pbas[i] + size_t(f0) * size_t(c->P);
+            E.a = ctx_pbas_args(c, rgb, dep, mp);
+            T.g[j] = ctx_gmm_args(c, rgb, dep, mg);
+            E.n = nf;
+            E.tiles_x = (c->W + 32 * px - 1) / (32 * px);
+            E.tiles_y = (c->H + ty - 1) / ty;
+            E.tile_off = tile_off;
+            E.gtile_off = gtile_off;
+            tile_off += E.tiles_x * E.tiles_y;
+            gtile_off += ((c->W + 31) / 32) * ((c->H + kGradStripRows - 1) / kGradStripRows);
+            E.rgb_stride = c->P * 3;
+            E.depth_stride = c->Pd;
+            E.mask_stride = c->P;
+            E.req_base = c->req;
+            E.prev_base = c->prev;
+            E.gprev = gs;
+            gs += 4 * size_t(nf + 1);
+            E.gsum_src = E.a.gsum_prev;
+            E.gsum_last = c->aux + ((c->t + nf - 1) % 3) * 4;
+            E.gsum_zero = c->aux + ((c->t + nf) % 3) * 4;
+            E.done = dn;
+            dn += size_t(E.tiles_x) * E.tiles_y;
+        }
+        T.gtiles = gtile_off;
+        T.maxn = T.e[0].n;
+        if (T.maxn > 65535) return bfail(b, FOS_ERR_INVALID_ARG, "at most 65535 frames per stream and call");
+        // runs of frame slots with the same active entries (a prefix of the order)
+        T.segs = 0;
+        long long claims = 0;
+        int slot0 = 0;
+        for (int mm = m; mm > 0; --mm) {
+            const int slot1 = T.e[mm - 1].n;  // entries 0 .. mm-1 have at least slot1 frames
+            if (slot1 <= slot0) continue;
+            const int tiles = T.e[mm - 1].tile_off + T.e[mm - 1].tiles_x * T.e[mm - 1].tiles_y;
+            T.seg_slot0[T.segs] = slot0;
+            T.seg_m[T.segs] = mm;
+            T.seg_tiles[T.segs] = tiles;
+            T.seg_claim0[T.segs] = claims;
+            claims += static_cast<long long>(slot1 - slot0) * tiles;
+            slot0 = slot1;
+            T.segs += 1;
+        }
+        T.seg_slot0[T.segs] = slot0;
+        T.seg_claim0[T.segs] = claims;
+        if (claims >= (1ll << 32)) return bfail(b, FOS_ERR_INVALID_ARG, "too many tiles x frames in one call");
+        const LaunchResult lr = launch_batch_sequence(T, px, ty, s);
+        if (lr == kLaunchUnsupported) return bfail(b, FOS_ERR_UNSUPPORTED, "batch sequence: shape not compiled in");
+        if (lr != kLaunchOk) return bcuda(b, "batch sequence launch", cudaGetLastError());
+        for (int j = 0; j < m; ++j) {
+            fos_ctx* c = b->slot[slots[order[c0 + j]]];
+            for (int k = 0; k < T.e[j].n; ++k) ctx_frame_done(c);
+        }
+    }
+    FOS_BTRY(b, cudaEventRecord(b->done, s));
+    b->used = true;
+    return FOS_OK;
+}
+
+fos_status fos_batch_sequence_status(fos_batch* b)
+{
+    if (!b) return FOS_ERR_INVALID_ARG;
+    if (!b->seq) return FOS_OK;
+    FOS_BTRY(b, cudaDeviceSynchronize());
+    int e = 0;
+    FOS_BTRY(b, cudaMemcpy(&e, b->seq + 4, 4, cudaMemcpyDeviceToHost));
+    if (e) return bfail(b, FOS_ERR_TIMEOUT, "batch sequence: a tile's wait for its neighbours gave up");
     return FOS_OK;
 }
 

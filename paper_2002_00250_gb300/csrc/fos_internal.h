@@ -238,6 +238,55 @@ void fused_sequence_tiles(const PbasArgs& a, int& tiles_x, int& tiles_y);
 // out[n][4] (zero on entry).
 LaunchResult launch_grad_sums(const PbasArgs& a0, const SeqArgs& q, unsigned long long* out, cudaStream_t s);
 
+// Several frames of many fused streams in one persistent launch: the
+// sequence launch above generalised over the streams of a batch.  Entries are
+// sorted by frame count, descending, so that at frame slot i the streams with
+// more than i frames are entries 0 .. m_i-1; the claim order is slot-major,
+// then entry, then tile, and a tile waits for its own stream's 3x3 tiles of
+// the previous slot.
+struct SeqBatchEntry {
+    PbasArgs a;                        // frame t0 of the stream
+    int n;                             // frames
+    int tiles_x, tiles_y;              // tile grid (sequence tile shape)
+    int tile_off;                      // first tile of the stream within a slot
+    int gtile_off;                     // first 32 x kGradStripRows strip of the stream in the gradient pre-pass
+    int pad[3];
+    int64_t rgb_stride, depth_stride, mask_stride;
+    uint32_t* req_base;
+    uint64_t* prev_base;
+    unsigned long long* gprev;         // [n + 1][4]: frame t0-1 (copied from gsum_src), then frames t0 .. t0+n-1
+    const unsigned long long* gsum_src;  // the context's sums of frame t0-1
+    unsigned long long* gsum_last;     // where the context keeps frame t0+n-1's sums
+    unsigned long long* gsum_zero;     // the context's accumulator of frame t0+n (zeroed)
+    int* done;                         // [tiles]
+};
+constexpr int kSeqBatchMax = 48;
+constexpr int kGradStripRows = 64;  // rows of one block of the gradient pre-pass (32 pixels wide)
+struct SeqBatchTable {
+    int n;                             // entries (sorted by n, descending)
+    int segs;                          // runs of slots with the same active entries
+    int gtiles;                        // pre-pass tiles of all entries
+    int maxn;                          // frames of entry 0
+    // run r: slots [seg_slot0[r], seg_slot0[r+1]) with entries 0 .. seg_m[r]-1
+    // active (seg_tiles[r] tiles per slot), claims from seg_claim0[r]
+    int seg_slot0[kSeqBatchMax + 1];
+    int seg_m[kSeqBatchMax];
+    int seg_tiles[kSeqBatchMax];
+    long long seg_claim0[kSeqBatchMax + 1];
+    unsigned int* claim;
+    int* err;
+    unsigned long long* gscratch;      // [8]
+    int* done_all;                     // every entry's completion words
+    int done_words;
+    int pad;
+    SeqBatchEntry e[kSeqBatchMax];
+    GmmArgs g[kSeqBatchMax];
+};
+// Zero the counter and completion words, gradient sums set up, pre-pass,
+// the persistent launch, and the sums left where per-frame launches expect
+// them; all on stream s.
+LaunchResult launch_batch_sequence(const SeqBatchTable& t, int px, int ty, cudaStream_t s);
+
 LaunchResult launch_pbas_init(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_classify(const PbasArgs& a, cudaStream_t s);
 LaunchResult launch_pbas_flush(const PbasArgs& a, cudaStream_t s);

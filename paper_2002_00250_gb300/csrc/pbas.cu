@@ -324,6 +324,43 @@ fused_classify_kernel(const PbasArgs a, const GmmArgs g)
 
 // --- several frames in one persistent launch ---------------------------------
 
+// One block of the gradient pre-pass: a 32-pixel-wide strip of kGradStrip
+// rows, staged at once (with its 1-pixel halo, edge-clamped, as classify
+// stages its tiles) and summed by kGradTY rows of 32 threads.
+constexpr int kGradStrip = kGradStripRows, kGradTY = 8;
+constexpr int kGradSW = 34, kGradSWP = 36, kGradSH = kGradStrip + 2, kGradCH = kGradSH * kGradSWP;
+
+// Sums of the Sobel magnitudes of the strip at (x0, y0) of frame a, added to v[4].
+__device__ __forceinline__ void grad_strip(const PbasArgs& a, int x0, int y0, uint8_t* sm, uint32_t (&v)[4])
+{
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const bool mapped = a.Wd != a.W || a.Hd != a.H;
+    for (int idx = tid; idx < kGradSH * kGradSW; idx += 32 * kGradTY) {
+        const int r = idx / kGradSW, col = idx - r * kGradSW;
+        const int gx = min(max(x0 - 1 + col, 0), a.W - 1);
+        const int gy = min(max(y0 - 1 + r, 0), a.H - 1);
+        const int64_t p = int64_t(gy) * a.W + gx;
+        const int o = r * kGradSWP + col;
+        constexpr int n = 4 * kGradCH;
+        at(sm, o, n, 1, a.oob) = at(a.rgb, 3 * p, 3 * a.P, 2, a.oob);
+        at(sm, kGradCH + o, n, 1, a.oob) = at(a.rgb, 3 * p + 1, 3 * a.P, 2, a.oob);
+        at(sm, 2 * kGradCH + o, n, 1, a.oob) = at(a.rgb, 3 * p + 2, 3 * a.P, 2, a.oob);
+        const int64_t pd = mapped ? int64_t(uint32_t(gy * a.Hd) / uint32_t(a.H)) * a.Wd +
+                                        int64_t(uint32_t(gx * a.Wd) / uint32_t(a.W))
+                                  : p;
+        at(sm, 3 * kGradCH + o, n, 1, a.oob) = uint8_t(depth_to_u8(at(a.depth, pd, depth_extent(a), 3, a.oob), a.depth_fs));
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x;
+    for (int r = threadIdx.y; r < kGradStrip; r += kGradTY) {
+        if (x < a.W && y0 + r < a.H) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                v[c] += sobel(sm + c * kGradCH, kGradSWP, r + 1, threadIdx.x + 1, kGradCH, a.oob);
+        }
+    }
+}
+
 __device__ __forceinline__ int ld_acquire_gpu(const int* p)
 {
     int v;
@@ -416,27 +453,162 @@ fused_sequence_kernel(const PbasArgs a0, const GmmArgs g0, const SeqArgs q)
     }
 }
 
-// Gradient sums of frame blockIdx.z (the Sobel magnitudes classify_tile adds
-// to gsum_cur), one tile per block.
-template <int TY>
-__global__ void __launch_bounds__(32 * TY) grad_sums_kernel(const PbasArgs a0, const SeqArgs q,
-                                                            unsigned long long* out)
+// --- many streams, several frames, one persistent launch -------------------
+
+// seq_wait for a tile grid given by pointer and size.
+__device__ __forceinline__ void seq_wait_grid(const int* done, int tiles_x, int tiles_y, int tx, int ty,
+                                              int need, int* err)
 {
-    using G = Geo<1, TY>;
-    __shared__ __align__(16) uint8_t sm[4 * G::CH];
+    if (tx < 0 || ty < 0 || tx >= tiles_x || ty >= tiles_y) return;
+    const int* f = done + ty * tiles_x + tx;
+    for (uint32_t spin = 0; ld_acquire_gpu(f) < need; ++spin) {
+        if (spin >= kSeqSpinLimit || ((spin & 1023u) == 1023u && *(volatile int*)err)) {
+            atomicExch(err, 1);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
+// The arguments of frame t0+i of entry E.
+template <int PX>
+__device__ __forceinline__ void seq_batch_frame_args(PbasArgs& a, GmmArgs& g, const SeqBatchEntry& E, int i,
+                                                     unsigned long long* gscratch)
+{
+    const int64_t f = i;
+    a.rgb += f * E.rgb_stride;
+    a.depth += f * E.depth_stride;
+    a.mask += f * E.mask_stride;
+    a.t += uint32_t(i);
+    const int64_t pl = a.plane;
+    a.req_cur = E.req_base + int64_t(a.t & 1u) * pl;
+    a.req_prev = E.req_base + int64_t((a.t + 1u) & 1u) * pl;
+    if (a.propagate) {
+        a.prev = E.prev_base + int64_t(a.t & 1u) * pl;
+        a.prev_src = E.prev_base + int64_t((a.t + 1u) & 1u) * pl;
+    }
+    a.gsum_prev = E.gprev + 4 * f;
+    a.gsum_cur = gscratch;
+    a.gsum_next = gscratch + 4;
+    if (i > 0) a.apply = 1;
+    a.mask_vec = (reinterpret_cast<uintptr_t>(a.mask) % uintptr_t(PX)) == 0 ? 1 : 0;
+    g.rgb = a.rgb;
+    g.depth = a.depth;
+    g.mask += f * E.mask_stride;
+}
+
+// Entry of tile g among entries 0 .. m-1 (tile_off ascending).
+__device__ __forceinline__ int seq_batch_entry_of(const SeqBatchTable& T, int g, int m)
+{
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.e[mid].tile_off <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int NT, int PX, int TY>
+__global__ void __launch_bounds__(32 * TY, PX <= 2 ? 1024 / (32 * TY) : 1)
+batch_sequence_kernel(const __grid_constant__ SeqBatchTable T)
+{
+    using G = Geo<PX, TY>;
+    __shared__ ClassifySmem<PX, TY> S;
+    __shared__ long long s_it;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    const long long total = T.seg_claim0[T.segs];
+    for (;;) {
+        if (tid == 0) s_it = static_cast<long long>(atomicAdd(T.claim, 1u));
+        __syncthreads();
+        const long long it = s_it;
+        if (it >= total) break;
+        int r = 0, hi = T.segs - 1;  // run of slots holding this claim
+        while (r < hi) {
+            const int mid = (r + hi + 1) >> 1;
+            if (T.seg_claim0[mid] <= it) r = mid;
+            else hi = mid - 1;
+        }
+        const long long off = it - T.seg_claim0[r];
+        const int i = T.seg_slot0[r] + int(off / T.seg_tiles[r]);
+        const int gtile = int(off % T.seg_tiles[r]);
+        const int je = seq_batch_entry_of(T, gtile, T.seg_m[r]);
+        const SeqBatchEntry& E = T.e[je];
+        const int j = gtile - E.tile_off;
+        const int tx = j % E.tiles_x, ty = j / E.tiles_x;
+        if (i > 0 && tid < 9) seq_wait_grid(E.done, E.tiles_x, E.tiles_y, tx + tid % 3 - 1, ty + tid / 3 - 1, i, T.err);
+        __syncthreads();
+        PbasArgs a = E.a;
+        GmmArgs g = T.g[je];
+        seq_batch_frame_args<PX>(a, g, E, i, T.gscratch);
+        classify_tile<NT, PX, TY, 3, 3>(a, &g, tx * G::TW, ty * TY, S, true);
+        __syncthreads();
+        if (tid == 0) st_release_gpu(E.done + j, i + 1);
+    }
+}
+
+// Zeroes the claim counter, the error word and the completion words; sets
+// each entry's gradient sums (frame t0-1 copied, the rest zero for the pre-pass).
+__global__ void seq_batch_prepare_kernel(const __grid_constant__ SeqBatchTable T)
+{
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x, nth = int64_t(gridDim.x) * blockDim.x;
+    if (tid == 0) {
+        *T.claim = 0u;
+        *T.err = 0;
+    }
+    for (int64_t i = tid; i < T.done_words; i += nth) T.done_all[i] = 0;
+    for (int j = 0; j < T.n; ++j) {
+        const SeqBatchEntry& E = T.e[j];
+        for (int64_t i = tid; i < 4 * int64_t(E.n + 1); i += nth) E.gprev[i] = i < 4 ? E.gsum_src[i] : 0ull;
+    }
+}
+
+// Gradient sums of every entry's frames: block (x, y) = pre-pass tile x of
+// all entries, frame y of its entry.
+__global__ void __launch_bounds__(32 * kGradTY) seq_batch_grad_kernel(const __grid_constant__ SeqBatchTable T)
+{
+    __shared__ __align__(16) uint8_t sm[4 * kGradCH];
+    const int gt = int(blockIdx.x), f = int(blockIdx.y);
+    int lo = 0, hi = T.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.e[mid].gtile_off <= gt) lo = mid;
+        else hi = mid - 1;
+    }
+    const SeqBatchEntry& E = T.e[lo];
+    if (f >= E.n) return;  // uniform over the block
+    PbasArgs a = E.a;
+    a.rgb += int64_t(f) * E.rgb_stride;
+    a.depth += int64_t(f) * E.depth_stride;
+    const int l = gt - E.gtile_off, gtx = (a.W + 31) / 32;
+    uint32_t v[4] = {0, 0, 0, 0};
+    grad_strip(a, (l % gtx) * 32, (l / gtx) * kGradStrip, sm, v);
+    block_add<kGradTY, 4>(v, [&](int c) { return E.gprev + 4 + 4 * int64_t(f) + c; });
+}
+
+// Each entry's last-frame sums where its next per-frame launch reads them,
+// and the accumulator of that frame zeroed (one block of 4 * kSeqBatchMax threads).
+__global__ void seq_batch_finish_kernel(const __grid_constant__ SeqBatchTable T)
+{
+    const int j = int(threadIdx.x) / 4, q = int(threadIdx.x) % 4;
+    if (j >= T.n) return;
+    const SeqBatchEntry& E = T.e[j];
+    E.gsum_last[q] = E.gprev[4 * int64_t(E.n) + q];
+    E.gsum_zero[q] = 0ull;
+}
+
+// Gradient sums of frame blockIdx.z (the Sobel magnitudes classify_tile adds
+// to gsum_cur), one 32 x kGradStrip strip per block.
+__global__ void __launch_bounds__(32 * kGradTY) grad_sums_kernel(const PbasArgs a0, const SeqArgs q,
+                                                                 unsigned long long* out)
+{
+    __shared__ __align__(16) uint8_t sm[4 * kGradCH];
     PbasArgs a = a0;
     a.rgb += int64_t(blockIdx.z) * q.rgb_stride;
     a.depth += int64_t(blockIdx.z) * q.depth_stride;
-    const int x0 = blockIdx.x * G::TW, y0 = blockIdx.y * TY;
-    stage_input<1, TY>(a, x0, y0, sm);
-    __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     uint32_t v[4] = {0, 0, 0, 0};
-    if (x < a.W && y < a.H) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = sobel(sm + c * G::CH, G::SWP, threadIdx.y + 1, threadIdx.x + 1, G::CH, a.oob);
-    }
-    block_add<TY, 4>(v, [&](int c) { return out + 4 * int64_t(blockIdx.z) + c; });
+    grad_strip(a, blockIdx.x * 32, blockIdx.y * kGradStrip, sm, v);
+    block_add<kGradTY, 4>(v, [&](int c) { return out + 4 * int64_t(blockIdx.z) + c; });
 }
 
 // Applies the pending neighbour requests of the last frame to the samples
@@ -639,6 +811,38 @@ LaunchResult sequence_shape(const PbasArgs& a0, const GmmArgs& g0, const SeqArgs
     return kLaunchUnsupported;
 }
 
+template <int NT, int PX, int TY>
+LaunchResult batch_sequence_go(const SeqBatchTable& t, cudaStream_t s)
+{
+    auto k = batch_sequence_kernel<NT, PX, TY>;
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * TY, 0) != cudaSuccess)
+            return kLaunchCudaError;
+    }
+    const long long total = t.seg_claim0[t.segs];
+    const int grid = int(std::min<long long>(total, static_cast<long long>(per_sm) * sms));
+    if (grid < 1) return kLaunchOk;
+    SeqBatchTable* tp = const_cast<SeqBatchTable*>(&t);
+    void* args[] = {tp};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(k), dim3(unsigned(grid)), dim3(32, TY), args, 0, s) ==
+                   cudaSuccess
+               ? kLaunchOk
+               : kLaunchCudaError;
+}
+
+template <int NT>
+LaunchResult batch_sequence_shape(const SeqBatchTable& t, cudaStream_t s, int px, int ty)
+{
+    if (px == 2 && ty == 8) return batch_sequence_go<NT, 2, 8>(t, s);
+    if (px == 2 && ty == 4) return batch_sequence_go<NT, 2, 4>(t, s);
+    if (px == 1 && ty == 8) return batch_sequence_go<NT, 1, 8>(t, s);
+    return kLaunchUnsupported;
+}
+
 // Tile shape of the sequence launch for a context's options: 2 px x 8 or 4
 // rows when the width allows; otherwise 1 px x 8 rows.
 static void sequence_tile(const PbasArgs& a, int& px, int& ty)
@@ -664,11 +868,26 @@ LaunchResult launch_fused_sequence(const PbasArgs& a0, const GmmArgs& g0, const 
     return a0.N == 20 ? sequence_shape<20>(a0, g0, q, s, px, ty) : sequence_shape<0>(a0, g0, q, s, px, ty);
 }
 
+LaunchResult launch_batch_sequence(const SeqBatchTable& t, int px, int ty, cudaStream_t s)
+{
+    static_assert(sizeof(SeqBatchTable) <= 32000, "kernel parameter space");
+    if (t.n == 0 || t.seg_claim0[t.segs] == 0) return kLaunchOk;
+    seq_batch_prepare_kernel<<<64, 256, 0, s>>>(t);
+    if (cudaGetLastError() != cudaSuccess) return kLaunchCudaError;
+    seq_batch_grad_kernel<<<dim3(unsigned(t.gtiles), unsigned(t.maxn)), dim3(32, kGradTY), 0, s>>>(t);
+    if (cudaGetLastError() != cudaSuccess) return kLaunchCudaError;
+    const int N = t.e[0].a.N;
+    const LaunchResult r = N == 20 ? batch_sequence_shape<20>(t, s, px, ty) : batch_sequence_shape<0>(t, s, px, ty);
+    if (r != kLaunchOk) return r;
+    seq_batch_finish_kernel<<<1, 4 * kSeqBatchMax, 0, s>>>(t);
+    return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
+}
+
 LaunchResult launch_grad_sums(const PbasArgs& a0, const SeqArgs& q, unsigned long long* out, cudaStream_t s)
 {
     if (a0.P == 0 || q.n == 0) return kLaunchOk;
-    const dim3 grid(unsigned((a0.W + 31) / 32), unsigned((a0.H + 7) / 8), unsigned(q.n));
-    grad_sums_kernel<8><<<grid, dim3(32, 8), 0, s>>>(a0, q, out);
+    const dim3 grid(unsigned((a0.W + 31) / 32), unsigned((a0.H + kGradStrip - 1) / kGradStrip), unsigned(q.n));
+    grad_sums_kernel<<<grid, dim3(32, kGradTY), 0, s>>>(a0, q, out);
     return cudaGetLastError() == cudaSuccess ? kLaunchOk : kLaunchCudaError;
 }
 

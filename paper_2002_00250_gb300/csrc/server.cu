@@ -1,15 +1,15 @@
 // server.cu -- serving loop with continuous batching over camera streams.
 //
 // No counterpart in the paper (one camera there).  Streams are admitted by
-// an HBM budget: a stream needs its device-resident models plus three input
-// and three mask buffers; a stream that does not fit waits (FIFO) until others
+// an HBM budget: a stream needs its device-resident models plus a ring of six
+// input and mask frames; a stream that does not fit waits (FIFO) until others
 // leave.  fos_server_submit copies a frame into one of the stream's pinned
 // input slots and returns at once; with no free slot, or before admission,
 // it refuses the frame (backpressure).  A worker thread runs ticks: each tick
-// takes the oldest pending frame of every admitted stream (at most one per
-// stream, so every stream's frames run in order), copies them to the device,
-// runs ONE batched launch over all of them (fos_batch), and copies the masks
-// back.  Three ticks are in flight, on three CUDA streams (input copies,
+// takes the oldest pending frames of every admitted stream (up to three per
+// stream, in order), copies them to the device, runs ONE batched launch over
+// all of them (fos_batch: one graph step per frame slot, back to back), and
+// copies the masks back.  Three ticks are in flight, on three CUDA streams (input copies,
 // kernels, mask copies): frames that arrive while a tick runs are admitted
 // into the next one.  Completed frames are delivered into the caller's mask
 // buffers and reported by fos_server_poll with their latency.
@@ -22,6 +22,7 @@
 // drain the pipeline).  Pinned host staging (the input slots of copying
 // submits, the mask staging for pageable mask buffers) is allocated by the
 // first submit of the stream that needs it, on the submitting thread.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -68,6 +69,11 @@ size_t depth_offset(size_t P) { return round16(P * 3); }
 // Ticks in flight: the input copies of one tick, the kernels of another and
 // the mask copies of a third run at the same time.
 constexpr int kTicks = 3;
+// Per stream: a ring of kRing device frame buffers (inputs and masks); a tick
+// takes up to kTickFrames of a stream's pending frames (consecutive ring
+// slots), so a stream has at most kRing frames in flight.
+constexpr int kRing = 6, kTickFrames = 3;
+size_t round256(size_t n) { return (n + 255) / 256 * 256; }
 
 // True for NULL and for page-locked host memory (cudaHostAlloc /
 // cudaHostRegister), which the copy engines can write directly.
@@ -82,8 +88,6 @@ bool host_pinned(const void* p)
     return a.type == cudaMemoryTypeHost;
 }
 size_t input_bytes(size_t P) { return depth_offset(P) + P * 2; }
-// One mask buffer: P bytes and 16 of slack, 16-byte aligned.
-size_t mask_bytes(size_t P) { return round16(P + 16); }
 
 struct Stream {
     int id;              // server handle
@@ -96,15 +100,14 @@ struct Stream {
     fos_ctx* ctx = nullptr;  // its models, from the housekeeper
     std::deque<Frame> pending;
     int inflight = 0;    // frames of this stream in ticks not yet completed
-    // by frame number mod kTicks: a stream has at most one frame in each of
-    // the kTicks ticks in flight
-    uint8_t* dbuf = nullptr;                   // the device buffers below, one allocation
-    uint8_t* d_in[kTicks] = {};                // device rgb+depth
-    uint8_t* d_mg[kTicks] = {};
-    uint8_t* d_mp[kTicks] = {};
-    uint8_t* hstage = nullptr;                 // pinned mask staging, on first need
-    uint8_t* h_mg[kTicks] = {};
-    uint8_t* h_mp[kTicks] = {};
+    // by frame number mod kRing; each ring is contiguous (frame k at k
+    // frames' bytes), as the batched multi-frame launch takes it
+    uint8_t* dbuf = nullptr;                   // the device rings below, one allocation
+    uint8_t* d_rgb = nullptr;                  // [kRing][P*3]
+    uint16_t* d_dep = nullptr;                 // [kRing][P]
+    uint8_t* d_mg = nullptr;                   // [kRing][P]
+    uint8_t* d_mp = nullptr;                   // [kRing][P]
+    uint8_t* hstage = nullptr;                 // pinned mask staging [kRing][2][P], on first need
     int64_t nframes = 0;
     uint8_t* arena = nullptr;                  // pinned input slots, on the first copying submit
     bool host_alloc = false;                   // a submit is allocating arena or staging now
@@ -114,7 +117,7 @@ struct Stream {
 
 struct TickItem {
     int stream;
-    int parity;
+    int ring;    // ring slot of the frame
     Frame f;
 };
 
@@ -159,10 +162,12 @@ struct fos_server {
 
 namespace {
 
-size_t stream_bytes(const fos_server* s, int32_t W, int32_t H)
+// Device bytes of a stream's frame rings (the model is fos_stream_device_bytes).
+size_t ring_bytes(size_t P) { return round256(kRing * P * 3) + round256(kRing * P * 2) + 2 * round256(kRing * P); }
+
+size_t stream_bytes(const fos_params* prm, int32_t W, int32_t H)
 {
-    const size_t P = size_t(W) * size_t(H);
-    return fos_stream_device_bytes(W, H, &s->prm) + kTicks * (input_bytes(P) + 2 * P);
+    return fos_stream_device_bytes(W, H, prm) + ring_bytes(size_t(W) * size_t(H));
 }
 
 size_t slot_bytes(size_t P) { return round16(input_bytes(P)); }
@@ -178,8 +183,7 @@ bool allocate_stream(fos_server* s, Stream* st, std::string& why)
         return false;
     }
     const size_t P = size_t(st->W) * size_t(st->H);
-    const size_t per = slot_bytes(P) + 2 * mask_bytes(P);
-    if (dev_alloc(reinterpret_cast<void**>(&st->dbuf), kTicks * per) != cudaSuccess) {
+    if (dev_alloc(reinterpret_cast<void**>(&st->dbuf), ring_bytes(P)) != cudaSuccess) {
         cudaGetLastError();
         fos_destroy(st->ctx);
         st->ctx = nullptr;
@@ -187,12 +191,10 @@ bool allocate_stream(fos_server* s, Stream* st, std::string& why)
         why = "admission: device memory exhausted (frame buffers)";
         return false;
     }
-    for (int k = 0; k < kTicks; ++k) {
-        uint8_t* b = st->dbuf + size_t(k) * per;
-        st->d_in[k] = b;
-        st->d_mg[k] = b + slot_bytes(P);
-        st->d_mp[k] = b + slot_bytes(P) + mask_bytes(P);
-    }
+    st->d_rgb = st->dbuf;
+    st->d_dep = reinterpret_cast<uint16_t*>(st->dbuf + round256(kRing * P * 3));
+    st->d_mg = st->dbuf + round256(kRing * P * 3) + round256(kRing * P * 2);
+    st->d_mp = st->d_mg + round256(kRing * P);
     return true;
 }
 
@@ -310,8 +312,8 @@ void publish(fos_server* s, Tick& t)
         Stream* st = s->streams[it.stream];
         const size_t P = size_t(st->W) * size_t(st->H);
         if (!it.f.direct_out) {
-            if (it.f.out_gmm) std::memcpy(it.f.out_gmm, st->h_mg[it.parity], P);
-            if (it.f.out_pbas) std::memcpy(it.f.out_pbas, st->h_mp[it.parity], P);
+            if (it.f.out_gmm) std::memcpy(it.f.out_gmm, st->hstage + (2 * size_t(it.ring)) * P, P);
+            if (it.f.out_pbas) std::memcpy(it.f.out_pbas, st->hstage + (2 * size_t(it.ring) + 1) * P, P);
         }
         if (it.f.host_in) st->free_in.push_back(it.f.host_in);
         fos_server_result r{};
@@ -350,10 +352,10 @@ void worker_main(fos_server* s)
 {
     cudaSetDevice(s->device);
     std::deque<Tick> inflight;
-    std::vector<int32_t> slots;
-    std::vector<const uint8_t*> rgb;
-    std::vector<const uint16_t*> dep;
-    std::vector<uint8_t*> mg, mp;
+    std::vector<int32_t> slots, counts, ks;
+    std::vector<const uint8_t*> rgb, kr;
+    std::vector<const uint16_t*> dep, kd;
+    std::vector<uint8_t*> mg, mp, kg, kp;
     for (;;) {
         Tick t;
         {
@@ -371,46 +373,56 @@ void worker_main(fos_server* s)
             if (inflight.empty()) s->cv.wait_for(lk, std::chrono::milliseconds(1), ready);
             if (s->stop && inflight.empty()) break;
             attach_ready(s);
-            // continuous batching: the oldest frame of every admitted stream
-            // whose previous frame is not still using this parity's buffers
+            // continuous batching: the oldest frames of every admitted stream,
+            // up to kTickFrames consecutive ring slots that no frame in flight
+            // still uses (items of one stream are adjacent, in frame order)
             for (size_t h = 0; h < s->streams.size(); ++h) {
                 Stream* st = s->streams[h];
-                if (!st || st->slot < 0 || st->pending.empty() || st->inflight >= kTicks) continue;
-                TickItem it;
-                it.stream = int(h);
-                it.parity = int(st->nframes % kTicks);
-                it.f = st->pending.front();
-                st->pending.pop_front();
-                st->nframes += 1;
-                st->inflight += 1;
-                t.items.push_back(it);
+                if (!st || st->slot < 0 || st->pending.empty()) continue;
+                const int r0 = int(st->nframes % kRing);
+                const int take = std::min({int(st->pending.size()), kTickFrames, kRing - st->inflight, kRing - r0});
+                for (int k = 0; k < take; ++k) {
+                    TickItem it;
+                    it.stream = int(h);
+                    it.ring = r0 + k;
+                    it.f = st->pending.front();
+                    st->pending.pop_front();
+                    st->nframes += 1;
+                    st->inflight += 1;
+                    t.items.push_back(it);
+                }
             }
         }
         if (!t.items.empty()) {
-            slots.clear(); rgb.clear(); dep.clear(); mg.clear(); mp.clear();
+            slots.clear(); counts.clear(); rgb.clear(); dep.clear(); mg.clear(); mp.clear();
             cudaError_t e = cudaSuccess;
-            for (TickItem& it : t.items) {
+            bool multi = false;
+            for (size_t q = 0; q < t.items.size(); ++q) {
+                TickItem& it = t.items[q];
                 Stream* st = s->streams[it.stream];
                 const size_t P = size_t(st->W) * size_t(st->H);
-                const size_t od = depth_offset(P);
-                if (it.f.host_in) {  // one copy of the packed slot
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.host_in, od + P * 2, cudaMemcpyHostToDevice, s->cin);
-                } else {             // zero-copy submit: straight from the caller's buffers
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(st->d_in[it.parity], it.f.ext_rgb, P * 3, cudaMemcpyHostToDevice, s->cin);
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(st->d_in[it.parity] + od, it.f.ext_depth, P * 2, cudaMemcpyHostToDevice, s->cin);
+                uint8_t* dr = st->d_rgb + size_t(it.ring) * P * 3;
+                uint16_t* dd = st->d_dep + size_t(it.ring) * P;
+                const uint8_t* hr = it.f.host_in ? it.f.host_in : it.f.ext_rgb;
+                const uint16_t* hd = it.f.host_in ? reinterpret_cast<const uint16_t*>(it.f.host_in + depth_offset(P))
+                                                  : it.f.ext_depth;
+                if (e == cudaSuccess) e = cudaMemcpyAsync(dr, hr, P * 3, cudaMemcpyHostToDevice, s->cin);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(dd, hd, P * 2, cudaMemcpyHostToDevice, s->cin);
+                if (q == 0 || t.items[q - 1].stream != it.stream) {  // the stream's first frame in the tick
+                    slots.push_back(st->slot);
+                    counts.push_back(1);
+                    rgb.push_back(dr);
+                    dep.push_back(dd);
+                    mg.push_back(st->d_mg + size_t(it.ring) * P);
+                    mp.push_back(st->d_mp + size_t(it.ring) * P);
+                } else {
+                    counts.back() += 1;
+                    multi = true;
                 }
-                slots.push_back(st->slot);
-                rgb.push_back(st->d_in[it.parity]);
-                dep.push_back(reinterpret_cast<const uint16_t*>(st->d_in[it.parity] + od));
-                mg.push_back(st->d_mg[it.parity]);
-                mp.push_back(st->d_mp[it.parity]);
             }
             // the input copies of this tick overlap the previous tick's kernels,
             // its mask copies the next tick's (at most kTicks ticks in flight,
-            // and a stream's frames in them use different buffers)
+            // and a stream's frames in them use different ring slots)
             if (e == cudaSuccess) e = take_event(s, &t.in);
             if (e == cudaSuccess) e = take_event(s, &t.k0);
             if (e == cudaSuccess) e = take_event(s, &t.k);
@@ -420,20 +432,35 @@ void worker_main(fos_server* s)
             if (e == cudaSuccess) e = cudaEventRecord(t.k0, s->cs);
             t.t_launch = now_us();
             fos_status bst = FOS_OK;
-            if (e == cudaSuccess)
-                bst = fos_batch_process_device(s->batch, int32_t(slots.size()), slots.data(), rgb.data(),
-                                               dep.data(), mg.data(), mp.data(), s->cs);
+            // one batched graph step per frame slot, back to back on the
+            // kernel stream (a stream with k frames takes part in the first k)
+            for (int k = 0; e == cudaSuccess && bst == FOS_OK && (k == 0 || multi); ++k) {
+                ks.clear(); kr.clear(); kd.clear(); kg.clear(); kp.clear();
+                for (size_t j = 0; j < slots.size(); ++j) {
+                    if (counts[j] <= k) continue;
+                    const fos_ctx* c = fos_batch_stream(s->batch, slots[j]);
+                    const size_t P = size_t(c->P);
+                    ks.push_back(slots[j]);
+                    kr.push_back(rgb[j] + size_t(k) * P * 3);
+                    kd.push_back(dep[j] + size_t(k) * P);
+                    kg.push_back(mg[j] + size_t(k) * P);
+                    kp.push_back(mp[j] + size_t(k) * P);
+                }
+                if (ks.empty()) break;
+                bst = fos_batch_process_device(s->batch, int32_t(ks.size()), ks.data(), kr.data(), kd.data(),
+                                               kg.data(), kp.data(), s->cs);
+            }
             if (e == cudaSuccess && bst == FOS_OK) e = cudaEventRecord(t.k, s->cs);
             if (e == cudaSuccess && bst == FOS_OK) e = cudaStreamWaitEvent(s->cout, t.k, 0);
             for (TickItem& it : t.items) {
                 Stream* st = s->streams[it.stream];
                 const size_t P = size_t(st->W) * size_t(st->H);
-                uint8_t* og = it.f.direct_out ? it.f.out_gmm : st->h_mg[it.parity];
-                uint8_t* op = it.f.direct_out ? it.f.out_pbas : st->h_mp[it.parity];
+                uint8_t* og = it.f.direct_out ? it.f.out_gmm : st->hstage + 2 * size_t(it.ring) * P;
+                uint8_t* op = it.f.direct_out ? it.f.out_pbas : st->hstage + (2 * size_t(it.ring) + 1) * P;
                 if (e == cudaSuccess && bst == FOS_OK && (s->prm.methods & FOS_METHOD_GMM) && og)
-                    e = cudaMemcpyAsync(og, st->d_mg[it.parity], P, cudaMemcpyDeviceToHost, s->cout);
+                    e = cudaMemcpyAsync(og, st->d_mg + size_t(it.ring) * P, P, cudaMemcpyDeviceToHost, s->cout);
                 if (e == cudaSuccess && bst == FOS_OK && (s->prm.methods & FOS_METHOD_PBAS) && op)
-                    e = cudaMemcpyAsync(op, st->d_mp[it.parity], P, cudaMemcpyDeviceToHost, s->cout);
+                    e = cudaMemcpyAsync(op, st->d_mp + size_t(it.ring) * P, P, cudaMemcpyDeviceToHost, s->cout);
             }
             if (e == cudaSuccess && bst == FOS_OK) e = cudaEventRecord(t.done, s->cout);
             if (e != cudaSuccess || bst != FOS_OK) {
@@ -517,8 +544,7 @@ fos_status ensure_host_memory(fos_server* s, int32_t stream, bool arena, bool st
         ok = cudaHostAlloc(reinterpret_cast<void**>(&a), size_t(s->queue_depth) * slot_bytes(P),
                            cudaHostAllocDefault) == cudaSuccess;
     if (ok && need_stage)
-        ok = cudaHostAlloc(reinterpret_cast<void**>(&g), kTicks * 2 * mask_bytes(P), cudaHostAllocDefault) ==
-             cudaSuccess;
+        ok = cudaHostAlloc(reinterpret_cast<void**>(&g), kRing * 2 * P, cudaHostAllocDefault) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         cudaFreeHost(a);
@@ -538,13 +564,7 @@ fos_status ensure_host_memory(fos_server* s, int32_t stream, bool arena, bool st
         st->free_in.clear();
         for (int q = 0; q < s->queue_depth; ++q) st->free_in.push_back(a + size_t(q) * slot_bytes(P));
     }
-    if (g) {
-        st->hstage = g;
-        for (int k = 0; k < kTicks; ++k) {
-            st->h_mg[k] = g + size_t(2 * k) * mask_bytes(P);
-            st->h_mp[k] = g + size_t(2 * k + 1) * mask_bytes(P);
-        }
-    }
+    if (g) st->hstage = g;
     return FOS_OK;
 }
 
@@ -615,6 +635,12 @@ void fos_server_destroy(fos_server* s)
 
 const char* fos_server_last_error(const fos_server* s) { return s ? s->err.c_str() : ""; }
 
+size_t fos_server_stream_bytes(int32_t width, int32_t height, const fos_params* params)
+{
+    if (!params || width < 1 || height < 1) return 0;
+    return stream_bytes(params, width, height);
+}
+
 int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uint32_t stream_id)
 {
     if (!s || width < 1 || height < 1) return -1;
@@ -622,7 +648,7 @@ int32_t fos_server_open_stream(fos_server* s, int32_t width, int32_t height, uin
     st->W = width;
     st->H = height;
     st->stream_id = stream_id;
-    st->bytes = stream_bytes(s, width, height);
+    st->bytes = stream_bytes(&s->prm, width, height);
     std::lock_guard<std::mutex> lk(s->mu);
     if (st->bytes > s->budget) {
         s->err = "stream needs more device memory than the whole budget";

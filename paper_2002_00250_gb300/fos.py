@@ -141,8 +141,11 @@ SIGNATURES = {
     "fos_batch_remove_stream": (_st, [_vp, _i32]),
     "fos_batch_stream": (_vp, [_vp, _i32]),
     "fos_batch_process_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fos_batch_process_frames_device": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "fos_batch_sequence_status": (_st, [_vp]),
     "fos_batch_set_shape": (_st, [_vp, _i32, _i32, _i32]),
     "fos_batch_autotune": (_st, [_vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(BatchTuning)]),
+    "fos_server_stream_bytes": (ctypes.c_size_t, [_i32, _i32, ctypes.POINTER(Params)]),
     "fos_server_create": (_vp, [ctypes.POINTER(Params), ctypes.c_size_t, _i32, _i32]),
     "fos_server_destroy": (None, [_vp]),
     "fos_server_last_error": (ctypes.c_char_p, [_vp]),
@@ -479,6 +482,22 @@ class Batch:
         self._check(self.lib.fos_batch_process_device(
             self.h, n, sl, self._arr([_ptr(r) for r in rgb]), self._arr([_ptr(d) for d in depth]),
             mg, mp, _stream_handle(stream)))
+
+    def process_frames(self, slots, rgb, depth, mask_gmm=None, mask_pbas=None, stream=None):
+        """Several frames for each listed slot: rgb[i] (n_i, H, W, 3), depth[i]
+        (n_i, Hd, Wd), masks (n_i, H, W) torch CUDA tensors (n_i may differ)."""
+        n = len(slots)
+        nf = [int(r.shape[0]) for r in rgb]
+        mg = self._arr([_ptr(m) for m in mask_gmm]) if mask_gmm is not None else None
+        mp = self._arr([_ptr(m) for m in mask_pbas]) if mask_pbas is not None else None
+        self._check(self.lib.fos_batch_process_frames_device(
+            self.h, n, (ctypes.c_int32 * n)(*slots), (ctypes.c_int32 * n)(*nf),
+            self._arr([_ptr(r) for r in rgb]), self._arr([_ptr(d) for d in depth]), mg, mp,
+            _stream_handle(stream)))
+
+    def sequence_status(self) -> None:
+        """Raises if a bounded wait of the last multi-frame launch gave up."""
+        self._check(self.lib.fos_batch_sequence_status(self.h))
 
     def set_shape(self, gmm_px: int, pbas_px: int, pbas_ty: int) -> None:
         self._check(self.lib.fos_batch_set_shape(self.h, gmm_px, pbas_px, pbas_ty))

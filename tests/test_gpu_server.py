@@ -23,7 +23,7 @@ def test_served_results_equal_alone_with_join_leave_and_waiting():
     n = 10
     data = [scene(W, H, n, seed=80 + i) for i, (W, H) in enumerate(sizes)]
     p = fos.default_params()
-    need = [fos.load().fos_stream_device_bytes(W, H, p) + 3 * 7 * W * H for W, H in sizes]
+    need = [fos.load().fos_server_stream_bytes(W, H, p) for W, H in sizes]
     # room for the first three streams only: the fourth waits until the
     # second closes, the fifth until the third closes
     budget = max(need[0] + need[1] + need[2], need[0] + need[3] + need[4]) + 4096
@@ -132,7 +132,7 @@ def test_waiting_stream_refuses_frames_until_admitted():
     from paper_2002_00250_gb300 import fos
     W, H = 64, 32
     rgb, depth, _ = scene(W, H, 2, seed=96)
-    need = fos.load().fos_stream_device_bytes(W, H, fos.default_params()) + 3 * 7 * W * H
+    need = fos.load().fos_server_stream_bytes(W, H, fos.default_params())
     srv = fos.Server(need + need // 2, 4, queue_depth=2)   # room for one stream
     a = srv.open_stream(W, H, stream_id=1)
     b = srv.open_stream(W, H, stream_id=2)
