@@ -306,7 +306,12 @@ fos_status fos_get_timing(fos_ctx* ctx, fos_kernel_timing out[FOS_KERNEL_COUNT])
                               call in one persistent launch, in which a tile of frame t+1 starts
                               as soon as the 3x3 tiles around it have finished frame t; 0: one
                               launch per frame.  Same bits either way. */
-#define FOS_OPT_COUNT 8
+#define FOS_OPT_GMM_STREAM 8 /* 1 (default): GMM frames >= 1 of the 3+3 model (depth of the colour
+                              frame's size, 16-byte aligned frame buffers) through the bulk-copy
+                              kernel, which stages 256-pixel chunks of the state planes and inputs
+                              in shared memory while the previous chunks compute; 0: the
+                              register kernels shaped by FOS_OPT_GMM_PX / _TPB.  Same bits. */
+#define FOS_OPT_COUNT 9
 
 /* Sets a kernel-shape option; FOS_ERR_INVALID_ARG for unknown options or
  * values, FOS_ERR_UNSUPPORTED for shapes not compiled in. */

@@ -28,7 +28,7 @@ thread_local fos_status g_create_status = FOS_OK;
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-constexpr int kAuxWords = 32;  // aux: gsum[3][4], counters[3], ..., OobWord at word 16
+constexpr int kAuxWords = 32;  // aux: gsum[3][4], counters[3], GMM error word 15, OobWord at word 16
 
 // The context's violation record in range-checked builds (none otherwise).
 fos::OobWord* oob_of(fos_ctx* c)
@@ -238,6 +238,8 @@ GmmArgs gmm_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_t*
     a.px = c->opt[FOS_OPT_GMM_PX];
     a.tpb = c->opt[FOS_OPT_GMM_TPB];
     a.oob = oob_of(c);
+    a.stream = c->opt[FOS_OPT_GMM_STREAM];
+    a.err = reinterpret_cast<int*>(c->aux + 15);
     return a;
 }
 
@@ -415,8 +417,13 @@ fos_status process_device_frames(fos_ctx* c, int32_t n, const uint8_t* rgb, size
 // Error word of the last sequence launch (after a synchronisation).
 fos_status seq_check(fos_ctx* c)
 {
-    if (!c->seq) return FOS_OK;
     int e = 0;
+    FOS_TRY(c, cudaMemcpy(&e, c->aux + 15, 4, cudaMemcpyDeviceToHost));
+    if (e) {
+        FOS_TRY(c, cudaMemset(c->aux + 15, 0, 4));
+        return fail(c, FOS_ERR_TIMEOUT, "gmm: a bulk copy's wait gave up");
+    }
+    if (!c->seq) return FOS_OK;
     FOS_TRY(c, cudaMemcpy(&e, c->seq + 4, 4, cudaMemcpyDeviceToHost));
     if (e) {
         FOS_TRY(c, cudaMemset(c->seq + 4, 0, 4));
@@ -933,6 +940,7 @@ fos_status fos_set_option(fos_ctx* ctx, int32_t option, int32_t value)
     case FOS_OPT_FUSE: ok = value == 0 || value == 1; break;
     case FOS_OPT_TEMPORAL: ok = value == 0 || value == 1; break;
     case FOS_OPT_SEQUENCE: ok = value == 0 || value == 1; break;
+    case FOS_OPT_GMM_STREAM: ok = value == 0 || value == 1; break;
     default: return fail(ctx, FOS_ERR_INVALID_ARG, "unknown option");
     }
     if (!ok) return fail(ctx, FOS_ERR_INVALID_ARG, "option value not supported");

@@ -37,7 +37,7 @@ struct fos_ctx {
     uint32_t* req = nullptr;            // [2][pplane] requests of even / odd frames
     uint64_t* prev = nullptr;           // [pplane]
     bool pending = false;               // requests of the last frame not yet applied
-    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1, 1, 1};  // kernel shapes (fos_set_option)
+    int opt[FOS_OPT_COUNT] = {0, 4, 128, 2, 8, 1, 1, 1, 1};  // kernel shapes (fos_set_option)
     unsigned long long* aux = nullptr;  // gsum[3][4], counters[3]
     // several frames in one launch (grown on demand): a 256-byte header (tile
     // counter, error word, 8 scratch sums), gradient sums [frames + 1][4],

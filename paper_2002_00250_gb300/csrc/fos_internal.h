@@ -97,6 +97,8 @@ struct GmmArgs {
     int tpb;            // threads per block: 64, 128 or 256
     int W, H, Wd, Hd;   // colour frame; depth frame (resampled on read when it differs)
     OobWord* oob;       // range-checked builds: the context's violation record
+    int stream;         // 1: frames >= 1 of the 3+3 model through the bulk-copy kernel
+    int* err;           // set to 1 by the bulk-copy kernel if a bounded wait gave up
 };
 
 LaunchResult launch_gmm(const GmmArgs& a, int Kr, int Kd, cudaStream_t s);

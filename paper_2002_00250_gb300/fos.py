@@ -165,6 +165,7 @@ SIGNATURES = {
     "fos_softgmm_backward": (_st, [_vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp]),
 }
 OPT_GMM_PX, OPT_GMM_TPB, OPT_PBAS_PX, OPT_PBAS_TY, OPT_FUSE, OPT_TEMPORAL, OPT_SEQUENCE = 1, 2, 3, 4, 5, 6, 7
+OPT_GMM_STREAM = 8
 
 _lib = None
 
