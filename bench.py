@@ -537,8 +537,31 @@ def run_softgmm(args):
     for _ in range(args.steps):
         loss, g = it()
     dt = (time.perf_counter() - t0) / args.steps
+    # instruction-issue roofline: the kernels are bound by issue, not memory
+    # (profiles/softgmm_640x480.md); warp instructions per pixel-frame from
+    # that capture, peak = SMs x 4 schedulers x 1 per cycle x max SM clock
+    roof = None
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "softgmm_640x480.md")).read()
+        f = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith("warp_instructions_per_pixel_frame"))
+        ipf = float(f["warp_instructions_per_pixel_frame_forward"]) + float(f["warp_instructions_per_pixel_frame_adjoint"])
+        props = torch.cuda.get_device_properties(0)
+        try:
+            smax = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]
+        except Exception:
+            smax = 2070.0
+        peak = props.multi_processor_count * 4 * smax * 1e6 / 1e9
+        ach = ipf * B * T * W * H / dt / 1e9
+        roof = {"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1),
+                "unit": "G warp-instructions/s", "frac": round(ach / peak, 3), "traffic": None,
+                "source": f"profiles/softgmm_640x480.md: {ipf:.1f} warp instructions per pixel-frame "
+                          f"(forward + adjoint); peak {props.multi_processor_count} SMs x 4 issues per "
+                          f"cycle at {smax:.0f} MHz"}
+    except Exception as e:
+        roof = {"unavailable": str(e)}
     out = {"metric": "soft-GMM forward+adjoint", "value": round(dt, 4), "unit": "s/iteration",
            "mpx_frames_per_s": round(B * T * W * H / dt / 1e6, 1), "higher_is_better": False,
+           "roofline": roof,
            "steps": args.steps, "warmup": args.warmup, "dtype": "f32 (reductions f64)", "data": "synthetic",
            "config": {"workload": f"soft-GMM {B}x{W}x{H}x{T}, checkpoint every 8", "theta": theta},
            "loss": loss, "grad": g}
