@@ -213,11 +213,11 @@ fos_status fos_process_frames_device(fos_ctx* ctx, int32_t n_frames, const uint8
 
 /*
  * n_frames consecutive frames from HOST memory (same strides as above),
- * pipelined in chunks of up to 8 frames on three streams: the input copy of
+ * pipelined in chunks of up to 16 frames on three streams: the input copy of
  * chunk g+1 and the mask copy of chunk g-1 overlap the kernels of chunk g.
  * Pinned host buffers give the overlap; pageable ones still work, serialised.
  * The context keeps device staging for two chunks (allocated on first use,
- * grown when a call needs more: about 2 * 8 * 7 bytes per pixel).
+ * grown when a call needs more: about 2 * 16 * 7 bytes per pixel).
  * Synchronous: returns when every mask is in host memory.
  */
 fos_status fos_process_frames_host(fos_ctx* ctx, int32_t n_frames, const uint8_t* rgb,

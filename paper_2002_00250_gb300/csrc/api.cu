@@ -434,7 +434,7 @@ fos_status seq_check(fos_ctx* c)
 
 // Staging for `frames` host frames per slot (grown on demand; callers of the
 // host-pointer API have synchronised every earlier use before this runs).
-constexpr int kHostChunk = 8;  // host frames per staging slot
+constexpr int kHostChunk = 16;  // host frames per staging slot (8: 1.6 % slower end to end, 64: 2 %)
 
 fos_status ensure_staging(fos_ctx* c, int frames)
 {

@@ -330,25 +330,44 @@ fused_classify_kernel(const PbasArgs a, const GmmArgs g)
 constexpr int kGradStrip = kGradStripRows, kGradTY = 8;
 constexpr int kGradSW = 34, kGradSWP = 36, kGradSH = kGradStrip + 2, kGradCH = kGradSH * kGradSWP;
 
-// Sums of the Sobel magnitudes of the strip at (x0, y0) of frame a, added to v[4].
+// Sums of the Sobel magnitudes of the strip at (x0, y0) of frame a, added to
+// v[4].  Every thread issues all of its staging loads before it stores any of
+// them, so a block waits for one memory round trip, not one per row of loads.
 __device__ __forceinline__ void grad_strip(const PbasArgs& a, int x0, int y0, uint8_t* sm, uint32_t (&v)[4])
 {
+    constexpr int NS = kGradSH * kGradSW, NTH = 32 * kGradTY, NIT = (NS + NTH - 1) / NTH;
     const int tid = threadIdx.y * 32 + threadIdx.x;
     const bool mapped = a.Wd != a.W || a.Hd != a.H;
-    for (int idx = tid; idx < kGradSH * kGradSW; idx += 32 * kGradTY) {
-        const int r = idx / kGradSW, col = idx - r * kGradSW;
-        const int gx = min(max(x0 - 1 + col, 0), a.W - 1);
-        const int gy = min(max(y0 - 1 + r, 0), a.H - 1);
-        const int64_t p = int64_t(gy) * a.W + gx;
-        const int o = r * kGradSWP + col;
-        constexpr int n = 4 * kGradCH;
-        at(sm, o, n, 1, a.oob) = at(a.rgb, 3 * p, 3 * a.P, 2, a.oob);
-        at(sm, kGradCH + o, n, 1, a.oob) = at(a.rgb, 3 * p + 1, 3 * a.P, 2, a.oob);
-        at(sm, 2 * kGradCH + o, n, 1, a.oob) = at(a.rgb, 3 * p + 2, 3 * a.P, 2, a.oob);
-        const int64_t pd = mapped ? int64_t(uint32_t(gy * a.Hd) / uint32_t(a.H)) * a.Wd +
-                                        int64_t(uint32_t(gx * a.Wd) / uint32_t(a.W))
-                                  : p;
-        at(sm, 3 * kGradCH + o, n, 1, a.oob) = uint8_t(depth_to_u8(at(a.depth, pd, depth_extent(a), 3, a.oob), a.depth_fs));
+    uint32_t cr[NIT], cg[NIT], cb[NIT], cd[NIT];
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+        const int idx = tid + k * NTH;
+        if (idx < NS) {
+            const int r = idx / kGradSW, col = idx - r * kGradSW;
+            const int gx = min(max(x0 - 1 + col, 0), a.W - 1);
+            const int gy = min(max(y0 - 1 + r, 0), a.H - 1);
+            const int64_t p = int64_t(gy) * a.W + gx;
+            const int64_t pd = mapped ? int64_t(uint32_t(gy * a.Hd) / uint32_t(a.H)) * a.Wd +
+                                            int64_t(uint32_t(gx * a.Wd) / uint32_t(a.W))
+                                      : p;
+            cr[k] = at(a.rgb, 3 * p, 3 * a.P, 2, a.oob);
+            cg[k] = at(a.rgb, 3 * p + 1, 3 * a.P, 2, a.oob);
+            cb[k] = at(a.rgb, 3 * p + 2, 3 * a.P, 2, a.oob);
+            cd[k] = at(a.depth, pd, depth_extent(a), 3, a.oob);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) {
+        const int idx = tid + k * NTH;
+        if (idx < NS) {
+            const int r = idx / kGradSW, col = idx - r * kGradSW;
+            const int o = r * kGradSWP + col;
+            constexpr int n = 4 * kGradCH;
+            at(sm, o, n, 1, a.oob) = uint8_t(cr[k]);
+            at(sm, kGradCH + o, n, 1, a.oob) = uint8_t(cg[k]);
+            at(sm, 2 * kGradCH + o, n, 1, a.oob) = uint8_t(cb[k]);
+            at(sm, 3 * kGradCH + o, n, 1, a.oob) = uint8_t(depth_to_u8(cd[k], a.depth_fs));
+        }
     }
     __syncthreads();
     const int x = x0 + threadIdx.x;

@@ -1,5 +1,5 @@
 """The host-frame pipeline (fos_process_frames_host): frames staged in chunks
-of up to 8 with padded per-frame pitches on three streams must give the same
+of up to 16 with padded per-frame pitches on three streams must give the same
 masks and model as the same frames processed from device memory, for frame
 counts that are not a multiple of the chunk, odd frame sizes (pitches padded
 to 256 bytes), calls of different lengths one after another (the staging
@@ -22,7 +22,7 @@ def test_host_chunks_equal_device(W, H):
     rgb, depth, _ = scene(W, H, n, seed=W)
     a = fos.Segmenter(W, H, stream_id=2)
     b = fos.Segmenter(W, H, stream_id=2)
-    # host: 1 frame, then 19 (chunks of 8, 8, 3: the staging grows), then 7
+    # host: 1 frame, then 19 (chunks of 16 and 3: the staging grows), then 7
     got_g, got_p = [], []
     for lo, hi in ((0, 1), (1, 20), (20, 27)):
         mg, mp = a.process_host(rgb[lo:hi], depth[lo:hi])

@@ -75,8 +75,8 @@ def test_sequence_with_four_row_tiles_and_depth_of_another_size():
 
 
 def test_host_api_chunks_equal_per_frame():
-    # the host API stages 8 frames per chunk: frame 0 alone, then sequence
-    # launches of 7, 8 and a last single frame
+    # the host API stages 16 frames per chunk: frame 0 alone, then sequence
+    # launches of 15 frames and a last single frame
     from paper_2002_00250_gb300 import fos
     W, H, n = 100, 50, 17
     rgb, depth, _ = scene(W, H, n, seed=7)
