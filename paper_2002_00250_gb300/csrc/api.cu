@@ -18,8 +18,15 @@
 #include "ctx.h"
 #include "fos.h"
 #include "fos_internal.h"
+#include "philox.cuh"
 
 using namespace fos;
+
+void fos::pbas_args_finish(PbasArgs& a)
+{
+    philox_round_keys(a.seed, a.stream_id, a.rk);
+    depth_divisor(a.depth_fs, a.depth_m, a.depth_sh);
+}
 
 namespace {
 
@@ -218,6 +225,7 @@ PbasArgs pbas_args(fos_ctx* c, const uint8_t* rgb, const uint16_t* depth, uint8_
     a.ty = c->opt[FOS_OPT_PBAS_TY];
     a.mask_vec = aligned(mask, uintptr_t(a.px)) ? 1 : 0;
     a.oob = oob_of(c);
+    pbas_args_finish(a);
     return a;
 }
 

@@ -202,7 +202,28 @@ struct PbasArgs {
     uint32_t* own;               // [plane] propagate only: byte c = slot of the pixel's own
                                  // update in channel c of the last frame (0x1F none)
     OobWord* oob;                // range-checked builds: the context's violation record
+    uint32_t rk[20];             // Philox round keys of (seed, stream_id) (pbas_args_finish)
+    uint32_t depth_m;            // depth rescale: floor(x / depth_fs) = (x * depth_m) >> depth_sh
+    int depth_sh;                //   (pbas_args_finish)
 };
+
+// floor(x / fs) = (x * m) >> sh for every 0 <= x < 2^25 and 1 <= fs <= 2^18:
+// the round-up multiplier of Granlund and Montgomery ("Division by invariant
+// integers using multiplication", PLDI 1994): with l = ceil(log2 fs),
+// sh = 25 + l and m = ceil(2^sh / fs), m fs lies in [2^sh, 2^sh + 2^l], which
+// makes the quotient exact for 25-bit x; m < 2^26 + 1 and x m < 2^51.  The
+// depth rescale's numerator d * 255 + fs / 2 stays below 2^25 for 16-bit d.
+inline void depth_divisor(uint32_t fs, uint32_t& m, int& sh)
+{
+    int l = 0;
+    while ((uint64_t(1) << l) < uint64_t(fs)) ++l;
+    sh = 25 + l;
+    m = uint32_t(((uint64_t(1) << sh) + fs - 1) / fs);
+}
+
+// The fields of a PbasArgs derived from others: the Philox round keys of
+// (seed, stream_id) and the depth rescale's multiplier (depth_fs >= 1).
+void pbas_args_finish(PbasArgs& a);
 
 // Extents (elements) of the PBAS buffers, for the range-checked build.
 __host__ __device__ inline int64_t samp_extent(const PbasArgs& a) { return 4 * a.nseg * a.N * kSeg; }

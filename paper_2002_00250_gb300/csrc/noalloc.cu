@@ -148,6 +148,7 @@ extern "C" fos_status fos_pbas_step_noalloc(int32_t width, int32_t height, const
     a.px = 2;
     a.ty = 8;
     a.mask_vec = (reinterpret_cast<uintptr_t>(d_mask) % 2) == 0 ? 1 : 0;
+    pbas_args_finish(a);
 
     LaunchResult r;
     if (t == 0) {

@@ -366,7 +366,7 @@ __device__ __forceinline__ void grad_strip(const PbasArgs& a, int x0, int y0, ui
             at(sm, o, n, 1, a.oob) = uint8_t(cr[k]);
             at(sm, kGradCH + o, n, 1, a.oob) = uint8_t(cg[k]);
             at(sm, 2 * kGradCH + o, n, 1, a.oob) = uint8_t(cb[k]);
-            at(sm, 3 * kGradCH + o, n, 1, a.oob) = uint8_t(depth_to_u8(cd[k], a.depth_fs));
+            at(sm, 3 * kGradCH + o, n, 1, a.oob) = uint8_t(depth_to_u8(cd[k], a.depth_fs, a.depth_m, a.depth_sh));
         }
     }
     __syncthreads();

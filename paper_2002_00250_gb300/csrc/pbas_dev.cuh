@@ -18,10 +18,13 @@ namespace {
 __host__ __device__ constexpr int dir_dx(int j) { return j == 0 || j == 4 ? 0 : (j < 4 ? 1 : -1); }
 __host__ __device__ constexpr int dir_dy(int j) { return j == 2 || j == 6 ? 0 : (j < 2 || j == 7 ? -1 : 1); }
 
-__device__ __forceinline__ uint32_t depth_to_u8(uint32_t d, uint32_t fs)
+// Depth u16 (mm) -> u8: 0 stays 0 (invalid), the full scale fs maps onto
+// 1..255 with round-half-up; the quotient by fs is the context's exact
+// multiply-shift (depth_divisor: m, sh).
+__device__ __forceinline__ uint32_t depth_to_u8(uint32_t d, uint32_t fs, uint32_t m, int sh)
 {
     if (d == 0) return 0;
-    uint32_t q = (d * 255u + (fs >> 1)) / fs;
+    const uint32_t q = uint32_t((uint64_t(d * 255u + (fs >> 1)) * m) >> sh);
     return q < 1u ? 1u : (q > 255u ? 255u : q);
 }
 
@@ -57,7 +60,8 @@ __device__ __forceinline__ void stage_input(const PbasArgs& a, int x0, int y0, u
         const int64_t pd = mapped ? int64_t(uint32_t(gy * a.Hd) / uint32_t(a.H)) * a.Wd +
                                         int64_t(uint32_t(gx * a.Wd) / uint32_t(a.W))
                                   : p;
-        at(sm, 3 * G::CH + o, n, 1, a.oob) = uint8_t(depth_to_u8(at(a.depth, pd, depth_extent(a), 3, a.oob), a.depth_fs));
+        at(sm, 3 * G::CH + o, n, 1, a.oob) = uint8_t(depth_to_u8(at(a.depth, pd, depth_extent(a), 3, a.oob), a.depth_fs,
+                                                                  a.depth_m, a.depth_sh));
     }
 }
 
@@ -372,9 +376,10 @@ struct Draws {
 };
 
 // Random draws for pixel p, frame t, channel c: Philox4x32-10 with counter
-// (p, t, c, 0) and key (seed, stream_id).  Words 0 and 2 give the two coins
-// (24-bit uniform < prob = fl(1/T), T the pixel's learning parameter before
-// this frame's update), word 1 the own slot, word 3 the direction (3 bits)
+// (p, t, c, 0) and key (seed, stream_id), its round keys precomputed in a.rk.
+// Words 0 and 2 give the two coins (24-bit uniform < prob = fl(1/T), T the
+// pixel's learning parameter before this frame's update), word 1 the own
+// slot, word 3 the direction (3 bits)
 // and the neighbour slot (29 bits).
 __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c, float prob, int N)
 {
@@ -394,7 +399,7 @@ __device__ __forceinline__ Draws draws(const PbasArgs& a, uint32_t p, uint32_t c
         }
         return d;
     }
-    const uint4 u = philox4x32_10(make_uint4(p, a.t, c, 0u), make_uint2(a.seed, a.stream_id));
+    const uint4 u = philox4x32_10_rk(make_uint4(p, a.t, c, 0u), a.rk);
     const float two_m24 = 5.9604644775390625e-8f;
     d.coin1 = __fmul_rn(__uint2float_rn(u.x >> 8), two_m24) < prob;
     d.k1 = __umulhi(u.y, uint32_t(N));
